@@ -1,0 +1,336 @@
+"""Benchmark: FP32 extended-stencil FDTD on a 256^3 periodic grid (plane wave, Courant 0.95
+of the scheme's limit) -- forward and adjoint Gcell-updates/s, FP64 forward for comparison,
+roofline fraction of the dominant kernel, end-to-end rate through the C ABI with host buffers,
+and the FP64 CPU oracle as the reported baseline.
+
+One "step" = one leapfrog step (B half step + E step) over the whole grid.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun (N > 1) every rank runs its own replica (weak scaling, no collective on the
+data path); timing is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_CELLS = 256
+LAMBDA = 16.0
+COURANT = 0.95
+SEED = 0
+WORKLOAD = "3D FDTD 256^3 periodic, FP32 fields, extended curl-E stencil (seeded coefficient set 0), " \
+           "plane wave lambda=16 along x, Courant 0.95 of the scheme's limit"
+BYTES_FWD32 = 48.0    # E, B read once and written once per cell-update (FP32)
+BYTES_FWD64 = 96.0
+BYTES_ADJ32 = 60.0    # lambda (6) read+write, E^n (3) read
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=50)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--n", type=int, default=N_CELLS)
+    return p.parse_args()
+
+
+def coeffs():
+    """Seeded coefficient set 0: first admissible draw of the seeded generator."""
+    from paper_1710_06829_gb300 import inputs
+    from paper_1710_06829_gb300 import sim as S
+    s = SEED
+    while True:
+        beta, delta = inputs.random_theta(s, 3)
+        _, smin, _ = S.dt_max(beta, delta, [1, 1, 1], 3)
+        if smin >= 0:
+            return beta, delta
+        s += 1000
+
+
+def coeffs_oracle():
+    from oracle import dispersion as D
+    from paper_1710_06829_gb300 import inputs
+    s = SEED
+    while True:
+        beta, delta = inputs.random_theta(s, 3)
+        smin, _ = D.S_extremes(beta, delta, [1, 1, 1], 3)
+        if smin >= 0:
+            return beta, delta
+        s += 1000
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampler running during the timed region."""
+
+    def __init__(self, index=0):
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        self.index = index
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index),
+                 "--query-gpu=clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.fh,
+                stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        try:
+            rows = [r.split(",") for r in open(self.path).read().strip().splitlines()]
+            sm = [float(r[0]) for r in rows if r[0].strip().replace(".", "").isdigit()]
+            mx = max(float(r[1]) for r in rows)
+            names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+            reasons = sorted({names[i] for r in rows for i in range(4)
+                              if r[4 + i].strip().lower() == "active"})
+            return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                    "reasons": reasons, "samples": len(rows)}
+        except Exception as e:  # noqa: BLE001
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "error": str(e)[:80]}
+
+
+def dist_init(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    return world, rank, local
+
+
+def barrier_max(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ---------------------------------------------------------------------------- reference arm
+
+
+def cpu_oracle_rate(n_cells, budget_s=15.0):
+    """FP64 numpy oracle forward rate on this host (bounded sample: whole steps at full size)."""
+    import numpy as np
+
+    from oracle import dispersion as D
+    from oracle import fdtd as F
+    from paper_1710_06829_gb300 import inputs
+    beta, delta = coeffs_oracle()
+    dt = COURANT * D.dt_max(beta, delta, [1, 1, 1], 3)
+    shape = (n_cells, n_cells, n_cells)
+    kx = 2 * math.pi * round(n_cells / LAMBDA) / n_cells
+    fields = inputs.plane_wave(shape, (kx, 0, 0), (0, 0, 1), [1, 1, 1])
+    s = F.State(fields[:3], fields[3:])
+    c = F.Coeffs(beta, delta, [1, 1, 1], dt)
+    steps = 0
+    t0 = time.perf_counter()
+    while True:
+        F.step(s, c)
+        steps += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s or steps >= 20:
+            break
+    cells = float(n_cells) ** 3
+    del np
+    return {"value": steps * cells / el / 1e9, "unit": "Gcell-updates/s", "cores": 1,
+            "kind": "oracle",
+            "sample": f"{steps} FP64 numpy forward steps at {n_cells}^3 in {el:.1f} s (single thread)"}
+
+
+def run_reference(args):
+    world, rank, _ = dist_init(args)
+    if rank != 0:
+        return
+    base = cpu_oracle_rate(args.n)
+    cells = float(args.n) ** 3
+    steps = max(1, min(args.steps, 3))
+    t0 = time.perf_counter()
+    rate = cpu_oracle_rate(args.n, budget_s=5.0 * steps)
+    el = time.perf_counter() - t0
+    line = {"impl": "reference", "metric": "Gcell-updates/s", "value": rate["value"],
+            "unit": "Gcell-updates/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": cells / (rate["value"] * 1e9) * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "l2": "inputs larger than L2"},
+            "cpu_baseline": {**rate, "kind": "oracle"},
+            "e2e": {"value": rate["value"], "unit": "Gcell-updates/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    del base, el
+    print(json.dumps(line))
+
+
+# ---------------------------------------------------------------------------- our arm
+
+
+def time_events(fn, steps, stream):
+    import torch
+    start = torch.cuda.Event(enable_timing=True)
+    stop = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    start.record(stream)
+    for _ in range(steps):
+        fn()
+    stop.record(stream)
+    torch.cuda.synchronize()
+    return start.elapsed_time(stop) / 1e3
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    world, rank, local = dist_init(args)
+    torch.cuda.set_device(local)
+    from paper_1710_06829_gb300 import _lib as L
+    from paper_1710_06829_gb300 import inputs
+    from paper_1710_06829_gb300 import sim as S
+
+    n = args.n
+    shape = (n, n, n)
+    cells = float(n) ** 3
+    beta, delta = coeffs()
+    dtm, _, _ = S.dt_max(beta, delta, [1, 1, 1], 3)
+    dt = COURANT * dtm
+    kx = 2 * math.pi * round(n / LAMBDA) / n
+    fields64 = inputs.plane_wave(shape, (kx, 0, 0), (0, 0, 1), [1, 1, 1])
+    fields = [torch.from_numpy(f.astype(np.float32)) for f in fields64]
+    stream = torch.cuda.current_stream()
+
+    # --- forward FP32
+    sm = S.Simulation(shape, [1, 1, 1], dt, beta, delta, dims=3, dtype="f32", stream=stream)
+    sm.set_state(fields)
+    for _ in range(max(3, args.warmup)):
+        sm.step(1)
+    barrier(world)
+    with Clocks(local) as clk:
+        t_fwd = time_events(lambda: sm.step(1), args.steps, stream)
+    t_fwd = barrier_max(t_fwd, world)
+    fwd = world * cells * args.steps / t_fwd / 1e9
+
+    # --- adjoint FP32 (record a segment, then reverse it)
+    seg = min(args.steps, 20)
+    sm.step(seg, record=True)
+    sm.set_adjoint([f for f in fields])
+    grad = torch.zeros(12, dtype=torch.float64, device="cuda")
+    sm.step_adjoint(2, grad)    # warm-up
+    sm.step(seg, record=True)
+    torch.cuda.synchronize()
+    t_adj = time_events(lambda: sm.step_adjoint(seg, grad), 1, stream)
+    t_adj = barrier_max(t_adj, world)
+    adj = world * cells * seg / t_adj / 1e9
+
+    # --- end to end through the C ABI with host buffers: upload, 100 steps, download
+    n_inner = 20
+    pinned_in = [f.pin_memory() for f in fields]
+    pinned_out = [torch.empty_like(f).pin_memory() for f in fields]
+
+    def e2e_step():
+        sm.set_state_host(pinned_in)
+        sm.step(n_inner)
+        sm.get_state_host(pinned_out)
+    e2e_step()
+    e2e_reps = 3
+    t0 = time.perf_counter()
+    for _ in range(e2e_reps):
+        e2e_step()
+    torch.cuda.synchronize()
+    t_e2e = barrier_max(time.perf_counter() - t0, world)
+    e2e = world * cells * n_inner * e2e_reps / t_e2e / 1e9
+    sm.close()
+
+    # --- FP64 forward for comparison
+    sm64 = S.Simulation(shape, [1, 1, 1], dt, beta, delta, dims=3, dtype="f64", stream=stream)
+    sm64.set_state([torch.from_numpy(f) for f in fields64])
+    for _ in range(3):
+        sm64.step(1)
+    k64 = max(3, args.steps // 5)
+    t64 = barrier_max(time_events(lambda: sm64.step(1), k64, stream), world)
+    fwd64 = world * cells * k64 / t64 / 1e9
+    sm64.close()
+
+    if rank != 0:
+        return
+    peak, peak_kind = peaks()
+    achieved = BYTES_FWD32 * cells / (t_fwd / args.steps) / 1e9
+    line = {
+        "metric": "Gcell-updates/s", "value": fwd, "unit": "Gcell-updates/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_fwd / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "grid": [n, n, n], "l2": "inputs larger than L2 "
+                   "(state 6 x 4 B x 256^3 = 403 MB per copy)", "parallelism": f"replicas x{world}"},
+        "adjoint": {"value": adj, "unit": "Gcell-updates/s", "steps": seg,
+                    "roofline_frac": BYTES_ADJ32 * cells * seg / t_adj / 1e9 / peak},
+        "fp64_forward": {"value": fwd64, "unit": "Gcell-updates/s",
+                         "roofline_frac": BYTES_FWD64 * cells * k64 / t64 / 1e9 / peak},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
+                     "kernel": "forward step (48 B/cell-update algorithmic)"},
+        "e2e": {"value": e2e, "unit": "Gcell-updates/s",
+                "h2d_bytes_per_step": int(6 * 4 * cells), "d2h_bytes_per_step": int(6 * 4 * cells),
+                "step": f"host upload + {n_inner} leapfrog steps + host download"},
+        "gpu_launches": args.steps * 2,
+        "clocks": clk.summary(),
+    }
+    if world == 1:
+        line["cpu_baseline"] = cpu_oracle_rate(n)
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

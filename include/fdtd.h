@@ -1,0 +1,188 @@
+/*
+ * fdtd.h -- C ABI of libfdtd: leapfrog FDTD on the staggered Yee grid with the
+ * extended, coefficient-parameterised curl-E stencil of Blinne et al.,
+ * "A Systematic Approach to Numerical Dispersion in Maxwell Solvers"
+ * (arXiv:1710.06829), its adjoint, and the paper's dispersion norm.
+ *
+ * Units: c = 1, mu0 = eps0 = 1.
+ *
+ * Grid and staggering (App. A, update equations).  Field arrays are dense
+ * [nz][ny][nx] (x fastest).  Integer index (i,j,k) of each component denotes
+ *     E_x (i+1/2, j, k)    B_x (i, j+1/2, k+1/2)
+ *     E_y (i, j+1/2, k)    B_y (i+1/2, j, k+1/2)
+ *     E_z (i, j, k+1/2)    B_z (i+1/2, j+1/2, k)
+ * All axes are periodic.  A field array set is always ordered
+ * {E_x, E_y, E_z, B_x, B_y, B_z}.
+ *
+ * Coefficients (Sec. 2, Eq. D*): beta[i][j] is beta_ij (taps of D*_i displaced
+ * along axis j; the diagonal is ignored), delta[i] is delta_i.  alpha_i is
+ * never passed: it is eliminated with Eq. (alpha),
+ *     alpha_i = 1 - 2 sum_{j != i} beta_ij - 3 delta_i.
+ * With dims < 3 every coefficient that refers to an absent axis is ignored.
+ *
+ * Memory: the library owns the simulation state (two padded copies of the six
+ * fields, ping-ponged by the fused step kernel), the adjoint state, the
+ * recorded E history and the checkpoint slots, all in device memory it
+ * allocates with cudaMalloc.  Caller buffers are only read or written during
+ * the call that receives them (asynchronously on the handle's stream).
+ *
+ * Errors: every entry point returns an int status (FDTD_OK = 0, negative on
+ * failure) and sets a thread-local message readable with fdtd_last_error().
+ * Argument and stability errors are detected synchronously; CUDA errors are
+ * reported by the call that observes them.
+ */
+#ifndef FDTD_H
+#define FDTD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define FDTD_OK          0
+#define FDTD_EINVAL     -1   /* bad argument, shape or layout */
+#define FDTD_EUNSTABLE  -2   /* coefficients/dt violate Eq. (constraints) */
+#define FDTD_ECUDA      -3   /* a CUDA runtime or driver call failed */
+#define FDTD_ENOMEM     -4   /* device allocation failed */
+#define FDTD_ENONFINITE -5   /* a non-finite value was found */
+#define FDTD_ESTATE     -6   /* call not valid in the handle's current state */
+
+/* dtypes */
+#define FDTD_F32 0
+#define FDTD_F64 1
+
+/* where caller buffers live */
+#define FDTD_MEM_DEVICE 0
+#define FDTD_MEM_HOST   1
+
+/* sources */
+#define FDTD_SRC_NONE  0
+#define FDTD_SRC_BUNCH 1
+
+/* dispersion-norm weights (Sec. 4 and Eq. norm_x_axis) */
+#define FDTD_W_UNIFORM 0   /* w = 1 */
+#define FDTD_W_CONE_X  1   /* w = 1 inside a cone of half-angle `param` (rad) about +x, else 0 */
+#define FDTD_W_GAUSS_Y 2   /* w = exp(-(k_y dy / param)^2) */
+
+typedef struct fdtd_handle fdtd_handle;
+
+typedef struct {
+    int32_t dims;          /* 1, 2 or 3: axes that carry wave propagation */
+    int32_t nx, ny, nz;    /* cells; nx % 4 == 0; dims 2 needs nz == 1, dims 1 ny == nz == 1 */
+    int32_t dtype;         /* FDTD_F32 or FDTD_F64: precision of fields and stepping */
+    int32_t absorb_cells;  /* width L of absorbing sponge layers on +-y and +-z (0 = none) */
+    double  absorb_sigma;  /* sponge strength: fields scaled by 1 - sigma (d/L)^3, d = 1..L */
+} fdtd_grid;
+
+typedef struct {
+    double beta[3][3];
+    double delta[3];
+} fdtd_coeffs;
+
+/* Rigid Gaussian charge moving along +x (stand-in for a PIC beam).  Its current
+ * J_x^{n+1/2} is evaluated inside the E update from the cell-integrated
+ * Gaussian so that the discrete continuity equation of App. A holds exactly. */
+typedef struct {
+    int32_t kind;          /* FDTD_SRC_NONE or FDTD_SRC_BUNCH */
+    double q, v;           /* charge, speed (units of c) */
+    double x0, y0, z0;     /* centre at absolute step 0 (length units) */
+    double sigma_par, sigma_perp;
+} fdtd_source;
+
+/* Probe: squared misfit of one E component on the plane i = x_index against a
+ * target, summed over all probed steps (the propagation loss of the
+ * differentiable path). */
+typedef struct {
+    int32_t component;     /* 0, 1, 2 -> E_x, E_y, E_z */
+    int32_t x_index;       /* plane i = x_index */
+    const void* target;    /* device, grid dtype, [target_steps][nz][ny]; row s-1 is the target
+                              at absolute step s (after s leapfrog steps) */
+    int64_t target_steps;
+} fdtd_probe;
+
+/* ---- handle ------------------------------------------------------------- */
+
+/* Create a simulation.  dx[3] > 0; dt > 0.  Validates Eq. (constraints):
+ * returns FDTD_EUNSTABLE if dt^2 max_k S(k) > 1 or min_k S(k) < 0.
+ * `stream` is a cudaStream_t (NULL = legacy default stream).  The initial
+ * state is all zero.  The handle is returned in *out. */
+int fdtd_create(const fdtd_grid* grid, const double dx[3], double dt, const fdtd_coeffs* coeffs,
+                void* stream, fdtd_handle** out);
+
+/* Replace coefficients and dt (re-validated as in fdtd_create). */
+int fdtd_set_coeffs(fdtd_handle* h, double dt, const fdtd_coeffs* coeffs);
+
+/* Copy the six fields in (set) or out (get).  fields[c] points to nx*ny*nz
+ * elements of the grid dtype in `mem` (FDTD_MEM_DEVICE or FDTD_MEM_HOST).
+ * For set_state a NULL entry means zero.  Host buffers may be pageable; the
+ * call returns after the host copy has completed.  set_state also resets the
+ * step counter to `step0`. */
+int fdtd_set_state(fdtd_handle* h, void* const fields[6], int32_t mem, int64_t step0);
+int fdtd_get_state(fdtd_handle* h, void* const fields[6], int32_t mem);
+
+/* Absolute step counter (number of leapfrog steps taken since set_state's step0). */
+int fdtd_get_step(fdtd_handle* h, int64_t* step);
+
+/* Advance n >= 0 leapfrog steps (App. A update equations):
+ *   B^{n+1/2} = B^{n-1/2} - dt D* x E^n            (extended stencil, Eq. D*)
+ *   E^{n+1}   = E^n + dt (D x B^{n+1/2} - J^{n+1/2}) (Yee stencil)
+ * `src` may be NULL (no current).  If `probe` is non-NULL, after every step s
+ * the probe misfit sum_{j,k} (E_c^s[x_index, j, k] - T^s[j,k])^2 is added in
+ * FP64 to *loss_dev (one device double).  If `record` is non-zero, E^n before
+ * each step and E after the last one are stored in the handle's history
+ * (n + 1 snapshots, replacing any earlier history) for fdtd_step_adjoint. */
+int fdtd_step(fdtd_handle* h, int32_t n, const fdtd_source* src, const fdtd_probe* probe,
+              double* loss_dev, int32_t record);
+
+/* Checkpoint slots: op 0 = save the current state (fields + step counter) to
+ * `slot`, op 1 = restore it.  Slots are allocated on first save. */
+int fdtd_checkpoint(fdtd_handle* h, int32_t slot, int32_t op);
+
+/* Adjoint state lambda = (lambda_E, lambda_B), same layout as the fields.
+ * set with NULL entries = zero. */
+int fdtd_set_adjoint(fdtd_handle* h, void* const fields[6], int32_t mem);
+int fdtd_get_adjoint(fdtd_handle* h, void* const fields[6], int32_t mem);
+
+/* Run n reverse steps of the transposed leapfrog map over the recorded
+ * history (which must hold >= n steps; the last n recorded steps are used,
+ * newest first).  Before reversing the step that produced E^s, the probe
+ * source 2 (E_c^s - T^s) is added to lambda_E on the probe plane (if probe is
+ * non-NULL).  Adds dt * sum_cells lambda_B^{s+1/2} . (dF/dtheta) E^s to
+ * grad_dev (12 device doubles: beta[3][3] row-major, then delta[3]; the
+ * diagonal entries stay unchanged), where F E = -D* x E.  The sponge is
+ * applied as its own transpose.  On return the history is consumed. */
+int fdtd_step_adjoint(fdtd_handle* h, int32_t n, const fdtd_probe* probe, double* grad_dev);
+
+/* Block until all work on the handle's stream has finished; reports any
+ * asynchronous CUDA error. */
+int fdtd_sync(fdtd_handle* h);
+
+void fdtd_destroy(fdtd_handle* h);
+
+/* ---- dispersion analysis (no handle) ------------------------------------ */
+
+/* Eq. (norm) by the midpoint rule on an N[0] x N[1] (x N[2]) grid over the
+ * positive octant 0 < k_i < pi/dx_i (axes beyond dims are absent), with
+ * omega(k) from Eq. (dispersion_relation), and its exact gradient.
+ * out (host, 14 doubles): [0] norm, [1..9] d/d beta (3x3 row-major, diagonal
+ * 0), [10..12] d/d delta, [13] d/d dt.  Accumulation is FP64 on the GPU;
+ * per-point arithmetic is FP64.  Runs on `stream` and synchronises it. */
+int disp_norm_eval(const fdtd_coeffs* coeffs, double dt, const double dx[3], int32_t dims,
+                   const int32_t N[3], int32_t weight, double weight_param, double* out,
+                   void* stream);
+
+/* Exact extremes of S(k) = sum_i s_i^2 A_i over the Brillouin box (host, FP64)
+ * and dt_max = 1/sqrt(max S), the CFL limit of Eq. (constraints). */
+int fdtd_dt_max(const fdtd_coeffs* coeffs, const double dx[3], int32_t dims, double* dt_max,
+                double* s_min, double* s_max);
+
+/* Thread-local description of the last error (never NULL). */
+const char* fdtd_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FDTD_H */

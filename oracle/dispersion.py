@@ -69,14 +69,15 @@ def s_sq(k, dx):
     return np.sin(0.5 * k * dx) ** 2 / dx ** 2
 
 
-def S_paper(kx, ky, kz, beta, delta, dx, dims=3):
+def S_paper(kx, ky, kz, beta, delta, dx, dims=3, alpha_override=None):
     """Right-hand side of Eq. (dispersion_relation): sum_i s_i^2 A_i, with A_i as printed.
 
     A_x = alpha_x + 2 beta_xy cos(k_y dy) + 2 beta_xz cos(k_z dz) + delta_x (1 + 2 cos(k_x dx)),
-    and cyclically for y and z.
+    and cyclically for y and z.  ``alpha_override`` replaces Eq. (alpha); it serves
+    only to evaluate the relation for coefficients rounded to a working precision.
     """
     b, d = clean_coeffs(beta, delta, dims)
-    a = alpha(b, d, dims)
+    a = alpha(b, d, dims) if alpha_override is None else np.asarray(alpha_override, dtype=np.float64)
     k = [np.asarray(kx, dtype=np.float64), np.asarray(ky, dtype=np.float64),
          np.asarray(kz, dtype=np.float64)]
     dxa = np.asarray(dx, dtype=np.float64)

@@ -54,14 +54,20 @@ def _plus(a, b):
 class Coeffs:
     """beta_ij / delta_i of Eq. (D*) with alpha_i from Eq. (alpha); grid spacing and dt."""
 
-    def __init__(self, beta, delta, dx, dt):
+    def __init__(self, beta, delta, dx, dt, alpha=None):
+        """``alpha`` overrides Eq. (alpha); it is used only to run the scheme with
+        coefficients as rounded to a lower working precision, where the rounded
+        alpha no longer satisfies Eq. (alpha) exactly."""
         self.beta = np.array(beta, dtype=np.float64).reshape(3, 3)
         self.delta = np.array(delta, dtype=np.float64).reshape(3)
         self.dx = np.array(dx, dtype=np.float64).reshape(3)
         self.dt = float(dt)
-        self.alpha = np.array([
-            1.0 - 2.0 * sum(self.beta[i, j] for j in range(3) if j != i) - 3.0 * self.delta[i]
-            for i in range(3)])
+        if alpha is not None:
+            self.alpha = np.array(alpha, dtype=np.float64).reshape(3)
+        else:
+            self.alpha = np.array([
+                1.0 - 2.0 * sum(self.beta[i, j] for j in range(3) if j != i) - 3.0 * self.delta[i]
+                for i in range(3)])
 
 
 # ----------------------------------------------------------------------------

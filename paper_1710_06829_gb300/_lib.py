@@ -1,0 +1,212 @@
+"""ctypes binding of libfdtd (include/fdtd.h): argument marshalling only.
+
+Every function here has the name of the C entry point it wraps and raises
+``FdtdError`` on a non-zero status.  The shared library is built in-tree by
+``paper_1710_06829_gb300.build``; if it is missing, importing the compute
+entry points fails loudly (there is no CPU fallback).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libfdtd.so")
+
+FDTD_OK = 0
+FDTD_EINVAL = -1
+FDTD_EUNSTABLE = -2
+FDTD_ECUDA = -3
+FDTD_ENOMEM = -4
+FDTD_ENONFINITE = -5
+FDTD_ESTATE = -6
+
+FDTD_F32 = 0
+FDTD_F64 = 1
+FDTD_MEM_DEVICE = 0
+FDTD_MEM_HOST = 1
+FDTD_SRC_NONE = 0
+FDTD_SRC_BUNCH = 1
+FDTD_W_UNIFORM = 0
+FDTD_W_CONE_X = 1
+FDTD_W_GAUSS_Y = 2
+
+STATUS_NAMES = {0: "FDTD_OK", -1: "FDTD_EINVAL", -2: "FDTD_EUNSTABLE", -3: "FDTD_ECUDA",
+                -4: "FDTD_ENOMEM", -5: "FDTD_ENONFINITE", -6: "FDTD_ESTATE"}
+
+# every symbol include/fdtd.h declares
+EXPORTS = ["fdtd_create", "fdtd_set_coeffs", "fdtd_set_state", "fdtd_get_state", "fdtd_get_step",
+           "fdtd_step", "fdtd_checkpoint", "fdtd_set_adjoint", "fdtd_get_adjoint",
+           "fdtd_step_adjoint", "fdtd_sync", "fdtd_destroy", "disp_norm_eval", "fdtd_dt_max",
+           "fdtd_last_error"]
+
+
+class FdtdError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class fdtd_grid(C.Structure):
+    _fields_ = [("dims", C.c_int32), ("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32),
+                ("dtype", C.c_int32), ("absorb_cells", C.c_int32), ("absorb_sigma", C.c_double)]
+
+
+class fdtd_coeffs(C.Structure):
+    _fields_ = [("beta", (C.c_double * 3) * 3), ("delta", C.c_double * 3)]
+
+
+class fdtd_source(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("q", C.c_double), ("v", C.c_double), ("x0", C.c_double),
+                ("y0", C.c_double), ("z0", C.c_double), ("sigma_par", C.c_double),
+                ("sigma_perp", C.c_double)]
+
+
+class fdtd_probe(C.Structure):
+    _fields_ = [("component", C.c_int32), ("x_index", C.c_int32), ("target", C.c_void_p),
+                ("target_steps", C.c_int64)]
+
+
+_lib = None
+
+
+def load():
+    """Load libfdtd.so (building it first if it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    from . import build as _build
+    if not _build.up_to_date():
+        _build.build()
+    lib = C.CDLL(LIB_PATH)
+    P = C.c_void_p
+    I32 = C.c_int32
+    D = C.c_double
+    pd = C.POINTER(C.c_double)
+    lib.fdtd_create.argtypes = [C.POINTER(fdtd_grid), pd, D, C.POINTER(fdtd_coeffs), P,
+                                C.POINTER(P)]
+    lib.fdtd_set_coeffs.argtypes = [P, D, C.POINTER(fdtd_coeffs)]
+    lib.fdtd_set_state.argtypes = [P, C.POINTER(P), I32, C.c_int64]
+    lib.fdtd_get_state.argtypes = [P, C.POINTER(P), I32]
+    lib.fdtd_get_step.argtypes = [P, C.POINTER(C.c_int64)]
+    lib.fdtd_step.argtypes = [P, I32, C.POINTER(fdtd_source), C.POINTER(fdtd_probe), P, I32]
+    lib.fdtd_checkpoint.argtypes = [P, I32, I32]
+    lib.fdtd_set_adjoint.argtypes = [P, C.POINTER(P), I32]
+    lib.fdtd_get_adjoint.argtypes = [P, C.POINTER(P), I32]
+    lib.fdtd_step_adjoint.argtypes = [P, I32, C.POINTER(fdtd_probe), P]
+    lib.fdtd_sync.argtypes = [P]
+    lib.fdtd_destroy.argtypes = [P]
+    lib.fdtd_destroy.restype = None
+    lib.disp_norm_eval.argtypes = [C.POINTER(fdtd_coeffs), D, pd, I32, C.POINTER(I32), I32, D,
+                                   pd, P]
+    lib.fdtd_dt_max.argtypes = [C.POINTER(fdtd_coeffs), pd, I32, pd, pd, pd]
+    lib.fdtd_last_error.restype = C.c_char_p
+    for name in EXPORTS:
+        if name not in ("fdtd_destroy", "fdtd_last_error"):
+            getattr(lib, name).restype = C.c_int
+    _lib = lib
+    return lib
+
+
+def check(status):
+    if status != FDTD_OK:
+        raise FdtdError(status, load().fdtd_last_error().decode())
+
+
+def _ptrs6(fields):
+    arr = (C.c_void_p * 6)()
+    if fields is not None:
+        for i, f in enumerate(fields):
+            arr[i] = f
+    return arr
+
+
+def make_coeffs(beta, delta):
+    c = fdtd_coeffs()
+    for i in range(3):
+        for j in range(3):
+            c.beta[i][j] = float(beta[i][j])
+        c.delta[i] = float(delta[i])
+    return c
+
+
+def _d3(x):
+    return (C.c_double * 3)(*[float(v) for v in x])
+
+
+# ---- entry points (same names as the C ABI) ---------------------------------
+
+
+def fdtd_create(grid: fdtd_grid, dx, dt, coeffs: fdtd_coeffs, stream=0):
+    h = C.c_void_p()
+    check(load().fdtd_create(C.byref(grid), _d3(dx), float(dt), C.byref(coeffs),
+                             C.c_void_p(stream), C.byref(h)))
+    return h
+
+
+def fdtd_set_coeffs(h, dt, coeffs):
+    check(load().fdtd_set_coeffs(h, float(dt), C.byref(coeffs)))
+
+
+def fdtd_set_state(h, fields, mem, step0=0):
+    check(load().fdtd_set_state(h, _ptrs6(fields), mem, int(step0)))
+
+
+def fdtd_get_state(h, fields, mem):
+    check(load().fdtd_get_state(h, _ptrs6(fields), mem))
+
+
+def fdtd_get_step(h):
+    s = C.c_int64()
+    check(load().fdtd_get_step(h, C.byref(s)))
+    return s.value
+
+
+def fdtd_step(h, n, src=None, probe=None, loss_dev=None, record=0):
+    check(load().fdtd_step(h, int(n), C.byref(src) if src is not None else None,
+                           C.byref(probe) if probe is not None else None,
+                           C.c_void_p(loss_dev) if loss_dev else None, int(record)))
+
+
+def fdtd_checkpoint(h, slot, op):
+    check(load().fdtd_checkpoint(h, int(slot), int(op)))
+
+
+def fdtd_set_adjoint(h, fields, mem):
+    check(load().fdtd_set_adjoint(h, _ptrs6(fields), mem))
+
+
+def fdtd_get_adjoint(h, fields, mem):
+    check(load().fdtd_get_adjoint(h, _ptrs6(fields), mem))
+
+
+def fdtd_step_adjoint(h, n, probe=None, grad_dev=None):
+    check(load().fdtd_step_adjoint(h, int(n), C.byref(probe) if probe is not None else None,
+                                   C.c_void_p(grad_dev)))
+
+
+def fdtd_sync(h):
+    check(load().fdtd_sync(h))
+
+
+def fdtd_destroy(h):
+    load().fdtd_destroy(h)
+
+
+def disp_norm_eval(coeffs, dt, dx, dims, N, weight=FDTD_W_UNIFORM, weight_param=0.0, stream=0):
+    out = (C.c_double * 14)()
+    n3 = (C.c_int32 * 3)(*[int(v) for v in N])
+    check(load().disp_norm_eval(C.byref(coeffs), float(dt), _d3(dx), int(dims), n3, int(weight),
+                                float(weight_param), out, C.c_void_p(stream)))
+    return list(out)
+
+
+def fdtd_dt_max(coeffs, dx, dims):
+    dtm, smin, smax = C.c_double(), C.c_double(), C.c_double()
+    check(load().fdtd_dt_max(C.byref(coeffs), _d3(dx), int(dims), C.byref(dtm), C.byref(smin),
+                             C.byref(smax)))
+    return dtm.value, smin.value, smax.value
+
+
+def fdtd_last_error():
+    return load().fdtd_last_error().decode()

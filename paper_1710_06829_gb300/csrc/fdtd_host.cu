@@ -1,0 +1,784 @@
+// Host side of libfdtd: the C ABI declared in include/fdtd.h.
+//
+// Coefficient preprocessing (FP64): alpha from Eq. (alpha), exact extremes of
+// S(k) over the Brillouin box for Eq. (constraints), update multipliers
+// rounded once to the working precision.  State management (padded library
+// layout, ping-pong sets, adjoint state, recorded E history, checkpoint
+// slots) and the launch sequences of the forward and adjoint steps.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "fdtd_internal.cuh"
+
+namespace fdtd {
+
+static thread_local char g_err[512] = "no error";
+
+void set_error(const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+
+template <typename T>
+void launch_bunch_table(int nx, int n, double x0, double vdt, double inv_sig, double scale,
+                        double dx, double Lx, long long step0, T* out, cudaStream_t st);
+void launch_disp_norm(const double alpha[3], const double beta[3][3], const double delta[3],
+                      double dt, const double dx[3], int dims, const int N[3], int weight,
+                      double wparam, double* scratch, double** out_dev, cudaStream_t st);
+size_t norm_scratch_doubles(const int N[3], long long npts);
+
+// ---------------------------------------------------------------------------
+// coefficient preprocessing
+// ---------------------------------------------------------------------------
+
+struct Clean {
+    double beta[3][3];
+    double delta[3];
+    double alpha[3];
+};
+
+static Clean clean_coeffs(const fdtd_coeffs* c, int dims) {
+    Clean r;
+    for (int i = 0; i < 3; ++i) {
+        r.delta[i] = (i < dims) ? c->delta[i] : 0.0;
+        for (int j = 0; j < 3; ++j)
+            r.beta[i][j] = (i != j && i < dims && j < dims) ? c->beta[i][j] : 0.0;
+    }
+    for (int i = 0; i < 3; ++i)
+        r.alpha[i] = 1.0 - 2.0 * (r.beta[i][0] + r.beta[i][1] + r.beta[i][2]) - 3.0 * r.delta[i];
+    return r;
+}
+
+// S as a quadratic in u_i = s_i^2 in [0, 1/dx_i^2] (Sec. 3 with alpha eliminated):
+//   S(u) = sum_i u_i - sum_i 4 dx_i^2 delta_i u_i^2 - sum_{i != j} 4 dx_j^2 beta_ij u_i u_j.
+// Its extremes over the box are attained where every coordinate is at a bound or
+// free with vanishing partial derivative; all 3^dims patterns are solved.
+static void S_extremes(const Clean& cc, const double dx[3], int dims, double* smin,
+                       double* smax) {
+    double Q[3][3] = {{0}};
+    for (int i = 0; i < dims; ++i) {
+        Q[i][i] = 4.0 * dx[i] * dx[i] * cc.delta[i];
+        for (int j = 0; j < dims; ++j)
+            if (i != j) Q[i][j] = 2.0 * (dx[j] * dx[j] * cc.beta[i][j] + dx[i] * dx[i] * cc.beta[j][i]);
+    }
+    double ub[3];
+    for (int i = 0; i < 3; ++i) ub[i] = 1.0 / (dx[i] * dx[i]);
+    double lo = 1e300, hi = -1e300;
+    int npat = 1;
+    for (int i = 0; i < dims; ++i) npat *= 3;
+    for (int p = 0; p < npat; ++p) {
+        int pat[3] = {0, 0, 0};
+        int t = p;
+        for (int i = 0; i < dims; ++i) { pat[i] = t % 3; t /= 3; }
+        double u[3] = {0, 0, 0};
+        int fr[3], nf = 0;
+        for (int i = 0; i < dims; ++i) {
+            if (pat[i] == 1) u[i] = ub[i];
+            if (pat[i] == 2) fr[nf++] = i;
+        }
+        bool ok = true;
+        if (nf > 0) {
+            // solve 2 Q_FF u_F = 1 - 2 Q_F,fixed u_fixed by Gaussian elimination with pivoting
+            double A[3][4];
+            for (int r = 0; r < nf; ++r) {
+                double rhs = 1.0;
+                for (int j = 0; j < dims; ++j)
+                    if (pat[j] != 2) rhs -= 2.0 * Q[fr[r]][j] * u[j];
+                for (int s = 0; s < nf; ++s) A[r][s] = 2.0 * Q[fr[r]][fr[s]];
+                A[r][nf] = rhs;
+            }
+            double scale = 0.0;
+            for (int r = 0; r < nf; ++r)
+                for (int s = 0; s < nf; ++s) scale = fmax(scale, fabs(A[r][s]));
+            for (int col = 0; col < nf && ok; ++col) {
+                int piv = col;
+                for (int r = col + 1; r < nf; ++r)
+                    if (fabs(A[r][col]) > fabs(A[piv][col])) piv = r;
+                if (fabs(A[piv][col]) <= 1e-13 * fmax(scale, 1.0)) { ok = false; break; }
+                for (int s = 0; s <= nf; ++s) { double tmp = A[col][s]; A[col][s] = A[piv][s]; A[piv][s] = tmp; }
+                for (int r = 0; r < nf; ++r) {
+                    if (r == col) continue;
+                    const double f = A[r][col] / A[col][col];
+                    for (int s = col; s <= nf; ++s) A[r][s] -= f * A[col][s];
+                }
+            }
+            if (!ok) continue;
+            for (int r = 0; r < nf; ++r) {
+                const double v = A[r][nf] / A[r][r];
+                const int i = fr[r];
+                if (v < -1e-15 || v > ub[i] * (1.0 + 1e-15)) { ok = false; break; }
+                u[i] = fmin(fmax(v, 0.0), ub[i]);
+            }
+            if (!ok) continue;
+        }
+        double S = 0.0;
+        for (int i = 0; i < dims; ++i) S += u[i];
+        for (int i = 0; i < dims; ++i)
+            for (int j = 0; j < dims; ++j) S -= Q[i][j] * u[i] * u[j];
+        lo = fmin(lo, S);
+        hi = fmax(hi, S);
+    }
+    *smin = lo;
+    *smax = hi;
+}
+
+static int validate(const Clean& cc, const double dx[3], int dims, double dt) {
+    for (int i = 0; i < 3; ++i) {
+        if (!std::isfinite(cc.delta[i]) || !std::isfinite(cc.alpha[i])) {
+            set_error("non-finite coefficient");
+            return FDTD_EINVAL;
+        }
+        for (int j = 0; j < 3; ++j)
+            if (!std::isfinite(cc.beta[i][j])) {
+                set_error("non-finite coefficient");
+                return FDTD_EINVAL;
+            }
+    }
+    if (!(dt > 0.0) || !std::isfinite(dt)) {
+        set_error("dt must be positive and finite (got %g)", dt);
+        return FDTD_EINVAL;
+    }
+    double smin, smax;
+    S_extremes(cc, dx, dims, &smin, &smax);
+    if (smin < -1e-12) {
+        set_error("Eq. (constraints) violated: min_k S = %.6g < 0", smin);
+        return FDTD_EUNSTABLE;
+    }
+    if (dt * dt * smax > 1.0 + 1e-12) {
+        set_error("Eq. (constraints) violated: dt^2 max_k S = %.12g > 1 (dt_max = %.12g)",
+                  dt * dt * smax, 1.0 / sqrt(smax));
+        return FDTD_EUNSTABLE;
+    }
+    return FDTD_OK;
+}
+
+template <typename T>
+static Mult<T> make_mult(const Clean& cc, const double dx[3], double dt) {
+    Mult<T> m;
+    for (int a = 0; a < 3; ++a) {
+        m.cA[a] = (T)(dt * cc.alpha[a] / dx[a]);
+        m.cD[a] = (T)(dt * cc.delta[a] / dx[a]);
+        for (int b = 0; b < 3; ++b) m.cB[a][b] = (T)(dt * cc.beta[a][b] / dx[a]);
+        m.cE[a] = (T)(dt / dx[a]);
+    }
+    m.dt = (T)dt;
+    return m;
+}
+
+}  // namespace fdtd
+
+using namespace fdtd;
+
+#define CK(call)                                                                        \
+    do {                                                                                \
+        cudaError_t e_ = (call);                                                        \
+        if (e_ != cudaSuccess) {                                                        \
+            set_error("%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, \
+                      __LINE__);                                                        \
+            return e_ == cudaErrorMemoryAllocation ? FDTD_ENOMEM : FDTD_ECUDA;          \
+        }                                                                               \
+    } while (0)
+
+struct fdtd_handle {
+    fdtd_grid grid;
+    double dx[3];
+    double dt;
+    fdtd_coeffs coeffs;
+    Clean cc;
+    cudaStream_t stream;
+    Geom g;
+    size_t esz;
+    char* state;        // 2 sets x 6 padded arrays
+    int cur;
+    char* lam;          // 6 padded arrays
+    char* hist;         // history: snapshots x 3 padded arrays
+    int hist_cap;
+    int hist_len;       // snapshots stored
+    long long hist_step0;
+    std::vector<char*> ckpt;
+    std::vector<long long> ckpt_step;
+    char* aux;          // sponge_y[ny], sponge_z[nz], bunch_y[ny], bunch_z[nz] (T)
+    char* jx;           // bunch x-profile table [cap][nx]
+    int jx_cap;
+    double* partials;   // adjoint gradient partials
+    int npart;
+    char* staging;      // one dense array
+    long long step;
+    int use_fused;
+
+    void* arr(int set, int c) { return state + ((size_t)set * 6 + c) * g.total * esz; }
+    void* lam_arr(int c) { return lam + (size_t)c * g.total * esz; }
+    void* hist_arr(int snap, int c) { return hist + ((size_t)snap * 3 + c) * g.total * esz; }
+};
+
+template <typename T>
+static FieldSet<T> fieldset(fdtd_handle* h, int set) {
+    FieldSet<T> s;
+    for (int c = 0; c < 6; ++c) s.c[c] = (T*)h->arr(set, c);
+    return s;
+}
+
+template <typename T>
+static FieldSet<T> lamset(fdtd_handle* h) {
+    FieldSet<T> s;
+    for (int c = 0; c < 6; ++c) s.c[c] = (T*)h->lam_arr(c);
+    return s;
+}
+
+template <typename T>
+static int upload_aux(fdtd_handle* h) {
+    const int ny = h->g.ny, nz = h->g.nz;
+    std::vector<T> a(2 * (size_t)(ny + nz), (T)1);
+    const int L = h->grid.absorb_cells;
+    const double sg = h->grid.absorb_sigma;
+    auto prof = [&](int n, int idx) -> double {
+        if (L <= 0) return 1.0;
+        int d = 0;
+        if (idx < L) d = L - idx;
+        else if (idx >= n - L) d = idx - (n - L - 1);
+        if (d <= 0) return 1.0;
+        const double x = (double)d / L;
+        return 1.0 - sg * x * x * x;
+    };
+    for (int j = 0; j < ny; ++j) a[j] = (T)prof(ny, j);
+    for (int k = 0; k < nz; ++k) a[ny + k] = (T)prof(nz, k);
+    CK(cudaMemcpyAsync(h->aux, a.data(), a.size() / 2 * sizeof(T), cudaMemcpyHostToDevice,
+                       h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return FDTD_OK;
+}
+
+static double Phi(double x) { return 0.5 * erfc(-x / sqrt(2.0)); }
+
+template <typename T>
+static int upload_bunch_yz(fdtd_handle* h, const fdtd_source* src) {
+    const int ny = h->g.ny, nz = h->g.nz;
+    std::vector<T> a((size_t)(ny + nz));
+    const double Ly = ny * h->dx[1], Lz = nz * h->dx[2];
+    for (int j = 0; j < ny; ++j) {
+        double d = j * h->dx[1] - src->y0;
+        d = d - Ly * floor(d / Ly + 0.5);
+        a[j] = (T)(Phi((d + 0.5 * h->dx[1]) / src->sigma_perp) -
+                   Phi((d - 0.5 * h->dx[1]) / src->sigma_perp));
+    }
+    for (int k = 0; k < nz; ++k) {
+        double d = k * h->dx[2] - src->z0;
+        d = d - Lz * floor(d / Lz + 0.5);
+        a[ny + k] = (T)(Phi((d + 0.5 * h->dx[2]) / src->sigma_perp) -
+                        Phi((d - 0.5 * h->dx[2]) / src->sigma_perp));
+    }
+    T* dst = (T*)h->aux + (ny + nz);
+    CK(cudaMemcpyAsync(dst, a.data(), a.size() * sizeof(T), cudaMemcpyHostToDevice, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return FDTD_OK;
+}
+
+// Exported functions: C linkage comes from their declarations in fdtd.h.
+
+const char* fdtd_last_error(void) { return g_err; }
+
+int fdtd_dt_max(const fdtd_coeffs* coeffs, const double dx[3], int32_t dims, double* dt_max,
+                double* s_min, double* s_max) {
+    if (!coeffs || !dx || dims < 1 || dims > 3) {
+        set_error("fdtd_dt_max: bad argument");
+        return FDTD_EINVAL;
+    }
+    for (int i = 0; i < 3; ++i)
+        if (!(dx[i] > 0)) {
+            set_error("dx must be positive");
+            return FDTD_EINVAL;
+        }
+    Clean cc = clean_coeffs(coeffs, dims);
+    double lo, hi;
+    S_extremes(cc, dx, dims, &lo, &hi);
+    if (s_min) *s_min = lo;
+    if (s_max) *s_max = hi;
+    if (dt_max) *dt_max = hi > 0 ? 1.0 / sqrt(hi) : INFINITY;
+    return FDTD_OK;
+}
+
+int fdtd_create(const fdtd_grid* grid, const double dx[3], double dt, const fdtd_coeffs* coeffs,
+                void* stream, fdtd_handle** out) {
+    if (!grid || !dx || !coeffs || !out) {
+        set_error("fdtd_create: NULL argument");
+        return FDTD_EINVAL;
+    }
+    *out = nullptr;
+    const fdtd_grid& G = *grid;
+    if (G.dims < 1 || G.dims > 3) { set_error("dims must be 1, 2 or 3"); return FDTD_EINVAL; }
+    if (G.nx < 4 || G.nx % 4 != 0) { set_error("nx must be a positive multiple of 4"); return FDTD_EINVAL; }
+    if (G.ny < 1 || G.nz < 1) { set_error("ny, nz must be >= 1"); return FDTD_EINVAL; }
+    if (G.dims <= 2 && G.nz != 1) { set_error("dims < 3 needs nz == 1"); return FDTD_EINVAL; }
+    if (G.dims == 1 && G.ny != 1) { set_error("dims == 1 needs ny == 1"); return FDTD_EINVAL; }
+    if (G.dtype != FDTD_F32 && G.dtype != FDTD_F64) { set_error("bad dtype"); return FDTD_EINVAL; }
+    if (G.absorb_cells < 0 || 2 * G.absorb_cells > G.ny || (G.absorb_cells > 0 && 2 * G.absorb_cells > G.nz)) {
+        set_error("absorbing layers do not fit the grid");
+        return FDTD_EINVAL;
+    }
+    if (G.absorb_cells > 0 && !(G.absorb_sigma >= 0.0 && G.absorb_sigma < 1.0)) {
+        set_error("absorb_sigma must be in [0, 1)");
+        return FDTD_EINVAL;
+    }
+    for (int i = 0; i < 3; ++i)
+        if (!(dx[i] > 0) || !std::isfinite(dx[i])) { set_error("dx must be positive"); return FDTD_EINVAL; }
+    Clean cc = clean_coeffs(coeffs, G.dims);
+    int rc = validate(cc, dx, G.dims, dt);
+    if (rc) return rc;
+
+    fdtd_handle* h = new (std::nothrow) fdtd_handle();
+    if (!h) { set_error("host allocation failed"); return FDTD_ENOMEM; }
+    h->grid = G;
+    for (int i = 0; i < 3; ++i) h->dx[i] = dx[i];
+    h->dt = dt;
+    h->coeffs = *coeffs;
+    h->cc = cc;
+    h->stream = (cudaStream_t)stream;
+    h->g = make_geom(G.nx, G.ny, G.nz);
+    h->esz = G.dtype == FDTD_F32 ? 4 : 8;
+    h->cur = 0;
+    h->step = 0;
+    h->use_fused = 1;
+    const size_t arr = (size_t)h->g.total * h->esz;
+    cudaError_t e = cudaMalloc(&h->state, 12 * arr);
+    if (e == cudaSuccess) e = cudaMalloc(&h->aux, 2 * (size_t)(G.ny + G.nz) * h->esz);
+    if (e != cudaSuccess) {
+        set_error("cudaMalloc of %zu bytes failed: %s", 12 * arr, cudaGetErrorString(e));
+        fdtd_destroy(h);
+        return e == cudaErrorMemoryAllocation ? FDTD_ENOMEM : FDTD_ECUDA;
+    }
+    e = cudaMemsetAsync(h->state, 0, 12 * arr, h->stream);
+    if (e != cudaSuccess) {
+        set_error("cudaMemsetAsync failed: %s", cudaGetErrorString(e));
+        fdtd_destroy(h);
+        return FDTD_ECUDA;
+    }
+    rc = G.dtype == FDTD_F32 ? upload_aux<float>(h) : upload_aux<double>(h);
+    if (rc) { fdtd_destroy(h); return rc; }
+    *out = h;
+    return FDTD_OK;
+}
+
+int fdtd_set_coeffs(fdtd_handle* h, double dt, const fdtd_coeffs* coeffs) {
+    if (!h || !coeffs) { set_error("NULL argument"); return FDTD_EINVAL; }
+    Clean cc = clean_coeffs(coeffs, h->grid.dims);
+    int rc = validate(cc, h->dx, h->grid.dims, dt);
+    if (rc) return rc;
+    h->cc = cc;
+    h->coeffs = *coeffs;
+    h->dt = dt;
+    return FDTD_OK;
+}
+
+static int ensure_staging(fdtd_handle* h) {
+    if (h->staging) return FDTD_OK;
+    const size_t n = (size_t)h->g.nx * h->g.ny * h->g.nz * h->esz;
+    CK(cudaMalloc(&h->staging, n));
+    return FDTD_OK;
+}
+
+template <typename T>
+static int copy_in(fdtd_handle* h, void* const fields[6], int32_t mem, T* const dst[6]) {
+    const size_t n = (size_t)h->g.nx * h->g.ny * h->g.nz;
+    for (int c = 0; c < 6; ++c) {
+        const T* src = (const T*)(fields ? fields[c] : nullptr);
+        if (src && mem == FDTD_MEM_HOST) {
+            int rc = ensure_staging(h);
+            if (rc) return rc;
+            CK(cudaMemcpyAsync(h->staging, src, n * sizeof(T), cudaMemcpyHostToDevice, h->stream));
+            src = (const T*)h->staging;
+        }
+        launch_unpack<T>(h->g, src, dst[c], h->stream);
+        CK(cudaGetLastError());
+    }
+    if (mem == FDTD_MEM_HOST) CK(cudaStreamSynchronize(h->stream));
+    return FDTD_OK;
+}
+
+template <typename T>
+static int copy_out(fdtd_handle* h, void* const fields[6], int32_t mem, T* const srcs[6]) {
+    const size_t n = (size_t)h->g.nx * h->g.ny * h->g.nz;
+    for (int c = 0; c < 6; ++c) {
+        if (!fields[c]) continue;
+        if (mem == FDTD_MEM_HOST) {
+            int rc = ensure_staging(h);
+            if (rc) return rc;
+            launch_pack<T>(h->g, srcs[c], (T*)h->staging, h->stream);
+            CK(cudaGetLastError());
+            CK(cudaMemcpyAsync(fields[c], h->staging, n * sizeof(T), cudaMemcpyDeviceToHost, h->stream));
+        } else {
+            launch_pack<T>(h->g, srcs[c], (T*)fields[c], h->stream);
+            CK(cudaGetLastError());
+        }
+    }
+    if (mem == FDTD_MEM_HOST) CK(cudaStreamSynchronize(h->stream));
+    return FDTD_OK;
+}
+
+int fdtd_set_state(fdtd_handle* h, void* const fields[6], int32_t mem, int64_t step0) {
+    if (!h || (mem != FDTD_MEM_DEVICE && mem != FDTD_MEM_HOST)) {
+        set_error("fdtd_set_state: bad argument");
+        return FDTD_EINVAL;
+    }
+    h->cur = 0;
+    h->step = step0;
+    h->hist_len = 0;
+    if (h->grid.dtype == FDTD_F32) {
+        float* d[6];
+        for (int c = 0; c < 6; ++c) d[c] = (float*)h->arr(0, c);
+        return copy_in<float>(h, fields, mem, d);
+    }
+    double* d[6];
+    for (int c = 0; c < 6; ++c) d[c] = (double*)h->arr(0, c);
+    return copy_in<double>(h, fields, mem, d);
+}
+
+int fdtd_get_state(fdtd_handle* h, void* const fields[6], int32_t mem) {
+    if (!h || !fields || (mem != FDTD_MEM_DEVICE && mem != FDTD_MEM_HOST)) {
+        set_error("fdtd_get_state: bad argument");
+        return FDTD_EINVAL;
+    }
+    if (h->grid.dtype == FDTD_F32) {
+        float* s[6];
+        for (int c = 0; c < 6; ++c) s[c] = (float*)h->arr(h->cur, c);
+        return copy_out<float>(h, fields, mem, s);
+    }
+    double* s[6];
+    for (int c = 0; c < 6; ++c) s[c] = (double*)h->arr(h->cur, c);
+    return copy_out<double>(h, fields, mem, s);
+}
+
+int fdtd_get_step(fdtd_handle* h, int64_t* step) {
+    if (!h || !step) { set_error("NULL argument"); return FDTD_EINVAL; }
+    *step = h->step;
+    return FDTD_OK;
+}
+
+static int ensure_lam(fdtd_handle* h) {
+    if (h->lam) return FDTD_OK;
+    const size_t arr = (size_t)h->g.total * h->esz;
+    CK(cudaMalloc(&h->lam, 6 * arr));
+    CK(cudaMemsetAsync(h->lam, 0, 6 * arr, h->stream));
+    return FDTD_OK;
+}
+
+int fdtd_set_adjoint(fdtd_handle* h, void* const fields[6], int32_t mem) {
+    if (!h || (mem != FDTD_MEM_DEVICE && mem != FDTD_MEM_HOST)) {
+        set_error("fdtd_set_adjoint: bad argument");
+        return FDTD_EINVAL;
+    }
+    int rc = ensure_lam(h);
+    if (rc) return rc;
+    if (h->grid.dtype == FDTD_F32) {
+        float* d[6];
+        for (int c = 0; c < 6; ++c) d[c] = (float*)h->lam_arr(c);
+        return copy_in<float>(h, fields, mem, d);
+    }
+    double* d[6];
+    for (int c = 0; c < 6; ++c) d[c] = (double*)h->lam_arr(c);
+    return copy_in<double>(h, fields, mem, d);
+}
+
+int fdtd_get_adjoint(fdtd_handle* h, void* const fields[6], int32_t mem) {
+    if (!h || !fields || (mem != FDTD_MEM_DEVICE && mem != FDTD_MEM_HOST)) {
+        set_error("fdtd_get_adjoint: bad argument");
+        return FDTD_EINVAL;
+    }
+    int rc = ensure_lam(h);
+    if (rc) return rc;
+    if (h->grid.dtype == FDTD_F32) {
+        float* s[6];
+        for (int c = 0; c < 6; ++c) s[c] = (float*)h->lam_arr(c);
+        return copy_out<float>(h, fields, mem, s);
+    }
+    double* s[6];
+    for (int c = 0; c < 6; ++c) s[c] = (double*)h->lam_arr(c);
+    return copy_out<double>(h, fields, mem, s);
+}
+
+static int ensure_hist(fdtd_handle* h, int snaps) {
+    if (h->hist_cap >= snaps) return FDTD_OK;
+    if (h->hist) { cudaFree(h->hist); h->hist = nullptr; h->hist_cap = 0; }
+    const size_t arr = (size_t)h->g.total * h->esz;
+    CK(cudaMalloc(&h->hist, (size_t)snaps * 3 * arr));
+    h->hist_cap = snaps;
+    return FDTD_OK;
+}
+
+static int ensure_jx(fdtd_handle* h, int n) {
+    if (h->jx_cap >= n) return FDTD_OK;
+    if (h->jx) { cudaFree(h->jx); h->jx = nullptr; h->jx_cap = 0; }
+    CK(cudaMalloc(&h->jx, (size_t)n * h->g.nx * h->esz));
+    h->jx_cap = n;
+    return FDTD_OK;
+}
+
+template <typename T>
+static int snapshot(fdtd_handle* h, int snap) {
+    const size_t arr = (size_t)h->g.total * sizeof(T);
+    for (int c = 0; c < 3; ++c)
+        CK(cudaMemcpyAsync(h->hist_arr(snap, c), h->arr(h->cur, c), arr, cudaMemcpyDeviceToDevice,
+                           h->stream));
+    return FDTD_OK;
+}
+
+template <typename T>
+static int step_impl(fdtd_handle* h, int n, const fdtd_source* src, const fdtd_probe* probe,
+                     double* loss, int record) {
+    const Geom& g = h->g;
+    const Mult<T> m = make_mult<T>(h->cc, h->dx, h->dt);
+    const T* spy = nullptr;
+    const T* spz = nullptr;
+    if (h->grid.absorb_cells > 0) {
+        spy = (const T*)h->aux;
+        spz = spy + g.ny;
+    }
+    const bool bunch = src && src->kind == FDTD_SRC_BUNCH && n > 0;
+    const T* jyz = nullptr;
+    if (bunch) {
+        int rc = upload_bunch_yz<T>(h, src);
+        if (rc) return rc;
+        rc = ensure_jx(h, n);
+        if (rc) return rc;
+        jyz = (const T*)h->aux + (g.ny + g.nz);
+        launch_bunch_table<T>(g.nx, n, src->x0, src->v * h->dt, 1.0 / src->sigma_par,
+                              src->q / (h->dx[1] * h->dx[2] * h->dt), h->dx[0], g.nx * h->dx[0],
+                              h->step, (T*)h->jx, h->stream);
+        CK(cudaGetLastError());
+    }
+    if (record) {
+        int rc = ensure_hist(h, n + 1);
+        if (rc) return rc;
+        h->hist_len = n + 1;
+        h->hist_step0 = h->step;
+    }
+    const bool fused = h->use_fused && fused_supported<T>(g);
+    for (int s = 0; s < n; ++s) {
+        if (record && !fused) {
+            int rc = snapshot<T>(h, s);
+            if (rc) return rc;
+        }
+        const T* jrow = bunch ? (const T*)h->jx + (size_t)s * g.nx : nullptr;
+        if (fused) {
+            T* hE[3] = {nullptr, nullptr, nullptr};
+            if (record) {
+                if (s == 0) {
+                    int rc = snapshot<T>(h, 0);
+                    if (rc) return rc;
+                }
+                for (int c = 0; c < 3; ++c) hE[c] = (T*)h->hist_arr(s + 1, c);
+            }
+            launch_step_fused<T>(g, m, fieldset<T>(h, h->cur), fieldset<T>(h, 1 - h->cur), spy,
+                                 spz, jyz, jrow, hE, h->stream);
+            h->cur = 1 - h->cur;
+        } else {
+            FieldSet<T> fs = fieldset<T>(h, h->cur);
+            launch_faraday_v0<T>(g, m, fs, spy, spz, h->stream);
+            launch_ampere_v0<T>(g, m, fs, spy, spz, jyz, jrow, h->stream);
+        }
+        CK(cudaGetLastError());
+        h->step += 1;
+        if (probe) {
+            const T* tgt = (const T*)probe->target + (size_t)(h->step - 1) * g.ny * g.nz;
+            launch_probe_loss<T>(g, (const T*)h->arr(h->cur, probe->component), probe->x_index,
+                                 tgt, loss, h->stream);
+            CK(cudaGetLastError());
+        }
+    }
+    if (record && !fused) {
+        int rc = snapshot<T>(h, n);
+        if (rc) return rc;
+    }
+    if (record && fused && n == 0) {
+        int rc = snapshot<T>(h, 0);
+        if (rc) return rc;
+    }
+    return FDTD_OK;
+}
+
+int fdtd_step(fdtd_handle* h, int32_t n, const fdtd_source* src, const fdtd_probe* probe,
+              double* loss_dev, int32_t record) {
+    if (!h || n < 0) { set_error("fdtd_step: bad argument"); return FDTD_EINVAL; }
+    if (src && src->kind != FDTD_SRC_NONE && src->kind != FDTD_SRC_BUNCH) {
+        set_error("unknown source kind %d", src->kind);
+        return FDTD_EINVAL;
+    }
+    if (src && src->kind == FDTD_SRC_BUNCH && !(src->sigma_par > 0 && src->sigma_perp > 0)) {
+        set_error("bunch widths must be positive");
+        return FDTD_EINVAL;
+    }
+    if (probe) {
+        if (probe->component < 0 || probe->component > 2 || probe->x_index < 0 ||
+            probe->x_index >= h->g.nx || !probe->target || !loss_dev) {
+            set_error("bad probe");
+            return FDTD_EINVAL;
+        }
+        if (h->step + n > probe->target_steps) {
+            set_error("probe target holds %lld steps, run needs %lld",
+                      (long long)probe->target_steps, (long long)(h->step + n));
+            return FDTD_EINVAL;
+        }
+    }
+    if (h->grid.dtype == FDTD_F32) return step_impl<float>(h, n, src, probe, loss_dev, record);
+    return step_impl<double>(h, n, src, probe, loss_dev, record);
+}
+
+int fdtd_checkpoint(fdtd_handle* h, int32_t slot, int32_t op) {
+    if (!h || slot < 0 || (op != 0 && op != 1)) { set_error("fdtd_checkpoint: bad argument"); return FDTD_EINVAL; }
+    const size_t arr = (size_t)h->g.total * h->esz;
+    if ((size_t)slot >= h->ckpt.size()) {
+        if (op == 1) { set_error("checkpoint slot %d is empty", slot); return FDTD_ESTATE; }
+        h->ckpt.resize(slot + 1, nullptr);
+        h->ckpt_step.resize(slot + 1, -1);
+    }
+    if (op == 0) {
+        if (!h->ckpt[slot]) CK(cudaMalloc(&h->ckpt[slot], 6 * arr));
+        for (int c = 0; c < 6; ++c)
+            CK(cudaMemcpyAsync(h->ckpt[slot] + c * arr, h->arr(h->cur, c), arr,
+                               cudaMemcpyDeviceToDevice, h->stream));
+        h->ckpt_step[slot] = h->step;
+    } else {
+        if (!h->ckpt[slot]) { set_error("checkpoint slot %d is empty", slot); return FDTD_ESTATE; }
+        for (int c = 0; c < 6; ++c)
+            CK(cudaMemcpyAsync(h->arr(h->cur, c), h->ckpt[slot] + c * arr, arr,
+                               cudaMemcpyDeviceToDevice, h->stream));
+        h->step = h->ckpt_step[slot];
+        h->hist_len = 0;
+    }
+    return FDTD_OK;
+}
+
+template <typename T>
+static int adjoint_impl(fdtd_handle* h, int n, const fdtd_probe* probe, double* grad) {
+    const Geom& g = h->g;
+    const Mult<T> m = make_mult<T>(h->cc, h->dx, h->dt);
+    const T* spy = nullptr;
+    const T* spz = nullptr;
+    if (h->grid.absorb_cells > 0) {
+        spy = (const T*)h->aux;
+        spz = spy + g.ny;
+    }
+    int rc = ensure_lam(h);
+    if (rc) return rc;
+    const int nblk = adjoint_B_blocks(g);
+    if (h->npart < nblk) {
+        if (h->partials) cudaFree(h->partials);
+        h->partials = nullptr;
+        CK(cudaMalloc(&h->partials, (size_t)nblk * 9 * sizeof(double)));
+        h->npart = nblk;
+    }
+    CK(cudaMemsetAsync(h->partials, 0, (size_t)nblk * 9 * sizeof(double), h->stream));
+    FieldSet<T> lam = lamset<T>(h);
+    const int top = h->hist_len - 1;   // newest snapshot index
+    for (int r = 0; r < n; ++r) {
+        const int snap_after = top - r;        // E^{s+1}
+        const int snap_before = top - r - 1;   // E^{s}
+        const long long s_after = h->hist_step0 + snap_after;
+        if (probe) {
+            const T* tgt = (const T*)probe->target + (size_t)(s_after - 1) * g.ny * g.nz;
+            launch_probe_adjoint<T>(g, lam.c[probe->component],
+                                    (const T*)h->hist_arr(snap_after, probe->component),
+                                    probe->x_index, tgt, h->stream);
+        }
+        const T* E[3] = {(const T*)h->hist_arr(snap_before, 0), (const T*)h->hist_arr(snap_before, 1),
+                         (const T*)h->hist_arr(snap_before, 2)};
+        launch_adjoint_B_v0<T>(g, m, lam, E, spy, spz, h->partials, nblk, h->stream);
+        launch_adjoint_E_v0<T>(g, m, lam, spy, spz, h->stream);
+        CK(cudaGetLastError());
+    }
+    launch_reduce_grad(h->partials, nblk, h->dt / h->dx[0], h->dt / h->dx[1], h->dt / h->dx[2],
+                       grad, h->stream);
+    CK(cudaGetLastError());
+    h->hist_len -= n;
+    return FDTD_OK;
+}
+
+int fdtd_step_adjoint(fdtd_handle* h, int32_t n, const fdtd_probe* probe, double* grad_dev) {
+    if (!h || n < 0 || !grad_dev) { set_error("fdtd_step_adjoint: bad argument"); return FDTD_EINVAL; }
+    if (h->hist_len < n + 1) {
+        set_error("history holds %d snapshots, %d reverse steps need %d", h->hist_len, n, n + 1);
+        return FDTD_ESTATE;
+    }
+    if (probe) {
+        if (probe->component < 0 || probe->component > 2 || probe->x_index < 0 ||
+            probe->x_index >= h->g.nx || !probe->target) {
+            set_error("bad probe");
+            return FDTD_EINVAL;
+        }
+        if (h->hist_step0 + h->hist_len - 1 > probe->target_steps) {
+            set_error("probe target too short");
+            return FDTD_EINVAL;
+        }
+    }
+    if (h->grid.dtype == FDTD_F32) return adjoint_impl<float>(h, n, probe, grad_dev);
+    return adjoint_impl<double>(h, n, probe, grad_dev);
+}
+
+int fdtd_sync(fdtd_handle* h) {
+    if (!h) { set_error("NULL handle"); return FDTD_EINVAL; }
+    CK(cudaStreamSynchronize(h->stream));
+    CK(cudaGetLastError());
+    return FDTD_OK;
+}
+
+void fdtd_destroy(fdtd_handle* h) {
+    if (!h) return;
+    cudaStreamSynchronize(h->stream);
+    if (h->state) cudaFree(h->state);
+    if (h->lam) cudaFree(h->lam);
+    if (h->hist) cudaFree(h->hist);
+    if (h->aux) cudaFree(h->aux);
+    if (h->jx) cudaFree(h->jx);
+    if (h->partials) cudaFree(h->partials);
+    if (h->staging) cudaFree(h->staging);
+    for (char* p : h->ckpt)
+        if (p) cudaFree(p);
+    delete h;
+}
+
+int disp_norm_eval(const fdtd_coeffs* coeffs, double dt, const double dx[3], int32_t dims,
+                   const int32_t N[3], int32_t weight, double weight_param, double* out,
+                   void* stream) {
+    if (!coeffs || !dx || !N || !out || dims < 1 || dims > 3) {
+        set_error("disp_norm_eval: bad argument");
+        return FDTD_EINVAL;
+    }
+    for (int i = 0; i < dims; ++i)
+        if (N[i] < 1 || !(dx[i] > 0)) { set_error("disp_norm_eval: bad grid"); return FDTD_EINVAL; }
+    if (weight != FDTD_W_UNIFORM && weight != FDTD_W_CONE_X && weight != FDTD_W_GAUSS_Y) {
+        set_error("unknown weight %d", weight);
+        return FDTD_EINVAL;
+    }
+    if (weight == FDTD_W_GAUSS_Y && !(weight_param > 0)) { set_error("gauss width must be > 0"); return FDTD_EINVAL; }
+    Clean cc = clean_coeffs(coeffs, dims);
+    int rc = validate(cc, dx, dims, dt);
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    int Nd[3];
+    long long npts = 1;
+    for (int i = 0; i < 3; ++i) {
+        Nd[i] = i < dims ? N[i] : 1;
+        npts *= Nd[i];
+    }
+    const size_t nscr = norm_scratch_doubles(Nd, npts);
+    double* scratch = nullptr;
+    CK(cudaMallocAsync((void**)&scratch, nscr * sizeof(double), st));
+    double* res = nullptr;
+    launch_disp_norm(cc.alpha, cc.beta, cc.delta, dt, dx, dims, Nd, weight, weight_param, scratch,
+                     &res, st);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, res, 14 * sizeof(double), cudaMemcpyDeviceToHost, st);
+    cudaFreeAsync(scratch, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        set_error("disp_norm_eval: %s", cudaGetErrorString(e));
+        return FDTD_ECUDA;
+    }
+    return FDTD_OK;
+}
+

@@ -1,0 +1,105 @@
+// Internal declarations shared by the libfdtd translation units.
+//
+// State layout in HBM.  Every field array is stored padded in x and y and
+// unpadded in z:
+//     element (i, j, k), 0 <= i < nx, 0 <= j < ny, 0 <= k < nz, lives at
+//     base[(k * nyp + (j + PY)) * nxp + (i + PX)],  nxp = nx + 2 PX, nyp = ny + 2 PY.
+// The PX x-columns and PY y-rows on each side hold periodic images of the
+// owned cells (ghosts).  Every kernel that writes an owned cell also writes
+// its images, so a tile load never wraps in x or y; z neighbours wrap by
+// plane index.  PX = 4 keeps every x-row 16-byte aligned (TMA boxes start on
+// a 16-byte boundary) and covers the widest x reach of the step
+// (E at i-2 .. i+2 and B at i-1); PY = 2 covers y reaches -2 .. +2.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/fdtd.h"
+
+namespace fdtd {
+
+constexpr int PX = 4;
+constexpr int PY = 2;
+
+struct Geom {
+    int nx, ny, nz;
+    int nxp, nyp;
+    long long plane;   // nxp * nyp elements
+    long long total;   // plane * nz elements (one padded array)
+};
+
+inline Geom make_geom(int nx, int ny, int nz) {
+    Geom g;
+    g.nx = nx; g.ny = ny; g.nz = nz;
+    g.nxp = nx + 2 * PX;
+    g.nyp = ny + 2 * PY;
+    g.plane = (long long)g.nxp * g.nyp;
+    g.total = g.plane * nz;
+    return g;
+}
+
+__host__ __device__ inline long long pidx(const Geom& g, int i, int j, int k) {
+    return ((long long)k * g.nyp + (j + PY)) * g.nxp + (i + PX);
+}
+
+// Update multipliers, computed in FP64 on the host and rounded once to T:
+//   cA[a] = dt alpha_a / dx_a, cD[a] = dt delta_a / dx_a, cB[a][b] = dt beta_ab / dx_a,
+//   cE[a] = dt / dx_a (c^2 dt / dx_a with c = 1).
+template <typename T>
+struct Mult {
+    T cA[3], cD[3], cB[3][3], cE[3];
+    T dt;
+};
+
+template <typename T>
+struct FieldSet {
+    T* c[6];   // Ex, Ey, Ez, Bx, By, Bz (padded)
+};
+
+// ---- kernels launched from the host translation unit ----------------------
+
+template <typename T>
+void launch_faraday_v0(const Geom& g, const Mult<T>& m, FieldSet<T> s, const T* sponge_y,
+                       const T* sponge_z, cudaStream_t st);
+template <typename T>
+void launch_ampere_v0(const Geom& g, const Mult<T>& m, FieldSet<T> s, const T* sponge_y,
+                      const T* sponge_z, const T* jyz, const T* jx_row, cudaStream_t st);
+
+// Fused leapfrog step: reads (E^n, B^{n-1/2}) from `in`, writes (E^{n+1}, B^{n+1/2})
+// to `out` (both padded, images included).  hist_E (nullable) receives E^{n+1}.
+template <typename T>
+void launch_step_fused(const Geom& g, const Mult<T>& m, FieldSet<T> in, FieldSet<T> out,
+                       const T* sponge_y, const T* sponge_z, const T* jyz, const T* jx_row,
+                       T* hist_E[3], cudaStream_t st);
+template <typename T>
+bool fused_supported(const Geom& g);
+
+template <typename T>
+void launch_adjoint_B_v0(const Geom& g, const Mult<T>& m, FieldSet<T> lam, const T* E_hist[3],
+                         const T* sponge_y, const T* sponge_z, double* partials, int nblk,
+                         cudaStream_t st);
+template <typename T>
+void launch_adjoint_E_v0(const Geom& g, const Mult<T>& m, FieldSet<T> lam, const T* sponge_y,
+                         const T* sponge_z, cudaStream_t st);
+int adjoint_B_blocks(const Geom& g);
+
+template <typename T>
+void launch_probe_loss(const Geom& g, const T* E, int x_index, const T* target, double* loss,
+                       cudaStream_t st);
+template <typename T>
+void launch_probe_adjoint(const Geom& g, T* lamE, const T* E, int x_index, const T* target,
+                          cudaStream_t st);
+template <typename T>
+void launch_pack(const Geom& g, const T* padded, T* dense, cudaStream_t st);
+template <typename T>
+void launch_unpack(const Geom& g, const T* dense, T* padded, cudaStream_t st);
+
+// grad12[beta 3x3 row-major, delta 3] += (dt/dx_a) * sum over blocks of the partials.
+void launch_reduce_grad(const double* part, int nblocks, double s0, double s1, double s2,
+                        double* grad12, cudaStream_t st);
+
+// thread-local error message
+void set_error(const char* fmt, ...);
+
+}  // namespace fdtd

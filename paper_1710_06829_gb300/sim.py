@@ -1,0 +1,161 @@
+"""Thin Python objects over the C ABI; torch provides device memory and streams only.
+
+All arithmetic of the method runs in libfdtd's CUDA kernels; this module
+allocates tensors, passes their pointers and reads results back.
+"""
+from __future__ import annotations
+
+import torch
+
+from . import _lib as L
+
+_DT = {"f32": (L.FDTD_F32, torch.float32), "f64": (L.FDTD_F64, torch.float64)}
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream
+
+
+def coeffs_struct(beta, delta):
+    return L.make_coeffs(beta, delta)
+
+
+def dt_max(beta, delta, dx, dims):
+    """Exact CFL limit of Eq. (constraints) and the extremes of S (host FP64 in libfdtd)."""
+    return L.fdtd_dt_max(coeffs_struct(beta, delta), dx, dims)
+
+
+class Bunch:
+    """Rigid Gaussian bunch source (see fdtd_source in include/fdtd.h)."""
+
+    def __init__(self, q, v, x0, y0, z0, sigma_par, sigma_perp):
+        self.s = L.fdtd_source(L.FDTD_SRC_BUNCH, q, v, x0, y0, z0, sigma_par, sigma_perp)
+
+
+class Probe:
+    """Probe-plane misfit of E_component at x = x_index against target[(steps), nz, ny]."""
+
+    def __init__(self, component, x_index, target: torch.Tensor):
+        assert target.is_cuda and target.is_contiguous() and target.dim() == 3
+        self.target = target
+        self.s = L.fdtd_probe(int(component), int(x_index), target.data_ptr(), target.shape[0])
+
+
+class Simulation:
+    """One FDTD state (E, B) on a periodic nx x ny x nz grid, owned by libfdtd."""
+
+    def __init__(self, shape, dx, dt, beta, delta, dims=3, dtype="f32", absorb_cells=0,
+                 absorb_sigma=0.0, stream=None):
+        nx, ny, nz = shape
+        self.shape = (nz, ny, nx)
+        self.dims = dims
+        self.code, self.tdtype = _DT[dtype]
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        g = L.fdtd_grid(dims, nx, ny, nz, self.code, absorb_cells, absorb_sigma)
+        self.h = L.fdtd_create(g, dx, dt, coeffs_struct(beta, delta), _stream_ptr(self.stream))
+        self.dx = tuple(dx)
+        self.dt = dt
+
+    def close(self):
+        if self.h is not None:
+            L.fdtd_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- state ---------------------------------------------------------------
+    def _empty6(self):
+        return [torch.empty(self.shape, dtype=self.tdtype, device="cuda") for _ in range(6)]
+
+    def set_state(self, fields, step0=0):
+        """fields: six tensors (E_x, E_y, E_z, B_x, B_y, B_z) of shape (nz, ny, nx); None = 0."""
+        keep, ptrs, mem = [], [], L.FDTD_MEM_DEVICE
+        for f in fields:
+            if f is None:
+                ptrs.append(None)
+                continue
+            t = torch.as_tensor(f).to(device="cuda", dtype=self.tdtype).contiguous()
+            keep.append(t)
+            ptrs.append(t.data_ptr())
+        L.fdtd_set_state(self.h, ptrs, mem, step0)
+        self.stream.synchronize()
+
+    def set_state_host(self, fields, step0=0):
+        """Host (CPU tensor) variant: the copy to the device happens inside libfdtd."""
+        ptrs = [None if f is None else f.data_ptr() for f in fields]
+        L.fdtd_set_state(self.h, ptrs, L.FDTD_MEM_HOST, step0)
+
+    def get_state(self):
+        out = self._empty6()
+        L.fdtd_get_state(self.h, [t.data_ptr() for t in out], L.FDTD_MEM_DEVICE)
+        self.stream.synchronize()
+        return out
+
+    def get_state_host(self, out):
+        L.fdtd_get_state(self.h, [t.data_ptr() for t in out], L.FDTD_MEM_HOST)
+        return out
+
+    @property
+    def step_index(self):
+        return L.fdtd_get_step(self.h)
+
+    def set_coeffs(self, dt, beta, delta):
+        L.fdtd_set_coeffs(self.h, dt, coeffs_struct(beta, delta))
+        self.dt = dt
+
+    # -- stepping ------------------------------------------------------------
+    def step(self, n, source: Bunch | None = None, probe: Probe | None = None, loss=None,
+             record=False):
+        L.fdtd_step(self.h, n, source.s if source is not None else None,
+                    probe.s if probe is not None else None,
+                    loss.data_ptr() if loss is not None else None, 1 if record else 0)
+
+    def checkpoint_save(self, slot):
+        L.fdtd_checkpoint(self.h, slot, 0)
+
+    def checkpoint_restore(self, slot):
+        L.fdtd_checkpoint(self.h, slot, 1)
+
+    # -- adjoint -------------------------------------------------------------
+    def set_adjoint(self, fields=None):
+        keep, ptrs = [], []
+        for f in (fields if fields is not None else [None] * 6):
+            if f is None:
+                ptrs.append(None)
+                continue
+            t = torch.as_tensor(f).to(device="cuda", dtype=self.tdtype).contiguous()
+            keep.append(t)
+            ptrs.append(t.data_ptr())
+        L.fdtd_set_adjoint(self.h, ptrs, L.FDTD_MEM_DEVICE)
+        self.stream.synchronize()
+
+    def get_adjoint(self):
+        out = self._empty6()
+        L.fdtd_get_adjoint(self.h, [t.data_ptr() for t in out], L.FDTD_MEM_DEVICE)
+        self.stream.synchronize()
+        return out
+
+    def step_adjoint(self, n, grad: torch.Tensor, probe: Probe | None = None):
+        """grad: float64 CUDA tensor of 12 entries (beta 3x3 row-major, delta 3), accumulated."""
+        assert grad.is_cuda and grad.dtype == torch.float64 and grad.numel() >= 12
+        L.fdtd_step_adjoint(self.h, n, probe.s if probe is not None else None, grad.data_ptr())
+
+    def sync(self):
+        L.fdtd_sync(self.h)
+
+
+def disp_norm(beta, delta, dt, dx, dims, N, weight=L.FDTD_W_UNIFORM, weight_param=0.0,
+              stream=None):
+    """Eq. (norm) and its gradient on the GPU.
+
+    Returns (f, g_beta 3x3 (list of lists), g_delta (3), g_dt)."""
+    out = L.disp_norm_eval(coeffs_struct(beta, delta), dt, dx, dims, N, weight, weight_param,
+                           _stream_ptr(stream))
+    gb = [out[1:4], out[4:7], out[7:10]]
+    return out[0], gb, out[10:13], out[13]

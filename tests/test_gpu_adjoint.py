@@ -1,0 +1,146 @@
+"""GPU adjoint step and coefficient gradient against the oracle adjoint and finite differences."""
+import math
+
+import numpy as np
+import pytest
+
+from gpu_util import admissible_theta, exact_coeffs, rel_l2, rounded_coeffs
+from oracle import dispersion as D
+from oracle import fdtd as F
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+from paper_1710_06829_gb300 import inputs  # noqa: E402
+from paper_1710_06829_gb300 import sim as S  # noqa: E402
+from paper_1710_06829_gb300.autograd import FdtdProbeLoss, ProbeLossProblem, tied_coefficients  # noqa: E402
+
+
+def oracle_adjoint(coeffs, fields, lam_fields, n, sponge=None, probe=None):
+    """Oracle reverse sweep: returns (lambda after n reverse steps, grad beta 3x3, grad delta 3).
+    probe = (component, x_index, target[n, nz, ny])."""
+    states = [F.State(fields[:3], fields[3:])]
+    for _ in range(n):
+        states.append(F.step(states[-1].copy(), coeffs, None, sponge))
+    lam = F.State(lam_fields[:3], lam_fields[3:])
+    g = {}
+    for m in range(n - 1, -1, -1):
+        if probe is not None:
+            comp, xp, tgt = probe
+            E = states[m + 1].E[comp]
+            lam.E[comp][:, :, xp] += 2.0 * (E[:, :, xp] - tgt[m])
+        F.adjoint_step(lam, states[m].E, coeffs, g, sponge)
+    gb, gd = F.grad_to_arrays(g)
+    return lam.E + lam.B, gb, gd
+
+
+def gpu_adjoint(shape, dx, dt, beta, delta, dtype, fields, lam_fields, n, probe=None, **kw):
+    sm = S.Simulation(shape, dx, dt, beta, delta, dims=3, dtype=dtype, **kw)
+    sm.set_state([torch.from_numpy(f) for f in fields])
+    pr = None
+    if probe is not None:
+        comp, xp, tgt = probe
+        tt = torch.from_numpy(tgt).to("cuda", dtype=sm.tdtype).contiguous()
+        pr = S.Probe(comp, xp, tt)
+    sm.step(n, record=True)
+    sm.set_adjoint([torch.from_numpy(f) for f in lam_fields])
+    grad = torch.zeros(12, dtype=torch.float64, device="cuda")
+    sm.step_adjoint(n, grad, probe=pr)
+    lam = [t.double().cpu().numpy() for t in sm.get_adjoint()]
+    g = grad.cpu().numpy()
+    sm.close()
+    return lam, g[:9].reshape(3, 3), g[9:]
+
+
+@pytest.mark.parametrize("shape,sponge", [((16, 12, 10), False), ((20, 24, 24), True), ((4, 3, 2), False)])
+def test_adjoint_fp64_matches_oracle(shape, sponge):
+    beta, delta = admissible_theta(6)
+    dx = [1.0, 1.1, 0.9]
+    dt = 0.9 * D.dt_max(beta, delta, dx, 3)
+    fields = inputs.random_fields(shape, 11)
+    lam0 = inputs.random_fields(shape, 12)
+    n = 6
+    kw = dict(absorb_cells=5, absorb_sigma=0.3) if sponge else {}
+    nx, ny, nz = shape
+    sp = F.sponge_factor((nz, ny, nx), 5, 0.3) if sponge else None
+    rng = np.random.default_rng(0)
+    probe = (2, 3, rng.standard_normal((n, nz, ny)))
+    lam, gb, gd = gpu_adjoint(shape, dx, dt, beta, delta, "f64", fields, lam0, n, probe, **kw)
+    rlam, rgb, rgd = oracle_adjoint(exact_coeffs(beta, delta, dx, dt, 3), fields, lam0, n, sp, probe)
+    assert rel_l2(lam, rlam) <= 1e-12
+    scale = max(np.abs(rgb).max(), np.abs(rgd).max())
+    assert np.max(np.abs(gb - rgb)) <= 1e-11 * scale
+    assert np.max(np.abs(gd - rgd)) <= 1e-11 * scale
+
+
+def test_adjoint_fp32_vs_fp64_finite_differences():
+    """FP32 fields, FP64 gradient reduction vs central differences (h = 1e-4) of the FP64 oracle."""
+    shape = (24, 16, 16)
+    beta, delta = admissible_theta(8)
+    dx = [1.0, 1.0, 1.0]
+    dt = 0.9 * D.dt_max(beta, delta, dx, 3)
+    fields = inputs.random_fields(shape, 21)
+    n = 10
+    nx, ny, nz = shape
+    tgt = np.zeros((n, nz, ny))
+    probe = (2, 5, tgt)
+    lam0 = [np.zeros((nz, ny, nx))] * 6
+    lam, gb, gd = gpu_adjoint(shape, dx, dt, beta, delta, "f32",
+                              [f.astype(np.float32) for f in fields], lam0, n, probe)
+
+    def loss(b, d):
+        s = F.State(fields[:3], fields[3:])
+        c = exact_coeffs(b, d, dx, dt, 3)
+        tot = 0.0
+        for m in range(n):
+            F.step(s, c)
+            tot += float(np.sum((s.E[2][:, :, 5] - tgt[m]) ** 2))
+        return tot
+    h = 1e-4
+    for (i, j) in [(0, 1), (1, 2), (2, 0)]:
+        bp, bm = beta.copy(), beta.copy()
+        bp[i, j] += h
+        bm[i, j] -= h
+        fd = (loss(bp, delta) - loss(bm, delta)) / (2 * h)
+        assert gb[i, j] == pytest.approx(fd, rel=1e-4)
+    for i in range(3):
+        dp, dm = delta.copy(), delta.copy()
+        dp[i] += h
+        dm[i] -= h
+        fd = (loss(beta, dp) - loss(beta, dm)) / (2 * h)
+        assert gd[i] == pytest.approx(fd, rel=1e-4)
+
+
+def test_autograd_checkpointed_matches_oracle():
+    """Config-4 shape at small size: probe loss, checkpoint every 5 of 20 steps, tied theta."""
+    shape = (32, 16, 16)
+    nx, ny, nz = shape
+    dx = [1.0, 1.0, 1.0]
+    theta0 = torch.tensor([-0.05, -0.04, 0.02, 0.01], dtype=torch.float64)
+    b0, d0 = inputs.isotropic_theta(*theta0.tolist())
+    dt = 0.95 * D.dt_max(b0, d0, dx, 3)
+    Ez = inputs.pulse_ez_3d(shape, dx, 10.0, 3.0, 5.0, 8.0)
+    z = np.zeros_like(Ez)
+    init = [torch.from_numpy(a) for a in (z, z, Ez, z, z, z)]
+    n, every, xp = 20, 5, 20
+    rng = np.random.default_rng(3)
+    tgt = rng.standard_normal((n, nz, ny)) * 0.01
+    prob = ProbeLossProblem(shape, dx, dt, init, 2, xp, torch.from_numpy(tgt).cuda(), n, every,
+                            dtype="f64")
+    theta = theta0.clone().requires_grad_(True)
+    beta, delta = tied_coefficients(theta)
+    loss = FdtdProbeLoss.apply(beta, delta, prob)
+    loss.backward()
+    # oracle: loss and gradient of the same problem
+    c = exact_coeffs(b0, d0, dx, dt, 3)
+    fields = [a.numpy() for a in init]
+    _, rgb, rgd = oracle_adjoint(c, fields, [np.zeros_like(Ez)] * 6, n, None, (2, xp, tgt))
+    g_ref = np.array([rgd[0], rgd[1] + rgd[2], rgb[0, 1] + rgb[0, 2] + rgb[1, 0] + rgb[2, 0],
+                      rgb[1, 2] + rgb[2, 1]])
+    s = F.State(fields[:3], fields[3:])
+    ref_loss = 0.0
+    for m in range(n):
+        F.step(s, c)
+        ref_loss += float(np.sum((s.E[2][:, :, xp] - tgt[m]) ** 2))
+    assert float(loss) == pytest.approx(ref_loss, rel=1e-12)
+    assert np.allclose(theta.grad.numpy(), g_ref, rtol=1e-10, atol=1e-12 * np.abs(g_ref).max())

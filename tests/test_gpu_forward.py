@@ -1,0 +1,200 @@
+"""Forward stepping on the GPU (libfdtd through the C ABI) against the FP64 oracle."""
+import math
+
+import numpy as np
+import pytest
+
+from gpu_util import admissible_theta, exact_coeffs, rel_l2, rounded_coeffs
+from oracle import dispersion as D
+from oracle import fdtd as F
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_1710_06829_gb300 import inputs  # noqa: E402
+from paper_1710_06829_gb300 import sim as S  # noqa: E402
+from paper_1710_06829_gb300._lib import FdtdError  # noqa: E402
+
+NP = {"f32": np.float32, "f64": np.float64}
+
+
+def run_gpu(shape, dx, dt, beta, delta, dims, dtype, fields, n, **kw):
+    sm = S.Simulation(shape, dx, dt, beta, delta, dims=dims, dtype=dtype, **kw)
+    sm.set_state([torch.from_numpy(np.ascontiguousarray(f)) for f in fields])
+    sm.step(n)
+    out = [t.double().cpu().numpy() for t in sm.get_state()]
+    sm.close()
+    return out
+
+
+def run_oracle(coeffs, fields, n, sponge=None, bunch=None):
+    s = F.State(fields[:3], fields[3:])
+    F.run(s, coeffs, n, bunch=bunch, sponge=sponge)
+    return s.E + s.B
+
+
+# ---------------------------------------------------------------- 2D TE, FP64 (128^2, 200 steps)
+
+@pytest.mark.parametrize("scheme", ["yee", "min3"])
+def test_te_2d_fp64_matches_oracle(scheme):
+    beta = np.zeros((3, 3))
+    delta = np.zeros(3)
+    if scheme == "min3":
+        beta[0, 1] = beta[1, 0] = -0.065
+        delta[:2] = -0.065
+    dx, dt, shape = [1.0, 1.0, 1.0], 0.5, (128, 128, 1)
+    fields = inputs.te_pulse((128, 128), dx, (64.0, 64.0), 8.0, 16.0, dt, seed=0)
+    got = run_gpu(shape, dx, dt, beta, delta, 2, "f64", fields, 200)
+    ref = run_oracle(exact_coeffs(beta, delta, dx, dt, 2), fields, 200)
+    assert rel_l2(got, ref) <= 1e-12
+
+
+# ---------------------------------------------------------------- 3D, several tiles + ragged
+
+@pytest.mark.parametrize("shape", [(32, 24, 20), (36, 13, 7), (68, 34, 9), (4, 3, 2)])
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+def test_3d_random_fields_match_oracle(shape, dtype):
+    beta, delta = admissible_theta(1)
+    dx = [1.0, 0.9, 1.1]
+    dt = 0.95 * D.dt_max(beta, delta, dx, 3)
+    fields = inputs.random_fields(shape, seed=3)
+    n = 40
+    got = run_gpu(shape, dx, dt, beta, delta, 3, dtype, fields, n)
+    if dtype == "f64":
+        ref = run_oracle(exact_coeffs(beta, delta, dx, dt, 3), fields, n)
+        assert rel_l2(got, ref) <= 1e-12
+    else:
+        fields32 = [f.astype(np.float32).astype(np.float64) for f in fields]
+        ref = run_oracle(rounded_coeffs(beta, delta, dx, dt, 3, np.float32), fields32, n)
+        assert rel_l2(got, ref) <= 2e-6
+
+
+def test_1d_yee_courant_one_exact_on_gpu():
+    nx = 64
+    i = np.arange(nx)
+    g = lambda idx: np.exp(-(((idx - 20 + nx / 2) % nx - nx / 2) / 4.0) ** 2)  # noqa: E731
+    z = np.zeros((1, 1, nx))
+    fields = [z, g(i)[None, None, :], z, z, z, g(i + 1)[None, None, :]]
+    got = run_gpu((nx, 1, 1), [1, 1, 1], 1.0, np.zeros((3, 3)), np.zeros(3), 1, "f64", fields, 1000)
+    assert np.max(np.abs(got[1] - g(i - 1000)[None, None, :])) < 1e-12
+
+
+def test_sponge_and_bunch_match_oracle():
+    shape = (32, 40, 40)
+    dx = [1.0, 1.0, 1.0]
+    beta, delta = admissible_theta(2)
+    dt = 0.95 * D.dt_max(beta, delta, dx, 3)
+    fields = inputs.random_fields(shape, seed=5, scale=0.1)
+    bunch = (1.0, 0.999, 8.0, 20.0, 20.0, 2.0, 3.0)
+    for dtype in ("f64", "f32"):
+        sm = S.Simulation(shape, dx, dt, beta, delta, dims=3, dtype=dtype, absorb_cells=8,
+                          absorb_sigma=0.2)
+        sm.set_state([torch.from_numpy(f) for f in fields])
+        sm.step(25, source=S.Bunch(*bunch))
+        got = [t.double().cpu().numpy() for t in sm.get_state()]
+        sm.close()
+        sp = F.sponge_factor((40, 40, 32), 8, 0.2)
+        if dtype == "f64":
+            ref = run_oracle(exact_coeffs(beta, delta, dx, dt, 3), fields, 25, sponge=sp,
+                             bunch=F.Bunch(*bunch))
+            assert rel_l2(got, ref) <= 1e-12
+        else:
+            f32 = [f.astype(np.float32).astype(np.float64) for f in fields]
+            ref = run_oracle(rounded_coeffs(beta, delta, dx, dt, 3, np.float32), f32, 25,
+                             sponge=sp.astype(np.float32).astype(np.float64), bunch=F.Bunch(*bunch))
+            assert rel_l2(got, ref) <= 2e-6
+
+
+def test_host_buffers_roundtrip():
+    shape = (16, 8, 4)
+    beta, delta = admissible_theta(3)
+    dt = 0.9 * D.dt_max(beta, delta, [1, 1, 1], 3)
+    fields = [torch.from_numpy(f.astype(np.float32)) for f in inputs.random_fields(shape, 1)]
+    sm = S.Simulation(shape, [1, 1, 1], dt, beta, delta, dims=3, dtype="f32")
+    pinned = [f.pin_memory() for f in fields]
+    sm.set_state_host(pinned)
+    sm.step(3)
+    out_h = [torch.empty_like(f).pin_memory() for f in fields]
+    sm.get_state_host(out_h)
+    out_d = sm.get_state()
+    for a, b in zip(out_h, out_d):
+        assert torch.equal(a, b.cpu())
+    sm.close()
+
+
+def test_checkpoint_restore_is_bitwise():
+    shape = (16, 12, 8)
+    beta, delta = admissible_theta(4)
+    dt = 0.9 * D.dt_max(beta, delta, [1, 1, 1], 3)
+    sm = S.Simulation(shape, [1, 1, 1], dt, beta, delta, dims=3, dtype="f32")
+    sm.set_state([torch.from_numpy(f) for f in inputs.random_fields(shape, 2)])
+    sm.step(5)
+    sm.checkpoint_save(0)
+    sm.step(7)
+    a = sm.get_state()
+    sm.checkpoint_restore(0)
+    assert sm.step_index == 5
+    sm.step(7)
+    b = sm.get_state()
+    for x, y in zip(a, b):
+        assert torch.equal(x, y)
+    sm.close()
+
+
+def test_unstable_dt_rejected():
+    beta, delta = admissible_theta(5)
+    dtm = D.dt_max(beta, delta, [1, 1, 1], 3)
+    with pytest.raises(FdtdError) as ei:
+        S.Simulation((8, 8, 8), [1, 1, 1], 1.001 * dtm, beta, delta)
+    assert "constraints" in str(ei.value)
+    with pytest.raises(FdtdError):
+        S.Simulation((6, 8, 8), [1, 1, 1], 0.5 * dtm, beta, delta)   # nx % 4 != 0
+
+
+def test_dt_max_matches_oracle():
+    for seed in range(5):
+        for dims in (1, 2, 3):
+            beta, delta = inputs.random_theta(seed, dims)
+            dx = [1.0, 1.3, 0.7]
+            got = S.dt_max(beta, delta, dx, dims)
+            smin, smax = D.S_extremes(beta, delta, dx, dims)
+            assert got[2] == pytest.approx(smax, rel=1e-13)
+            assert got[1] == pytest.approx(smin, rel=1e-12, abs=1e-14)
+
+
+# ---------------------------------------------------------------- full size (256^3, 1000 steps)
+
+def closed_form_plane_wave(shape, dx, dt, coeffs, kvec, pol, n):
+    """Exact discrete solution for E^0 = pol cos(k.r) (transverse), B^{-1/2} = 0:
+    E^m = a_m E^0 with a_0 = 1, a_1 = 1 - 4 dt^2 S, a_{m+1} = 2 (1 - 2 dt^2 S) a_m - a_{m-1};
+    B^{m-1/2} = dt (F E^0) sum_{l<m} a_l."""
+    theta = [kvec[a] * dx[a] for a in range(3)]
+    kk = [theta[a] / coeffs.dx[a] for a in range(3)]
+    Sv = float(D.S_paper(*kk, coeffs.beta, coeffs.delta, coeffs.dx, 3, alpha_override=coeffs.alpha))
+    c = 1.0 - 2.0 * dt * dt * Sv
+    a_prev, a = 1.0, 1.0 - 4.0 * dt * dt * Sv
+    acc = 1.0  # sum_{l<1} a_l
+    for m in range(1, n):
+        acc += a
+        a_prev, a = a, 2 * c * a - a_prev
+    E0 = inputs.plane_wave(shape, kvec, pol, dx)[:3]
+    FE = F.faraday_rhs(E0, coeffs)
+    return [a * e for e in E0] + [dt * acc * f for f in FE], a
+
+
+@pytest.mark.parametrize("direction,pol,lam", [((1, 0, 0), (0, 0, 1), 16), ((1, 1, 0), (0, 0, 1), 8),
+                                               ((1, 1, 1), (1, -1, 0), 32)])
+def test_full_size_plane_wave_fp32_1000_steps(direction, pol, lam):
+    n_cells = 256
+    shape = (n_cells, n_cells, n_cells)
+    dx = [1.0, 1.0, 1.0]
+    beta, delta = admissible_theta(0)
+    dt = 0.95 * D.dt_max(beta, delta, dx, 3)
+    dvec = np.array(direction, dtype=np.float64)
+    m = max(1, round(n_cells / (lam * np.linalg.norm(dvec))))
+    kvec = dvec * 2 * math.pi * m / n_cells
+    fields = inputs.plane_wave(shape, kvec, pol, dx)
+    got = run_gpu(shape, dx, dt, beta, delta, 3, "f32", [f.astype(np.float32) for f in fields], 1000)
+    ref, _ = closed_form_plane_wave(shape, dx, dt, rounded_coeffs(beta, delta, dx, dt, 3, np.float32),
+                                    kvec, pol, 1000)
+    assert rel_l2(got, ref) <= 1e-5
