@@ -61,7 +61,8 @@ class FdtdProbeLoss(torch.autograd.Function):
             sm.step(n, probe=problem.probe, loss=loss)
         ctx.problem = problem
         ctx.coeffs = (b, d)
-        return loss[0]
+        ctx.devices = (beta.device, delta.device)
+        return loss[0].to(beta.device)
 
     @staticmethod
     def backward(ctx, gout):
@@ -75,9 +76,8 @@ class FdtdProbeLoss(torch.autograd.Function):
             sm.checkpoint_restore(slot)
             sm.step(n, record=True)
             sm.step_adjoint(n, grad, probe=problem.probe)
-        gb = grad[:9].reshape(3, 3) * gout
-        gd = grad[9:12] * gout
-        return gb, gd, None
+        g = grad.to(ctx.devices[0]) * gout.to(ctx.devices[0])
+        return g[:9].reshape(3, 3), g[9:12].to(ctx.devices[1]), None
 
 
 def tied_coefficients(theta: torch.Tensor):

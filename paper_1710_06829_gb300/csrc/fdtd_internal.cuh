@@ -52,6 +52,28 @@ struct Mult {
     T dt;
 };
 
+// D*_a F times dt (Eq. D*), from its 12 tap values, in one fixed rounding order shared by
+// every kernel (so all step kernels give bitwise-identical B):
+//   cA (F[+a] - F[0]) + cD (F[+2a] - F[-a]) + cBb ((F[+a+b] - F[+b]) + (F[+a-b] - F[-b]))
+//                                          + cBc ((F[+a+c] - F[+c]) + (F[+a-c] - F[-c]))
+template <typename T>
+__device__ __forceinline__ T dstar_taps(T f_a1, T f_0, T f_a2, T f_am1, T f_a1bp, T f_bp, T f_a1bm,
+                                        T f_bm, T f_a1cp, T f_cp, T f_a1cm, T f_cm, T cA, T cD,
+                                        T cBb, T cBc) {
+    T v = cA * (f_a1 - f_0);
+    v = fma(cD, f_a2 - f_am1, v);
+    v = fma(cBb, (f_a1bp - f_bp) + (f_a1bm - f_bm), v);
+    v = fma(cBc, (f_a1cp - f_cp) + (f_a1cm - f_cm), v);
+    return v;
+}
+
+// One Ampere component: E + (c1 (P - P[-a1]) - c2 (Q - Q[-a2])), in a fixed rounding order.
+template <typename T>
+__device__ __forceinline__ T ampere_comp(T e, T p0, T pm, T q0, T qm, T c1, T c2) {
+    const T t = c2 * (q0 - qm);
+    return e + fma(c1, p0 - pm, -t);
+}
+
 template <typename T>
 struct FieldSet {
     T* c[6];   // Ex, Ey, Ez, Bx, By, Bz (padded)

@@ -29,11 +29,9 @@ template <typename T>
 __device__ __forceinline__ T dstar_at(const T* __restrict__ F, long long c, long long a1,
                                       long long a2, long long am1, long long bp, long long bm,
                                       long long cp, long long cm, T cA, T cD, T cBb, T cBc) {
-    T v = cA * (F[c + a1] - F[c]);
-    v = fma(cD, F[c + a2] - F[c + am1], v);
-    v = fma(cBb, (F[c + a1 + bp] - F[c + bp]) + (F[c + a1 + bm] - F[c + bm]), v);
-    v = fma(cBc, (F[c + a1 + cp] - F[c + cp]) + (F[c + a1 + cm] - F[c + cm]), v);
-    return v;
+    return dstar_taps(F[c + a1], F[c], F[c + a2], F[c + am1], F[c + a1 + bp], F[c + bp],
+                      F[c + a1 + bm], F[c + bm], F[c + a1 + cp], F[c + cp], F[c + a1 + cm],
+                      F[c + cm], cA, cD, cBb, cBc);
 }
 
 template <typename T>
@@ -99,13 +97,13 @@ __global__ void ampere_v0_kernel(Geom g, Mult<T> m, FieldSet<T> s, const T* __re
     const T* Bx = s.c[3];
     const T* By = s.c[4];
     const T* Bz = s.c[5];
-    T ex = s.c[0][c] + (m.cE[1] * (Bz[c] - Bz[c - Y]) - m.cE[2] * (By[c] - By[c + zm1]));
-    T ey = s.c[1][c] + (m.cE[2] * (Bx[c] - Bx[c + zm1]) - m.cE[0] * (Bz[c] - Bz[c - 1]));
-    T ez = s.c[2][c] + (m.cE[0] * (By[c] - By[c - 1]) - m.cE[1] * (Bx[c] - Bx[c - Y]));
+    T ex = ampere_comp(s.c[0][c], Bz[c], Bz[c - Y], By[c], By[c + zm1], m.cE[1], m.cE[2]);
+    T ey = ampere_comp(s.c[1][c], Bx[c], Bx[c + zm1], Bz[c], Bz[c - 1], m.cE[2], m.cE[0]);
+    T ez = ampere_comp(s.c[2][c], By[c], By[c - 1], Bx[c], Bx[c - Y], m.cE[0], m.cE[1]);
     if (jx_row != nullptr) {
         // J_x^{n+1/2} at (i+1/2, j, k): x-profile x transverse profile, both tabulated.
-        const T jx = jx_row[i] * jyz[j] * jyz[g.ny + k];
-        ex = ex - m.dt * jx;
+        const T jx = (jx_row[i] * jyz[j]) * jyz[g.ny + k];
+        ex = fma(-m.dt, jx, ex);
     }
     if (spy != nullptr) {
         const T f = spy[j] * spz[k];
