@@ -37,10 +37,13 @@ BYTES_ADJ32 = 60.0    # lambda (6) read+write, E^n (3) read
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=50)
+    p.add_argument("--steps", type=int, default=1000)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--n", type=int, default=N_CELLS)
+    p.add_argument("--part", default="all", choices=["all", "fwd32"],
+                   help="fwd32: run only the FP32 forward steps (profiling driver); prints a "
+                        "short line that is not a bench result")
     return p.parse_args()
 
 
@@ -79,27 +82,39 @@ def peaks():
 
 
 class Clocks:
-    """nvidia-smi sampler running during the timed region."""
+    """nvidia-smi sampler; samples inside [mark_start, mark_end] describe the timed region."""
+
+    FIELDS = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, index=0):
         self.proc = None
         self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
         self.index = index
+        self.t0 = self.t1 = None
 
     def __enter__(self):
         try:
             os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(
-                ["nvidia-smi", "-i", str(self.index),
-                 "--query-gpu=clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
-                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
-                 "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.fh,
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "50"], stdout=self.fh,
                 stderr=subprocess.DEVNULL)
+            deadline = time.time() + 5.0
+            while time.time() < deadline and os.path.getsize(self.path) == 0:
+                time.sleep(0.05)
         except Exception:
             self.proc = None
         return self
+
+    def mark_start(self):
+        self.t0 = time.time()
+
+    def mark_end(self):
+        self.t1 = time.time()
+        time.sleep(0.15)
 
     def __exit__(self, *a):
         if self.proc is not None:
@@ -111,15 +126,30 @@ class Clocks:
             self.fh.close()
 
     def summary(self):
+        import datetime as _dt
         try:
-            rows = [r.split(",") for r in open(self.path).read().strip().splitlines()]
-            sm = [float(r[0]) for r in rows if r[0].strip().replace(".", "").isdigit()]
-            mx = max(float(r[1]) for r in rows)
+            rows = []
+            for line in open(self.path).read().strip().splitlines():
+                r = [x.strip() for x in line.split(",")]
+                try:
+                    ts = _dt.datetime.strptime(r[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                    rows.append((ts, r))
+                except ValueError:
+                    continue
+            inside = [r for ts, r in rows if self.t0 is not None and self.t0 <= ts <= self.t1]
+            window = "timed region"
+            if len(inside) < 2:
+                # region shorter than the sampling period: take the samples closest to it
+                mid = 0.5 * (self.t0 + self.t1)
+                inside = [r for _, r in sorted(rows, key=lambda x: abs(x[0] - mid))[:3]]
+                window = "nearest samples (timed region shorter than the sampling period)"
+            sm = [float(r[1]) for r in inside if r[1].replace(".", "").isdigit()]
+            mx = max(float(r[2]) for r in inside)
             names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-            reasons = sorted({names[i] for r in rows for i in range(4)
-                              if r[4 + i].strip().lower() == "active"})
+            reasons = sorted({names[i] for r in inside for i in range(4)
+                              if r[5 + i].lower() == "active"})
             return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
-                    "reasons": reasons, "samples": len(rows)}
+                    "reasons": reasons, "samples": len(inside), "window": window}
         except Exception as e:  # noqa: BLE001
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "error": str(e)[:80]}
 
@@ -250,9 +280,16 @@ def run_ours(args):
         sm.step(1)
     barrier(world)
     with Clocks(local) as clk:
+        clk.mark_start()
         t_fwd = time_events(lambda: sm.step(1), args.steps, stream)
+        clk.mark_end()
     t_fwd = barrier_max(t_fwd, world)
     fwd = world * cells * args.steps / t_fwd / 1e9
+    if args.part == "fwd32":
+        sm.close()
+        if rank == 0:
+            print(json.dumps({"part": "fwd32", "gcells_per_s": fwd, "ms_per_step": t_fwd / args.steps * 1e3}))
+        return
 
     # --- adjoint FP32 (record a segment, then reverse it)
     seg = min(args.steps, 20)
@@ -316,7 +353,7 @@ def run_ours(args):
         "e2e": {"value": e2e, "unit": "Gcell-updates/s",
                 "h2d_bytes_per_step": int(6 * 4 * cells), "d2h_bytes_per_step": int(6 * 4 * cells),
                 "step": f"host upload + {n_inner} leapfrog steps + host download"},
-        "gpu_launches": args.steps * 2,
+        "gpu_launches": args.steps * (1 if (n % 64 == 0 and n % 8 == 0) else 2),
         "clocks": clk.summary(),
     }
     if world == 1:

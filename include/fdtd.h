@@ -48,6 +48,7 @@ extern "C" {
 #define FDTD_ENOMEM     -4   /* device allocation failed */
 #define FDTD_ENONFINITE -5   /* a non-finite value was found */
 #define FDTD_ESTATE     -6   /* call not valid in the handle's current state */
+#define FDTD_ETIMEOUT   -7   /* a bounded wait inside a kernel expired (reported by fdtd_sync) */
 
 /* dtypes */
 #define FDTD_F32 0

@@ -20,6 +20,7 @@ FDTD_ECUDA = -3
 FDTD_ENOMEM = -4
 FDTD_ENONFINITE = -5
 FDTD_ESTATE = -6
+FDTD_ETIMEOUT = -7
 
 FDTD_F32 = 0
 FDTD_F64 = 1
@@ -32,7 +33,8 @@ FDTD_W_CONE_X = 1
 FDTD_W_GAUSS_Y = 2
 
 STATUS_NAMES = {0: "FDTD_OK", -1: "FDTD_EINVAL", -2: "FDTD_EUNSTABLE", -3: "FDTD_ECUDA",
-                -4: "FDTD_ENOMEM", -5: "FDTD_ENONFINITE", -6: "FDTD_ESTATE"}
+                -4: "FDTD_ENOMEM", -5: "FDTD_ENONFINITE", -6: "FDTD_ESTATE",
+                -7: "FDTD_ETIMEOUT"}
 
 # every symbol include/fdtd.h declares
 EXPORTS = ["fdtd_create", "fdtd_set_coeffs", "fdtd_set_state", "fdtd_get_state", "fdtd_get_step",

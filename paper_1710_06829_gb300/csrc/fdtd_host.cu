@@ -8,6 +8,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -211,6 +212,8 @@ struct fdtd_handle {
     char* staging;      // one dense array
     long long step;
     int use_fused;
+    FusedPlan* plan;    // TMA descriptors of both state sets (nullptr: reference-form kernels)
+    int* err_dev;       // raised by a kernel whose bounded wait expired
 
     void* arr(int set, int c) { return state + ((size_t)set * 6 + c) * g.total * esz; }
     void* lam_arr(int c) { return lam + (size_t)c * g.total * esz; }
@@ -360,6 +363,29 @@ int fdtd_create(const fdtd_grid* grid, const double dx[3], double dt, const fdtd
     }
     rc = G.dtype == FDTD_F32 ? upload_aux<float>(h) : upload_aux<double>(h);
     if (rc) { fdtd_destroy(h); return rc; }
+    e = cudaMalloc(&h->err_dev, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->err_dev, 0, sizeof(int), h->stream);
+    if (e != cudaSuccess) {
+        set_error("cudaMalloc failed: %s", cudaGetErrorString(e));
+        fdtd_destroy(h);
+        return FDTD_ECUDA;
+    }
+    // FDTD_FUSED=0 in the environment selects the reference-form kernels (same arithmetic).
+    const char* env = getenv("FDTD_FUSED");
+    h->use_fused = !(env && env[0] == '0');
+    if (h->use_fused) {
+        if (G.dtype == FDTD_F32) {
+            float* s0[6];
+            float* s1[6];
+            for (int c = 0; c < 6; ++c) { s0[c] = (float*)h->arr(0, c); s1[c] = (float*)h->arr(1, c); }
+            h->plan = fused_plan_create<float>(h->g, s0, s1);
+        } else {
+            double* s0[6];
+            double* s1[6];
+            for (int c = 0; c < 6; ++c) { s0[c] = (double*)h->arr(0, c); s1[c] = (double*)h->arr(1, c); }
+            h->plan = fused_plan_create<double>(h->g, s0, s1);
+        }
+    }
     *out = h;
     return FDTD_OK;
 }
@@ -557,7 +583,7 @@ static int step_impl(fdtd_handle* h, int n, const fdtd_source* src, const fdtd_p
         h->hist_len = n + 1;
         h->hist_step0 = h->step;
     }
-    const bool fused = h->use_fused && fused_supported<T>(g);
+    const bool fused = h->plan != nullptr;
     for (int s = 0; s < n; ++s) {
         if (record && !fused) {
             int rc = snapshot<T>(h, s);
@@ -573,8 +599,8 @@ static int step_impl(fdtd_handle* h, int n, const fdtd_source* src, const fdtd_p
                 }
                 for (int c = 0; c < 3; ++c) hE[c] = (T*)h->hist_arr(s + 1, c);
             }
-            launch_step_fused<T>(g, m, fieldset<T>(h, h->cur), fieldset<T>(h, 1 - h->cur), spy,
-                                 spz, jyz, jrow, hE, h->stream);
+            launch_step_fused<T>(h->plan, h->cur, g, m, fieldset<T>(h, 1 - h->cur), spy, spz, jyz,
+                                 jrow, hE, h->err_dev, h->stream);
             h->cur = 1 - h->cur;
         } else {
             FieldSet<T> fs = fieldset<T>(h, h->cur);
@@ -723,6 +749,13 @@ int fdtd_sync(fdtd_handle* h) {
     if (!h) { set_error("NULL handle"); return FDTD_EINVAL; }
     CK(cudaStreamSynchronize(h->stream));
     CK(cudaGetLastError());
+    int flag = 0;
+    CK(cudaMemcpy(&flag, h->err_dev, sizeof(int), cudaMemcpyDeviceToHost));
+    if (flag) {
+        cudaMemset(h->err_dev, 0, sizeof(int));
+        set_error("a bounded wait inside a step kernel expired; the state is not valid");
+        return FDTD_ETIMEOUT;
+    }
     return FDTD_OK;
 }
 
@@ -736,6 +769,8 @@ void fdtd_destroy(fdtd_handle* h) {
     if (h->jx) cudaFree(h->jx);
     if (h->partials) cudaFree(h->partials);
     if (h->staging) cudaFree(h->staging);
+    if (h->err_dev) cudaFree(h->err_dev);
+    if (h->plan) fused_plan_destroy(h->plan);
     for (char* p : h->ckpt)
         if (p) cudaFree(p);
     delete h;

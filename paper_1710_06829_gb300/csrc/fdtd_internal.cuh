@@ -88,14 +88,19 @@ template <typename T>
 void launch_ampere_v0(const Geom& g, const Mult<T>& m, FieldSet<T> s, const T* sponge_y,
                       const T* sponge_z, const T* jyz, const T* jx_row, cudaStream_t st);
 
-// Fused leapfrog step: reads (E^n, B^{n-1/2}) from `in`, writes (E^{n+1}, B^{n+1/2})
-// to `out` (both padded, images included).  hist_E (nullable) receives E^{n+1}.
-template <typename T>
-void launch_step_fused(const Geom& g, const Mult<T>& m, FieldSet<T> in, FieldSet<T> out,
-                       const T* sponge_y, const T* sponge_z, const T* jyz, const T* jx_row,
-                       T* hist_E[3], cudaStream_t st);
+// Fused leapfrog step: reads (E^n, B^{n-1/2}) from state set `in_set`, writes
+// (E^{n+1}, B^{n+1/2}) to `out` (padded, images included).  hist_E (entries
+// nullable) receives E^{n+1}.  The plan holds the TMA descriptors of both sets.
+struct FusedPlan;
 template <typename T>
 bool fused_supported(const Geom& g);
+template <typename T>
+FusedPlan* fused_plan_create(const Geom& g, T* const set0[6], T* const set1[6]);
+void fused_plan_destroy(FusedPlan* p);
+template <typename T>
+void launch_step_fused(const FusedPlan* plan, int in_set, const Geom& g, const Mult<T>& m,
+                       FieldSet<T> out, const T* sponge_y, const T* sponge_z, const T* jyz,
+                       const T* jx_row, T* hist_E[3], int* err, cudaStream_t st);
 
 template <typename T>
 void launch_adjoint_B_v0(const Geom& g, const Mult<T>& m, FieldSet<T> lam, const T* E_hist[3],

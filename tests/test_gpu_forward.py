@@ -51,7 +51,10 @@ def test_te_2d_fp64_matches_oracle(scheme):
 
 # ---------------------------------------------------------------- 3D, several tiles + ragged
 
-@pytest.mark.parametrize("shape", [(32, 24, 20), (36, 13, 7), (68, 34, 9), (4, 3, 2)])
+# (64, 16, 20), (128, 24, 33), (64, 8, 1) take the fused TMA kernel (nx % 64 == 0, ny % 8 == 0;
+# 33 planes leave a ragged last z-chunk); the others take the reference-form kernels.
+@pytest.mark.parametrize("shape", [(32, 24, 20), (36, 13, 7), (68, 34, 9), (4, 3, 2), (64, 16, 20),
+                                   (128, 24, 33), (64, 8, 1)])
 @pytest.mark.parametrize("dtype", ["f32", "f64"])
 def test_3d_random_fields_match_oracle(shape, dtype):
     beta, delta = admissible_theta(1)
@@ -198,3 +201,25 @@ def test_full_size_plane_wave_fp32_1000_steps(direction, pol, lam):
     ref, _ = closed_form_plane_wave(shape, dx, dt, rounded_coeffs(beta, delta, dx, dt, 3, np.float32),
                                     kvec, pol, 1000)
     assert rel_l2(got, ref) <= 1e-5
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+@pytest.mark.parametrize("shape", [(64, 16, 20), (128, 8, 3), (64, 8, 1)])
+def test_fused_kernel_bitwise_equals_reference_form(dtype, shape, monkeypatch):
+    """The fused TMA step and the reference-form kernels share their arithmetic: equal bits."""
+    beta, delta = admissible_theta(7)
+    dx = [1.0, 1.0, 1.0]
+    dt = 0.95 * D.dt_max(beta, delta, dx, 3)
+    fields = inputs.random_fields(shape, seed=8)
+    kw = dict(absorb_cells=2, absorb_sigma=0.2) if shape[2] >= 4 else {}
+    outs = []
+    for flag in ("1", "0"):
+        monkeypatch.setenv("FDTD_FUSED", flag)
+        sm = S.Simulation(shape, dx, dt, beta, delta, dims=3, dtype=dtype, **kw)
+        sm.set_state([torch.from_numpy(f) for f in fields])
+        sm.step(7, source=S.Bunch(1.0, 0.9, 10.0, 4.0, 1.0, 2.0, 2.0))
+        sm.sync()
+        outs.append(sm.get_state())
+        sm.close()
+    for a, b in zip(*outs):
+        assert torch.equal(a, b)
