@@ -21,21 +21,11 @@
 //
 // Every mbarrier wait is bounded; on expiry the CTA raises *err, waits (again
 // bounded) for its copies in flight and returns without writing.
-#include <cuda.h>
+#include <type_traits>
 
-#include "fdtd_internal.cuh"
+#include "fdtd_tma.cuh"
 
 namespace fdtd {
-
-struct FusedMaps {
-    CUtensorMap e[3];   // E boxes of the input set
-    CUtensorMap b[3];   // B boxes of the input set
-};
-
-struct FusedPlan {
-    int dtype;
-    FusedMaps maps[2];   // indexed by input set
-};
 
 template <typename T>
 struct FusedCfg;
@@ -66,70 +56,6 @@ struct Layout {
     static constexpr uint32_t UNIT_BYTES = 3u * EPL * sizeof(T) + 3u * BPL * sizeof(T);
     static constexpr uint32_t PRO_BYTES = 9u * EPL * sizeof(T);
 };
-
-// ---------------------------------------------------------------- PTX helpers
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
-                 : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
-                 "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// bounded wait: about a second at most
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-    for (uint32_t it = 0; it < (1u << 20); ++it)
-        if (mbar_try_wait(bar, parity)) return true;
-    return false;
-}
-
-__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z,
-                                            uint64_t* bar) {
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
-        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
-        : "memory");
-}
-
-template <typename T>
-__device__ __forceinline__ void store_img(const Geom& g, T* F, int i, int j, int k, T v) {
-    const long long base = (long long)k * g.nyp;
-    F[(base + j + PY) * g.nxp + i + PX] = v;
-    const bool xedge = (i < PX) || (i >= g.nx - PX);
-    const bool yedge = (j < PY) || (j >= g.ny - PY);
-    if (!xedge && !yedge) return;
-    for (int my = -2; my <= 2; ++my) {
-        const int jj = j + my * g.ny;
-        if (jj < -PY || jj >= g.ny + PY) continue;
-        for (int mx = -1; mx <= 1; ++mx) {
-            const int ii = i + mx * g.nx;
-            if (ii < -PX || ii >= g.nx + PX) continue;
-            if (mx == 0 && my == 0) continue;
-            F[(base + jj + PY) * g.nxp + ii + PX] = v;
-        }
-    }
-}
 
 // ---------------------------------------------------------------- kernel
 
@@ -336,8 +262,15 @@ static EncodeTiledFn encode_fn() {
     return fn;
 }
 
+bool fused32_supported(const Geom& g);
+bool fused32_prepare();
+void launch_fused32(const FusedMaps& maps, FieldSet<float> in, const Geom& g, const Mult<float>& m,
+                    FieldSet<float> out, const float* spy, const float* spz, const float* jyz,
+                    const float* jx_row, float* hist_E[3], int* err, cudaStream_t st);
+
 template <typename T>
 bool fused_supported(const Geom& g) {
+    if constexpr (std::is_same<T, float>::value) return fused32_supported(g);
     using C = FusedCfg<T>;
     return g.nx % C::TX == 0 && g.ny % C::TY == 0 && g.nx >= C::TX && g.ny >= C::TY;
 }
@@ -373,8 +306,13 @@ FusedPlan* fused_plan_create(const Geom& g, T* const set0[6], T* const set1[6]) 
             }
         }
     }
-    if (cudaFuncSetAttribute(step_fused_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)Lc::SMEM) != cudaSuccess) {
+    bool ok;
+    if constexpr (std::is_same<T, float>::value)
+        ok = fused32_prepare();
+    else
+        ok = cudaFuncSetAttribute(step_fused_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)Lc::SMEM) == cudaSuccess;
+    if (!ok) {
         delete p;
         return nullptr;
     }
@@ -385,8 +323,13 @@ void fused_plan_destroy(FusedPlan* p) { delete p; }
 
 template <typename T>
 void launch_step_fused(const FusedPlan* plan, int in_set, const Geom& g, const Mult<T>& m,
-                       FieldSet<T> out, const T* sponge_y, const T* sponge_z, const T* jyz,
-                       const T* jx_row, T* hist_E[3], int* err, cudaStream_t st) {
+                       FieldSet<T> in, FieldSet<T> out, const T* sponge_y, const T* sponge_z,
+                       const T* jyz, const T* jx_row, T* hist_E[3], int* err, cudaStream_t st) {
+    if constexpr (std::is_same<T, float>::value) {
+        launch_fused32(plan->maps[in_set], in, g, m, out, sponge_y, sponge_z, jyz, jx_row, hist_E,
+                       err, st);
+        return;
+    }
     using C = FusedCfg<T>;
     const int nblk = (g.nx / C::TX) * (g.ny / C::TY) * ((g.nz + C::TZ - 1) / C::TZ);
     step_fused_kernel<T><<<nblk, C::NT, Layout<T>::SMEM, st>>>(
@@ -399,10 +342,10 @@ template bool fused_supported<double>(const Geom&);
 template FusedPlan* fused_plan_create<float>(const Geom&, float* const[6], float* const[6]);
 template FusedPlan* fused_plan_create<double>(const Geom&, double* const[6], double* const[6]);
 template void launch_step_fused<float>(const FusedPlan*, int, const Geom&, const Mult<float>&,
-                                       FieldSet<float>, const float*, const float*, const float*,
+                                       FieldSet<float>, FieldSet<float>, const float*, const float*, const float*,
                                        const float*, float* [3], int*, cudaStream_t);
 template void launch_step_fused<double>(const FusedPlan*, int, const Geom&, const Mult<double>&,
-                                        FieldSet<double>, const double*, const double*,
+                                        FieldSet<double>, FieldSet<double>, const double*, const double*,
                                         const double*, const double*, double* [3], int*,
                                         cudaStream_t);
 

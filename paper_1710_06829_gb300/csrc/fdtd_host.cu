@@ -599,8 +599,9 @@ static int step_impl(fdtd_handle* h, int n, const fdtd_source* src, const fdtd_p
                 }
                 for (int c = 0; c < 3; ++c) hE[c] = (T*)h->hist_arr(s + 1, c);
             }
-            launch_step_fused<T>(h->plan, h->cur, g, m, fieldset<T>(h, 1 - h->cur), spy, spz, jyz,
-                                 jrow, hE, h->err_dev, h->stream);
+            launch_step_fused<T>(h->plan, h->cur, g, m, fieldset<T>(h, h->cur),
+                                 fieldset<T>(h, 1 - h->cur), spy, spz, jyz, jrow, hE, h->err_dev,
+                                 h->stream);
             h->cur = 1 - h->cur;
         } else {
             FieldSet<T> fs = fieldset<T>(h, h->cur);

@@ -99,8 +99,8 @@ FusedPlan* fused_plan_create(const Geom& g, T* const set0[6], T* const set1[6]);
 void fused_plan_destroy(FusedPlan* p);
 template <typename T>
 void launch_step_fused(const FusedPlan* plan, int in_set, const Geom& g, const Mult<T>& m,
-                       FieldSet<T> out, const T* sponge_y, const T* sponge_z, const T* jyz,
-                       const T* jx_row, T* hist_E[3], int* err, cudaStream_t st);
+                       FieldSet<T> in, FieldSet<T> out, const T* sponge_y, const T* sponge_z,
+                       const T* jyz, const T* jx_row, T* hist_E[3], int* err, cudaStream_t st);
 
 template <typename T>
 void launch_adjoint_B_v0(const Geom& g, const Mult<T>& m, FieldSet<T> lam, const T* E_hist[3],
