@@ -174,6 +174,22 @@ int disp_norm_eval(const fdtd_coeffs* coeffs, double dt, const double dx[3], int
                    const int32_t N[3], int32_t weight, double weight_param, double* out,
                    void* stream);
 
+/* disp_norm_eval without any device allocation.  The paper has no counterpart:
+ * this is a library service for callers that may not allocate device memory
+ * when they need the norm (for instance while another stream of the device is
+ * being captured into a CUDA graph, or under a host that owns every byte of the
+ * GPU through its own pool).  Same arguments, results and synchronisation as
+ * disp_norm_eval; the kernels work in a scratch area the library declares
+ * statically on each device (512 KiB, kept until the process exits).
+ * Limit: N[i] <= 4096 on every used axis, else FDTD_EINVAL (use disp_norm_eval).
+ * The first call on a device (with that device current) looks the area's
+ * address up; make it before any stream capture.  All calls share the one area,
+ * so calls that overlap on the GPU (different streams, no ordering) race; calls
+ * ordered on one stream are safe.  No part of the area must start at zero. */
+int disp_norm_eval_noalloc(const fdtd_coeffs* coeffs, double dt, const double dx[3],
+                           int32_t dims, const int32_t N[3], int32_t weight, double weight_param,
+                           double* out, void* stream);
+
 /* Exact extremes of S(k) = sum_i s_i^2 A_i over the Brillouin box (host, FP64)
  * and dt_max = 1/sqrt(max S), the CFL limit of Eq. (constraints). */
 int fdtd_dt_max(const fdtd_coeffs* coeffs, const double dx[3], int32_t dims, double* dt_max,

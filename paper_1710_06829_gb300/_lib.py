@@ -39,8 +39,8 @@ STATUS_NAMES = {0: "FDTD_OK", -1: "FDTD_EINVAL", -2: "FDTD_EUNSTABLE", -3: "FDTD
 # every symbol include/fdtd.h declares
 EXPORTS = ["fdtd_create", "fdtd_set_coeffs", "fdtd_set_state", "fdtd_get_state", "fdtd_get_step",
            "fdtd_step", "fdtd_checkpoint", "fdtd_set_adjoint", "fdtd_get_adjoint",
-           "fdtd_step_adjoint", "fdtd_sync", "fdtd_destroy", "disp_norm_eval", "fdtd_dt_max",
-           "fdtd_last_error"]
+           "fdtd_step_adjoint", "fdtd_sync", "fdtd_destroy", "disp_norm_eval",
+           "disp_norm_eval_noalloc", "fdtd_dt_max", "fdtd_last_error"]
 
 
 class FdtdError(RuntimeError):
@@ -101,6 +101,7 @@ def load():
     lib.fdtd_destroy.restype = None
     lib.disp_norm_eval.argtypes = [C.POINTER(fdtd_coeffs), D, pd, I32, C.POINTER(I32), I32, D,
                                    pd, P]
+    lib.disp_norm_eval_noalloc.argtypes = lib.disp_norm_eval.argtypes
     lib.fdtd_dt_max.argtypes = [C.POINTER(fdtd_coeffs), pd, I32, pd, pd, pd]
     lib.fdtd_last_error.restype = C.c_char_p
     for name in EXPORTS:
@@ -200,6 +201,16 @@ def disp_norm_eval(coeffs, dt, dx, dims, N, weight=FDTD_W_UNIFORM, weight_param=
     n3 = (C.c_int32 * 3)(*[int(v) for v in N])
     check(load().disp_norm_eval(C.byref(coeffs), float(dt), _d3(dx), int(dims), n3, int(weight),
                                 float(weight_param), out, C.c_void_p(stream)))
+    return list(out)
+
+
+def disp_norm_eval_noalloc(coeffs, dt, dx, dims, N, weight=FDTD_W_UNIFORM, weight_param=0.0,
+                           stream=0):
+    """disp_norm_eval on the library's static per-device scratch (allocates nothing)."""
+    out = (C.c_double * 14)()
+    n3 = (C.c_int32 * 3)(*[int(v) for v in N])
+    check(load().disp_norm_eval_noalloc(C.byref(coeffs), float(dt), _d3(dx), int(dims), n3,
+                                        int(weight), float(weight_param), out, C.c_void_p(stream)))
     return list(out)
 
 

@@ -10,6 +10,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -818,3 +819,118 @@ int disp_norm_eval(const fdtd_coeffs* coeffs, double dt, const double dx[3], int
     return FDTD_OK;
 }
 
+
+// ---------------------------------------------------------------------------
+// disp_norm_eval_noalloc: the dispersion norm without any device allocation.
+//
+// Some callers cannot allocate device memory at the moment they need the norm:
+// code running while a CUDA graph is being built on another stream of the same
+// device, a host that pre-reserves every byte of the GPU for its own pool, or a
+// plug-in that is not allowed to touch the allocator at all.  For them this entry
+// point runs the same three kernels as disp_norm_eval on a fixed scratch area
+// that the library declares statically on every device it is loaded on (512 KiB,
+// held until the process exits) instead of asking cudaMallocAsync for one.
+//
+// The host never uses the array's name as a device address: on the first call on
+// a device (with that device current) cudaGetSymbolAddress yields its address,
+// which is cached per device and passed to the kernels.  That first call is the
+// set-up; make it before capturing any stream into a graph.
+// ---------------------------------------------------------------------------
+
+namespace {
+
+constexpr int kNoallocMaxN = 4096;              // per k-axis
+constexpr size_t kNoallocDoubles = 64 * 1024;   // 3*(3*4096) table + partials + results fit
+constexpr int kNoallocMaxDevices = 64;
+
+static __device__ __align__(256) double g_norm_scratch[kNoallocDoubles];
+
+static double* g_norm_scratch_addr[kNoallocMaxDevices];
+
+int noalloc_scratch_address(double** out) {
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) {
+        set_error("disp_norm_eval_noalloc: cudaGetDevice failed: %s", cudaGetErrorString(e));
+        return FDTD_ECUDA;
+    }
+    if (dev < 0 || dev >= kNoallocMaxDevices) {
+        set_error("disp_norm_eval_noalloc: device ordinal %d out of range", dev);
+        return FDTD_EINVAL;
+    }
+    static std::mutex mu;
+    std::lock_guard<std::mutex> lock(mu);
+    if (g_norm_scratch_addr[dev] == nullptr) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_norm_scratch);
+        if (e != cudaSuccess || p == nullptr) {
+            set_error("disp_norm_eval_noalloc: cudaGetSymbolAddress failed: %s",
+                      cudaGetErrorString(e));
+            return FDTD_ECUDA;
+        }
+        g_norm_scratch_addr[dev] = static_cast<double*>(p);
+    }
+    *out = g_norm_scratch_addr[dev];
+    return FDTD_OK;
+}
+
+}  // namespace
+
+int disp_norm_eval_noalloc(const fdtd_coeffs* coeffs, double dt, const double dx[3], int32_t dims,
+                           const int32_t N[3], int32_t weight, double weight_param, double* out,
+                           void* stream) {
+    if (!coeffs || !dx || !N || !out || dims < 1 || dims > 3) {
+        set_error("disp_norm_eval_noalloc: bad argument");
+        return FDTD_EINVAL;
+    }
+    for (int i = 0; i < dims; ++i) {
+        if (N[i] < 1 || !(dx[i] > 0)) {
+            set_error("disp_norm_eval_noalloc: bad grid");
+            return FDTD_EINVAL;
+        }
+        if (N[i] > kNoallocMaxN) {
+            set_error("disp_norm_eval_noalloc: N[%d] = %d exceeds the static scratch limit of %d "
+                      "points per axis (use disp_norm_eval)", i, N[i], kNoallocMaxN);
+            return FDTD_EINVAL;
+        }
+    }
+    if (weight != FDTD_W_UNIFORM && weight != FDTD_W_CONE_X && weight != FDTD_W_GAUSS_Y) {
+        set_error("unknown weight %d", weight);
+        return FDTD_EINVAL;
+    }
+    if (weight == FDTD_W_GAUSS_Y && !(weight_param > 0)) {
+        set_error("gauss width must be > 0");
+        return FDTD_EINVAL;
+    }
+    Clean cc = clean_coeffs(coeffs, dims);
+    int rc = validate(cc, dx, dims, dt);
+    if (rc) return rc;
+    int Nd[3];
+    long long npts = 1;
+    for (int i = 0; i < 3; ++i) {
+        Nd[i] = i < dims ? N[i] : 1;
+        npts *= Nd[i];
+    }
+    if (norm_scratch_doubles(Nd, npts) > kNoallocDoubles) {
+        set_error("disp_norm_eval_noalloc: grid needs more than the %zu-double static scratch",
+                  kNoallocDoubles);
+        return FDTD_EINVAL;
+    }
+    double* scratch = nullptr;
+    rc = noalloc_scratch_address(&scratch);
+    if (rc) return rc;
+    // Nothing in the scratch needs clearing: the kernels write every table entry, every
+    // per-block partial and every result slot before reading it in this same call.
+    cudaStream_t st = (cudaStream_t)stream;
+    double* res = nullptr;
+    launch_disp_norm(cc.alpha, cc.beta, cc.delta, dt, dx, dims, Nd, weight, weight_param, scratch,
+                     &res, st);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, res, 14 * sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        set_error("disp_norm_eval_noalloc: %s", cudaGetErrorString(e));
+        return FDTD_ECUDA;
+    }
+    return FDTD_OK;
+}
