@@ -71,10 +71,13 @@ typedef struct fdtd_handle fdtd_handle;
 
 typedef struct {
     int32_t dims;          /* 1, 2 or 3: axes that carry wave propagation */
-    int32_t nx, ny, nz;    /* cells; nx % 4 == 0; dims 2 needs nz == 1, dims 1 ny == nz == 1 */
+    int32_t nx, ny, nz;    /* cells; nx % 4 == 0; dims 2 needs nz == 1 (unless batched),
+                              dims 1 needs ny == nz == 1 */
     int32_t dtype;         /* FDTD_F32 or FDTD_F64: precision of fields and stepping */
     int32_t absorb_cells;  /* width L of absorbing sponge layers on +-y and +-z (0 = none) */
     double  absorb_sigma;  /* sponge strength: fields scaled by 1 - sigma (d/L)^3, d = 1..L */
+    int32_t batched;       /* dims == 2 only: 1 = the nz planes are nz independent 2D problems
+                              (no coupling along z; sponge on +-y only; no bunch source) */
 } fdtd_grid;
 
 typedef struct {
@@ -189,6 +192,19 @@ int disp_norm_eval(const fdtd_coeffs* coeffs, double dt, const double dx[3], int
 int disp_norm_eval_noalloc(const fdtd_coeffs* coeffs, double dt, const double dx[3],
                            int32_t dims, const int32_t N[3], int32_t weight, double weight_param,
                            double* out, void* stream);
+
+/* One step of the constrained coefficient minimisation (Sec. 4; projected gradient descent
+ * in FP64 on the GPU instead of SLSQP).  The n <= 16 free parameters theta map linearly
+ * onto the 13 scheme parameters c = (beta 3x3 row-major, delta 3, dt) as c = c0 + T^T theta
+ * (T: n x 13 row-major, host; the tying of Sec. 4, e.g. beta_xy = beta_yx).  With grad13 the
+ * gradient of the objective in c (the layout of disp_norm_eval's out[1..13]):
+ *     theta' = clip(theta - eta T grad13, lo, hi),   c' = c0 + T^T theta'.
+ * theta, grad13, T, c0, lo, hi are host arrays; out_dev is a caller-owned device buffer of
+ * n + 13 doubles receiving (theta', c').  Asynchronous on `stream`.  Eq. (constraints) is not
+ * checked here: the caller validates c' (fdtd_dt_max or disp_norm_eval) and backtracks. */
+int fdtd_coeff_update(int32_t n, const double* theta, const double* grad13, const double* T,
+                      const double* c0, double eta, const double* lo, const double* hi,
+                      double* out_dev, void* stream);
 
 /* Exact extremes of S(k) = sum_i s_i^2 A_i over the Brillouin box (host, FP64)
  * and dt_max = 1/sqrt(max S), the CFL limit of Eq. (constraints). */

@@ -40,7 +40,7 @@ STATUS_NAMES = {0: "FDTD_OK", -1: "FDTD_EINVAL", -2: "FDTD_EUNSTABLE", -3: "FDTD
 EXPORTS = ["fdtd_create", "fdtd_set_coeffs", "fdtd_set_state", "fdtd_get_state", "fdtd_get_step",
            "fdtd_step", "fdtd_checkpoint", "fdtd_set_adjoint", "fdtd_get_adjoint",
            "fdtd_step_adjoint", "fdtd_sync", "fdtd_destroy", "disp_norm_eval",
-           "disp_norm_eval_noalloc", "fdtd_dt_max", "fdtd_last_error"]
+           "disp_norm_eval_noalloc", "fdtd_coeff_update", "fdtd_dt_max", "fdtd_last_error"]
 
 
 class FdtdError(RuntimeError):
@@ -51,7 +51,8 @@ class FdtdError(RuntimeError):
 
 class fdtd_grid(C.Structure):
     _fields_ = [("dims", C.c_int32), ("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32),
-                ("dtype", C.c_int32), ("absorb_cells", C.c_int32), ("absorb_sigma", C.c_double)]
+                ("dtype", C.c_int32), ("absorb_cells", C.c_int32), ("absorb_sigma", C.c_double),
+                ("batched", C.c_int32)]
 
 
 class fdtd_coeffs(C.Structure):
@@ -102,6 +103,7 @@ def load():
     lib.disp_norm_eval.argtypes = [C.POINTER(fdtd_coeffs), D, pd, I32, C.POINTER(I32), I32, D,
                                    pd, P]
     lib.disp_norm_eval_noalloc.argtypes = lib.disp_norm_eval.argtypes
+    lib.fdtd_coeff_update.argtypes = [I32, pd, pd, pd, pd, D, pd, pd, P, P]
     lib.fdtd_dt_max.argtypes = [C.POINTER(fdtd_coeffs), pd, I32, pd, pd, pd]
     lib.fdtd_last_error.restype = C.c_char_p
     for name in EXPORTS:
@@ -212,6 +214,15 @@ def disp_norm_eval_noalloc(coeffs, dt, dx, dims, N, weight=FDTD_W_UNIFORM, weigh
     check(load().disp_norm_eval_noalloc(C.byref(coeffs), float(dt), _d3(dx), int(dims), n3,
                                         int(weight), float(weight_param), out, C.c_void_p(stream)))
     return list(out)
+
+
+def fdtd_coeff_update(theta, grad13, T, c0, eta, lo, hi, out_dev, stream=0):
+    """theta' = clip(theta - eta T grad13, lo, hi), c' = c0 + T^T theta' into out_dev (device)."""
+    n = len(theta)
+    arr = lambda v: (C.c_double * len(v))(*[float(x) for x in v])  # noqa: E731
+    Tflat = [float(x) for row in T for x in row]
+    check(load().fdtd_coeff_update(n, arr(theta), arr(grad13), arr(Tflat), arr(c0), float(eta),
+                                   arr(lo), arr(hi), C.c_void_p(out_dev), C.c_void_p(stream)))
 
 
 def fdtd_dt_max(coeffs, dx, dims):

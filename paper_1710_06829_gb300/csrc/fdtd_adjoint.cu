@@ -215,8 +215,8 @@ template void launch_adjoint_E_v0<double>(const Geom&, const Mult<double>&, Fiel
                                           const double*, const double*, cudaStream_t);
 
 // grad12[beta row-major 3x3, delta 3] += scale_a * sum_b partials[b][.]  (one block, fixed order)
-__global__ void reduce_grad_kernel(const double* __restrict__ part, int nblocks, double s0,
-                                   double s1, double s2, double* __restrict__ grad) {
+__global__ void reduce_grad_kernel(const double* __restrict__ part, int nblocks, GradScale sc,
+                                   double* __restrict__ grad) {
     __shared__ double red[9][32];
     const int q = threadIdx.y;       // 0..8
     const int l = threadIdx.x;       // 0..31
@@ -228,20 +228,19 @@ __global__ void reduce_grad_kernel(const double* __restrict__ part, int nblocks,
         double s = 0.0;
         for (int t = 0; t < 32; ++t) s += red[q][t];
         const int a = q / 3, which = q % 3;
-        const double sc = a == 0 ? s0 : (a == 1 ? s1 : s2);
         if (which == 0) {
-            grad[9 + a] += sc * s;
+            grad[9 + a] += sc.s[q] * s;
         } else {
             // transverse axes of a in increasing order
             const int b = (which == 1) ? (a == 0 ? 1 : 0) : (a == 2 ? 1 : 2);
-            grad[a * 3 + b] += sc * s;
+            grad[a * 3 + b] += sc.s[q] * s;
         }
     }
 }
 
-void launch_reduce_grad(const double* part, int nblocks, double s0, double s1, double s2,
-                        double* grad12, cudaStream_t st) {
-    reduce_grad_kernel<<<1, dim3(32, 9), 0, st>>>(part, nblocks, s0, s1, s2, grad12);
+void launch_reduce_grad(const double* part, int nblocks, GradScale sc, double* grad12,
+                        cudaStream_t st) {
+    reduce_grad_kernel<<<1, dim3(32, 9), 0, st>>>(part, nblocks, sc, grad12);
 }
 
 }  // namespace fdtd

@@ -160,14 +160,20 @@ static int validate(const Clean& cc, const double dx[3], int dims, double dt) {
     return FDTD_OK;
 }
 
+// zcouple = false (batched 2D problems): every multiplier of a z difference is zero, so
+// the planes never exchange values.
 template <typename T>
-static Mult<T> make_mult(const Clean& cc, const double dx[3], double dt) {
+static Mult<T> make_mult(const Clean& cc, const double dx[3], double dt, bool zcouple = true) {
     Mult<T> m;
     for (int a = 0; a < 3; ++a) {
         m.cA[a] = (T)(dt * cc.alpha[a] / dx[a]);
         m.cD[a] = (T)(dt * cc.delta[a] / dx[a]);
         for (int b = 0; b < 3; ++b) m.cB[a][b] = (T)(dt * cc.beta[a][b] / dx[a]);
         m.cE[a] = (T)(dt / dx[a]);
+    }
+    if (!zcouple) {
+        m.cA[2] = m.cD[2] = m.cE[2] = (T)0;
+        for (int b = 0; b < 3; ++b) m.cB[2][b] = m.cB[b][2] = (T)0;
     }
     m.dt = (T)dt;
     return m;
@@ -251,7 +257,7 @@ static int upload_aux(fdtd_handle* h) {
         return 1.0 - sg * x * x * x;
     };
     for (int j = 0; j < ny; ++j) a[j] = (T)prof(ny, j);
-    for (int k = 0; k < nz; ++k) a[ny + k] = (T)prof(nz, k);
+    for (int k = 0; k < nz; ++k) a[ny + k] = h->grid.batched ? (T)1 : (T)prof(nz, k);
     CK(cudaMemcpyAsync(h->aux, a.data(), a.size() / 2 * sizeof(T), cudaMemcpyHostToDevice,
                        h->stream));
     CK(cudaStreamSynchronize(h->stream));
@@ -318,10 +324,16 @@ int fdtd_create(const fdtd_grid* grid, const double dx[3], double dt, const fdtd
     if (G.dims < 1 || G.dims > 3) { set_error("dims must be 1, 2 or 3"); return FDTD_EINVAL; }
     if (G.nx < 4 || G.nx % 4 != 0) { set_error("nx must be a positive multiple of 4"); return FDTD_EINVAL; }
     if (G.ny < 1 || G.nz < 1) { set_error("ny, nz must be >= 1"); return FDTD_EINVAL; }
-    if (G.dims <= 2 && G.nz != 1) { set_error("dims < 3 needs nz == 1"); return FDTD_EINVAL; }
+    if (G.batched != 0 && G.batched != 1) { set_error("batched must be 0 or 1"); return FDTD_EINVAL; }
+    if (G.batched && G.dims != 2) { set_error("batched needs dims == 2"); return FDTD_EINVAL; }
+    if (G.dims <= 2 && G.nz != 1 && !G.batched) {
+        set_error("dims < 3 needs nz == 1 (or batched = 1)");
+        return FDTD_EINVAL;
+    }
     if (G.dims == 1 && G.ny != 1) { set_error("dims == 1 needs ny == 1"); return FDTD_EINVAL; }
     if (G.dtype != FDTD_F32 && G.dtype != FDTD_F64) { set_error("bad dtype"); return FDTD_EINVAL; }
-    if (G.absorb_cells < 0 || 2 * G.absorb_cells > G.ny || (G.absorb_cells > 0 && 2 * G.absorb_cells > G.nz)) {
+    if (G.absorb_cells < 0 || 2 * G.absorb_cells > G.ny ||
+        (G.absorb_cells > 0 && !G.batched && 2 * G.absorb_cells > G.nz)) {
         set_error("absorbing layers do not fit the grid");
         return FDTD_EINVAL;
     }
@@ -558,7 +570,7 @@ template <typename T>
 static int step_impl(fdtd_handle* h, int n, const fdtd_source* src, const fdtd_probe* probe,
                      double* loss, int record) {
     const Geom& g = h->g;
-    const Mult<T> m = make_mult<T>(h->cc, h->dx, h->dt);
+    const Mult<T> m = make_mult<T>(h->cc, h->dx, h->dt, !h->grid.batched);
     const T* spy = nullptr;
     const T* spz = nullptr;
     if (h->grid.absorb_cells > 0) {
@@ -636,6 +648,10 @@ int fdtd_step(fdtd_handle* h, int32_t n, const fdtd_source* src, const fdtd_prob
         set_error("unknown source kind %d", src->kind);
         return FDTD_EINVAL;
     }
+    if (src && src->kind == FDTD_SRC_BUNCH && h->grid.batched) {
+        set_error("the bunch source is not defined for batched 2D problems");
+        return FDTD_EINVAL;
+    }
     if (src && src->kind == FDTD_SRC_BUNCH && !(src->sigma_par > 0 && src->sigma_perp > 0)) {
         set_error("bunch widths must be positive");
         return FDTD_EINVAL;
@@ -684,7 +700,7 @@ int fdtd_checkpoint(fdtd_handle* h, int32_t slot, int32_t op) {
 template <typename T>
 static int adjoint_impl(fdtd_handle* h, int n, const fdtd_probe* probe, double* grad) {
     const Geom& g = h->g;
-    const Mult<T> m = make_mult<T>(h->cc, h->dx, h->dt);
+    const Mult<T> m = make_mult<T>(h->cc, h->dx, h->dt, !h->grid.batched);
     const T* spy = nullptr;
     const T* spz = nullptr;
     if (h->grid.absorb_cells > 0) {
@@ -719,8 +735,18 @@ static int adjoint_impl(fdtd_handle* h, int n, const fdtd_probe* probe, double* 
         launch_adjoint_E_v0<T>(g, m, lam, spy, spz, h->stream);
         CK(cudaGetLastError());
     }
-    launch_reduce_grad(h->partials, nblk, h->dt / h->dx[0], h->dt / h->dx[1], h->dt / h->dx[2],
-                       grad, h->stream);
+    // scale of each partial: dt/dx_a, zero for entries that refer to an absent axis
+    // (their brackets may mix independent batched problems)
+    GradScale sc;
+    const int dims = h->grid.dims;
+    for (int a = 0; a < 3; ++a) {
+        const int b1 = a == 0 ? 1 : 0, b2 = a == 2 ? 1 : 2;
+        const double s_a = a < dims ? h->dt / h->dx[a] : 0.0;
+        sc.s[3 * a + 0] = s_a;
+        sc.s[3 * a + 1] = b1 < dims ? s_a : 0.0;
+        sc.s[3 * a + 2] = b2 < dims ? s_a : 0.0;
+    }
+    launch_reduce_grad(h->partials, nblk, sc, grad, h->stream);
     CK(cudaGetLastError());
     h->hist_len -= n;
     return FDTD_OK;

@@ -122,9 +122,13 @@ void launch_pack(const Geom& g, const T* padded, T* dense, cudaStream_t st);
 template <typename T>
 void launch_unpack(const Geom& g, const T* dense, T* padded, cudaStream_t st);
 
-// grad12[beta 3x3 row-major, delta 3] += (dt/dx_a) * sum over blocks of the partials.
-void launch_reduce_grad(const double* part, int nblocks, double s0, double s1, double s2,
-                        double* grad12, cudaStream_t st);
+// grad12[beta 3x3 row-major, delta 3] += s[q] * sum over blocks of partial q, where partial
+// q = 3a + w is (axis a; w = 0: delta_a, 1 / 2: beta of the first / second other axis).
+struct GradScale {
+    double s[9];
+};
+void launch_reduce_grad(const double* part, int nblocks, GradScale sc, double* grad12,
+                        cudaStream_t st);
 
 // thread-local error message
 void set_error(const char* fmt, ...);

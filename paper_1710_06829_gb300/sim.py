@@ -47,13 +47,13 @@ class Simulation:
     """One FDTD state (E, B) on a periodic nx x ny x nz grid, owned by libfdtd."""
 
     def __init__(self, shape, dx, dt, beta, delta, dims=3, dtype="f32", absorb_cells=0,
-                 absorb_sigma=0.0, stream=None):
+                 absorb_sigma=0.0, stream=None, batched=False):
         nx, ny, nz = shape
         self.shape = (nz, ny, nx)
         self.dims = dims
         self.code, self.tdtype = _DT[dtype]
         self.stream = stream if stream is not None else torch.cuda.current_stream()
-        g = L.fdtd_grid(dims, nx, ny, nz, self.code, absorb_cells, absorb_sigma)
+        g = L.fdtd_grid(dims, nx, ny, nz, self.code, absorb_cells, absorb_sigma, int(batched))
         self.h = L.fdtd_create(g, dx, dt, coeffs_struct(beta, delta), _stream_ptr(self.stream))
         self.dx = tuple(dx)
         self.dt = dt

@@ -26,7 +26,7 @@ def test_library_loads_and_exports_all_symbols():
 
 def test_struct_layouts_match_header():
     import ctypes as C
-    assert C.sizeof(L.fdtd_grid) == 6 * 4 + 8
+    assert C.sizeof(L.fdtd_grid) == 6 * 4 + 8 + 8
     assert C.sizeof(L.fdtd_coeffs) == 12 * 8
     assert C.sizeof(L.fdtd_source) == 8 + 7 * 8
     assert C.sizeof(L.fdtd_probe) == 8 + 8 + 8

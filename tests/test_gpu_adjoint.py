@@ -144,3 +144,41 @@ def test_autograd_checkpointed_matches_oracle():
         ref_loss += float(np.sum((s.E[2][:, :, xp] - tgt[m]) ** 2))
     assert float(loss) == pytest.approx(ref_loss, rel=1e-12)
     assert np.allclose(theta.grad.numpy(), g_ref, rtol=1e-10, atol=1e-12 * np.abs(g_ref).max())
+
+
+def test_batched_2d_adjoint_gradient_is_the_sum_over_members():
+    shape = (64, 16, 3)
+    nx, ny, nz = shape
+    beta = np.zeros((3, 3))
+    beta[0, 1], beta[1, 0] = 0.02, -0.01
+    delta = np.array([-0.04, -0.02, 0.0])
+    dx = [1.0, 1.0, 1.0]
+    dt = 0.9 * D.dt_max(beta, delta, dx, 2)
+    fields = inputs.random_fields(shape, 31)
+    lam0 = inputs.random_fields(shape, 32)
+    n = 5
+    rng = np.random.default_rng(1)
+    tgt = rng.standard_normal((n, nz, ny))
+    sm = S.Simulation(shape, dx, dt, beta, delta, dims=2, dtype="f64", batched=True)
+    sm.set_state([torch.from_numpy(f) for f in fields])
+    sm.step(n, record=True)
+    sm.set_adjoint([torch.from_numpy(f) for f in lam0])
+    grad = torch.zeros(12, dtype=torch.float64, device="cuda")
+    probe = S.Probe(1, 7, torch.from_numpy(tgt).cuda())
+    sm.step_adjoint(n, grad, probe=probe)
+    lam = [t.cpu().numpy() for t in sm.get_adjoint()]
+    g = grad.cpu().numpy()
+    sm.close()
+    c = exact_coeffs(beta, delta, dx, dt, 2)
+    gb_sum, gd_sum = np.zeros((3, 3)), np.zeros(3)
+    for k in range(nz):
+        rl, gb, gd = oracle_adjoint(c, [f[k:k + 1] for f in fields], [f[k:k + 1] for f in lam0], n,
+                                    None, (1, 7, tgt[:, k:k + 1, :]))
+        assert rel_l2([x[k:k + 1] for x in lam], rl) <= 1e-12
+        gb_sum += gb
+        gd_sum += gd
+    scale = max(np.abs(gb_sum).max(), np.abs(gd_sum).max())
+    assert np.max(np.abs(g[:9].reshape(3, 3) - gb_sum)) <= 1e-11 * scale
+    assert np.max(np.abs(g[9:] - gd_sum)) <= 1e-11 * scale
+    # entries of the absent z axis are exactly zero
+    assert g[2] == 0 and g[5] == 0 and g[6] == 0 and g[7] == 0 and g[11] == 0

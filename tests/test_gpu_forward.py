@@ -223,3 +223,33 @@ def test_fused_kernel_bitwise_equals_reference_form(dtype, shape, monkeypatch):
         sm.close()
     for a, b in zip(*outs):
         assert torch.equal(a, b)
+
+
+@pytest.mark.parametrize("dtype,shape", [("f64", (64, 32, 4)), ("f32", (64, 32, 5)), ("f64", (36, 10, 3))])
+def test_batched_2d_equals_independent_runs(dtype, shape):
+    """batched = 1: the nz planes are independent 2D problems (z multipliers are zero)."""
+    nx, ny, nz = shape
+    beta = np.zeros((3, 3))
+    beta[0, 1], beta[1, 0] = 0.02, 0.03
+    delta = np.array([-0.03, -0.05, 0.0])
+    dx = [1.0, 1.0, 1.0]
+    dt = 0.9 * D.dt_max(beta, delta, dx, 2)
+    fields = inputs.random_fields(shape, seed=9)
+    sm = S.Simulation(shape, dx, dt, beta, delta, dims=2, dtype=dtype, batched=True,
+                      absorb_cells=3, absorb_sigma=0.2)
+    sm.set_state([torch.from_numpy(f) for f in fields])
+    sm.step(30)
+    got = [t.double().cpu().numpy() for t in sm.get_state()]
+    sm.close()
+    np_t = NP[dtype]
+    c = exact_coeffs(beta, delta, dx, dt, 2) if dtype == "f64" else \
+        rounded_coeffs(beta, delta, dx, dt, 2, np_t)
+    # the sponge acts on +-y only: the z axis is the batch axis
+    sp = F.sponge_profile(ny, 3, 0.2)[None, :, None] * np.ones((1, ny, nx))
+    if dtype == "f32":
+        sp = sp.astype(np.float32).astype(np.float64)
+    for k in range(nz):
+        f_k = [f[k:k + 1].astype(np_t).astype(np.float64) for f in fields]
+        ref = run_oracle(c, f_k, 30, sponge=sp)
+        err = rel_l2([g[k:k + 1] for g in got], ref)
+        assert err <= (1e-12 if dtype == "f64" else 2e-6), (k, err)

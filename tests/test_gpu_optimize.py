@@ -1,0 +1,62 @@
+"""GPU constrained minimisation (fdtd_coeff_update + disp_norm_eval) against the SLSQP oracle."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import dispersion as D
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+from paper_1710_06829_gb300 import _lib as L  # noqa: E402
+from paper_1710_06829_gb300 import optimize as O  # noqa: E402
+
+
+def test_coeff_update_kernel_is_the_projected_step():
+    tie = O.Tying.isotropic_3d(0.4)
+    theta = np.array([-0.05, -0.02, 0.03, 0.01])
+    g = np.linspace(-1.0, 1.0, 13)
+    lo, hi = np.full(4, -0.06), np.full(4, 0.06)
+    out = torch.empty(17, dtype=torch.float64, device="cuda")
+    L.fdtd_coeff_update(theta, g, tie.T, tie.c0, 0.05, lo, hi, out.data_ptr())
+    v = out.cpu().numpy()
+    th_ref = np.clip(theta - 0.05 * tie.T @ g, lo, hi)
+    assert np.allclose(v[:4], th_ref, rtol=0, atol=1e-15)
+    assert np.allclose(v[4:], tie.c0 + tie.T.T @ th_ref, rtol=0, atol=1e-15)
+
+
+def test_2d_minimum_matches_slsqp_oracle():
+    """Fixed c dt/dx = 0.5, beta_xy = beta_yx, delta_x = delta_y (Table 1 setting without Eq. beta)."""
+    nu, N = 0.5, (256, 256, 1)
+    tie = O.Tying.symmetric_2d(dt=nu)
+    lo, hi = np.array([-0.125, -0.125]), np.array([0.25, 0.125])
+    obj = O.NormObjective([1, 1, 1], 2, N)
+    theta, c, J, hist = O.minimise(obj, tie, [0.0, 0.0], lo, hi, iters=50)
+
+    def up(x):
+        beta = np.zeros((3, 3))
+        beta[0, 1] = beta[1, 0] = x[0]
+        return beta, np.array([x[1], x[1], 0.0]), nu
+    x, fs = D.minimise(up, [(-0.125, 0.25), (-0.125, 0.125)], [[0.0, 0.0], [0.1, -0.1]],
+                       [1, 1, 1], N, 2)
+    assert J <= 1.01 * fs
+    assert np.allclose(theta, x, atol=2e-3)
+
+
+def test_3d_isotropic_minimum_matches_slsqp_oracle():
+    """3D, theta = (delta_x, delta_perp, beta_x, beta_perp), fixed dt, uniform weight, small k-grid."""
+    N = (24, 24, 24)
+    beta0, delta0 = np.zeros((3, 3)), np.zeros(3)
+    dt = 0.5 * D.dt_max(beta0, delta0, [1, 1, 1], 3)
+    tie = O.Tying.isotropic_3d(dt)
+    lo, hi = np.full(4, -0.125), np.full(4, 0.125)
+    obj = O.NormObjective([1, 1, 1], 3, N)
+    theta, c, J, hist = O.minimise(obj, tie, np.zeros(4), lo, hi, iters=100)
+
+    def up(x):
+        beta = np.array([[0, x[2], x[2]], [x[2], 0, x[3]], [x[2], x[3], 0]])
+        return beta, np.array([x[0], x[1], x[1]]), dt
+    x, fs = D.minimise(up, [(-0.125, 0.125)] * 4, [np.zeros(4), np.array([-0.1, -0.1, 0.05, 0.0])],
+                       [1, 1, 1], N, 3)
+    assert J <= 1.01 * fs, (J, fs, theta, x)
