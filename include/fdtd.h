@@ -159,6 +159,31 @@ int fdtd_get_adjoint(fdtd_handle* h, void* const fields[6], int32_t mem);
  * applied as its own transpose.  On return the history is consumed. */
 int fdtd_step_adjoint(fdtd_handle* h, int32_t n, const fdtd_probe* probe, double* grad_dev);
 
+/* Diagnostics on the current state, FP64 accumulation, result in device memory
+ * (asynchronous on the handle's stream):
+ *   FDTD_DIAG_ENERGY:    params = {x_lo, x_len, margin}; out_dev[0] = (1/2) sum (E^2 + B^2) dV
+ *                        over cells with i in the periodic window [x_lo, x_lo + x_len) and
+ *                        margin <= j < ny - margin (and margin <= k < nz - margin when z is a
+ *                        spatial axis) -- field energy, e.g. the radiation behind a moving
+ *                        bunch (Sec. 6).
+ *   FDTD_DIAG_PLANEWAVE: params = {component 0..5, k_x, k_y, k_z}; out_dev[0..1] = Re, Im of
+ *                        sum_cells F exp(-i k . r) with r the component's staggered position
+ *                        (App. A); its phase advance per step measures the scheme's omega(k)
+ *                        of Eq. (dispersion_relation), Sec. 3.                          */
+#define FDTD_DIAG_ENERGY    0
+#define FDTD_DIAG_PLANEWAVE 1
+int fdtd_diagnostic(fdtd_handle* h, int32_t kind, const double* params, double* out_dev);
+
+/* Divergences of the current state, FP64, dense [nz][ny][nx] into out_dev (device):
+ *   FDTD_DIV_STAR_B: D* . B with the extended stencil (Eq. divstarb), conserved by the
+ *                    scheme for any coefficients (Sec. 2.1);
+ *   FDTD_DIV_YEE_B:  Yee D . B, conserved only under Eq. (beta) (Sec. 2.2);
+ *   FDTD_DIV_E:      Yee D . E at the nodes (Eq. divE; equals rho_E of App. A).        */
+#define FDTD_DIV_STAR_B 0
+#define FDTD_DIV_YEE_B  1
+#define FDTD_DIV_E      2
+int fdtd_divergence(fdtd_handle* h, int32_t which, double* out_dev);
+
 /* Block until all work on the handle's stream has finished; reports any
  * asynchronous CUDA error. */
 int fdtd_sync(fdtd_handle* h);

@@ -31,6 +31,11 @@ FDTD_SRC_BUNCH = 1
 FDTD_W_UNIFORM = 0
 FDTD_W_CONE_X = 1
 FDTD_W_GAUSS_Y = 2
+FDTD_DIAG_ENERGY = 0
+FDTD_DIAG_PLANEWAVE = 1
+FDTD_DIV_STAR_B = 0
+FDTD_DIV_YEE_B = 1
+FDTD_DIV_E = 2
 
 STATUS_NAMES = {0: "FDTD_OK", -1: "FDTD_EINVAL", -2: "FDTD_EUNSTABLE", -3: "FDTD_ECUDA",
                 -4: "FDTD_ENOMEM", -5: "FDTD_ENONFINITE", -6: "FDTD_ESTATE",
@@ -39,7 +44,7 @@ STATUS_NAMES = {0: "FDTD_OK", -1: "FDTD_EINVAL", -2: "FDTD_EUNSTABLE", -3: "FDTD
 # every symbol include/fdtd.h declares
 EXPORTS = ["fdtd_create", "fdtd_set_coeffs", "fdtd_set_state", "fdtd_get_state", "fdtd_get_step",
            "fdtd_step", "fdtd_checkpoint", "fdtd_set_adjoint", "fdtd_get_adjoint",
-           "fdtd_step_adjoint", "fdtd_sync", "fdtd_destroy", "disp_norm_eval",
+           "fdtd_step_adjoint", "fdtd_diagnostic", "fdtd_divergence", "fdtd_sync", "fdtd_destroy", "disp_norm_eval",
            "disp_norm_eval_noalloc", "fdtd_coeff_update", "fdtd_dt_max", "fdtd_last_error"]
 
 
@@ -97,6 +102,8 @@ def load():
     lib.fdtd_set_adjoint.argtypes = [P, C.POINTER(P), I32]
     lib.fdtd_get_adjoint.argtypes = [P, C.POINTER(P), I32]
     lib.fdtd_step_adjoint.argtypes = [P, I32, C.POINTER(fdtd_probe), P]
+    lib.fdtd_diagnostic.argtypes = [P, I32, pd, P]
+    lib.fdtd_divergence.argtypes = [P, I32, P]
     lib.fdtd_sync.argtypes = [P]
     lib.fdtd_destroy.argtypes = [P]
     lib.fdtd_destroy.restype = None
@@ -188,6 +195,15 @@ def fdtd_get_adjoint(h, fields, mem):
 def fdtd_step_adjoint(h, n, probe=None, grad_dev=None):
     check(load().fdtd_step_adjoint(h, int(n), C.byref(probe) if probe is not None else None,
                                    C.c_void_p(grad_dev)))
+
+
+def fdtd_diagnostic(h, kind, params, out_dev):
+    check(load().fdtd_diagnostic(h, int(kind), (C.c_double * len(params))(*map(float, params)),
+                                 C.c_void_p(out_dev)))
+
+
+def fdtd_divergence(h, which, out_dev):
+    check(load().fdtd_divergence(h, int(which), C.c_void_p(out_dev)))
 
 
 def fdtd_sync(h):

@@ -34,6 +34,16 @@ void launch_disp_norm(const double alpha[3], const double beta[3][3], const doub
                       double dt, const double dx[3], int dims, const int N[3], int weight,
                       double wparam, double* scratch, double** out_dev, cudaStream_t st);
 size_t norm_scratch_doubles(const int N[3], long long npts);
+int diag_blocks(const Geom& g);
+template <typename T>
+void launch_energy(const Geom& g, FieldSet<T> s, int x_lo, int x_len, int my, int mz, double dV,
+                   double* part, double* out, cudaStream_t st);
+template <typename T>
+void launch_planewave(const Geom& g, const T* F, const double k[3], const double off[3],
+                      double* part, double* out, cudaStream_t st);
+template <typename T>
+void launch_divergence(const Geom& g, const Mult<double>& w, FieldSet<T> s, int which, double* out,
+                       cudaStream_t st);
 
 // ---------------------------------------------------------------------------
 // coefficient preprocessing
@@ -219,6 +229,7 @@ struct fdtd_handle {
     char* staging;      // one dense array
     long long step;
     int use_fused;
+    double* dpart;      // diagnostics partials (2 per block)
     FusedPlan* plan;    // TMA descriptors of both state sets (nullptr: reference-form kernels)
     int* err_dev;       // raised by a kernel whose bounded wait expired
 
@@ -773,6 +784,58 @@ int fdtd_step_adjoint(fdtd_handle* h, int32_t n, const fdtd_probe* probe, double
     return adjoint_impl<double>(h, n, probe, grad_dev);
 }
 
+static int ensure_dpart(fdtd_handle* h) {
+    if (h->dpart) return FDTD_OK;
+    CK(cudaMalloc(&h->dpart, (size_t)diag_blocks(h->g) * 2 * sizeof(double)));
+    return FDTD_OK;
+}
+
+int fdtd_diagnostic(fdtd_handle* h, int32_t kind, const double* params, double* out_dev) {
+    if (!h || !params || !out_dev) { set_error("fdtd_diagnostic: NULL argument"); return FDTD_EINVAL; }
+    int rc = ensure_dpart(h);
+    if (rc) return rc;
+    const Geom& g = h->g;
+    const bool f32 = h->grid.dtype == FDTD_F32;
+    if (kind == FDTD_DIAG_ENERGY) {
+        const int x_lo = (int)params[0], x_len = (int)params[1], margin = (int)params[2];
+        // the margin trims y always and z when z is a spatial axis (nz > 1, not batched)
+        const int my = margin, mz = (g.nz > 1 && !h->grid.batched) ? margin : 0;
+        if (x_len < 1 || x_len > g.nx || margin < 0 || 2 * my >= g.ny || 2 * mz >= g.nz) {
+            set_error("fdtd_diagnostic: bad energy window");
+            return FDTD_EINVAL;
+        }
+        const double dV = h->dx[0] * h->dx[1] * h->dx[2];
+        if (f32) launch_energy<float>(g, fieldset<float>(h, h->cur), x_lo, x_len, my, mz, dV, h->dpart, out_dev, h->stream);
+        else launch_energy<double>(g, fieldset<double>(h, h->cur), x_lo, x_len, my, mz, dV, h->dpart, out_dev, h->stream);
+    } else if (kind == FDTD_DIAG_PLANEWAVE) {
+        const int comp = (int)params[0];
+        if (comp < 0 || comp > 5) { set_error("fdtd_diagnostic: component must be 0..5"); return FDTD_EINVAL; }
+        static const double offs[6][3] = {{0.5, 0, 0}, {0, 0.5, 0}, {0, 0, 0.5},
+                                          {0, 0.5, 0.5}, {0.5, 0, 0.5}, {0.5, 0.5, 0}};
+        const double kd[3] = {params[1] * h->dx[0], params[2] * h->dx[1], params[3] * h->dx[2]};
+        if (f32) launch_planewave<float>(g, (const float*)h->arr(h->cur, comp), kd, offs[comp], h->dpart, out_dev, h->stream);
+        else launch_planewave<double>(g, (const double*)h->arr(h->cur, comp), kd, offs[comp], h->dpart, out_dev, h->stream);
+    } else {
+        set_error("fdtd_diagnostic: unknown kind %d", kind);
+        return FDTD_EINVAL;
+    }
+    CK(cudaGetLastError());
+    return FDTD_OK;
+}
+
+int fdtd_divergence(fdtd_handle* h, int32_t which, double* out_dev) {
+    if (!h || !out_dev || which < 0 || which > 2) {
+        set_error("fdtd_divergence: bad argument");
+        return FDTD_EINVAL;
+    }
+    // multipliers of the difference operators themselves (1/dx_a, not dt/dx_a)
+    const Mult<double> w = make_mult<double>(h->cc, h->dx, 1.0, !h->grid.batched);
+    if (h->grid.dtype == FDTD_F32) launch_divergence<float>(h->g, w, fieldset<float>(h, h->cur), which, out_dev, h->stream);
+    else launch_divergence<double>(h->g, w, fieldset<double>(h, h->cur), which, out_dev, h->stream);
+    CK(cudaGetLastError());
+    return FDTD_OK;
+}
+
 int fdtd_sync(fdtd_handle* h) {
     if (!h) { set_error("NULL handle"); return FDTD_EINVAL; }
     CK(cudaStreamSynchronize(h->stream));
@@ -798,6 +861,7 @@ void fdtd_destroy(fdtd_handle* h) {
     if (h->partials) cudaFree(h->partials);
     if (h->staging) cudaFree(h->staging);
     if (h->err_dev) cudaFree(h->err_dev);
+    if (h->dpart) cudaFree(h->dpart);
     if (h->plan) fused_plan_destroy(h->plan);
     for (char* p : h->ckpt)
         if (p) cudaFree(p);

@@ -146,6 +146,26 @@ class Simulation:
         assert grad.is_cuda and grad.dtype == torch.float64 and grad.numel() >= 12
         L.fdtd_step_adjoint(self.h, n, probe.s if probe is not None else None, grad.data_ptr())
 
+    # -- diagnostics -----------------------------------------------------------
+    def energy(self, x_lo, x_len, margin=0, out=None):
+        """(1/2) sum (E^2 + B^2) dV over a periodic x-window (FP64, device tensor of 1)."""
+        out = out if out is not None else torch.empty(1, dtype=torch.float64, device="cuda")
+        L.fdtd_diagnostic(self.h, L.FDTD_DIAG_ENERGY, [x_lo, x_len, margin], out.data_ptr())
+        return out
+
+    def plane_wave(self, component, k, out=None):
+        """sum F exp(-i k.r) over the grid: device tensor (Re, Im)."""
+        out = out if out is not None else torch.empty(2, dtype=torch.float64, device="cuda")
+        L.fdtd_diagnostic(self.h, L.FDTD_DIAG_PLANEWAVE, [component, *k], out.data_ptr())
+        return out
+
+    def divergence(self, which):
+        """Dense FP64 divergence field (nz, ny, nx): L.FDTD_DIV_STAR_B / _YEE_B / _E."""
+        out = torch.empty(self.shape, dtype=torch.float64, device="cuda")
+        L.fdtd_divergence(self.h, which, out.data_ptr())
+        self.stream.synchronize()
+        return out
+
     def sync(self):
         L.fdtd_sync(self.h)
 
