@@ -41,7 +41,7 @@ def parse():
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--n", type=int, default=N_CELLS)
-    p.add_argument("--part", default="all", choices=["all", "fwd32"],
+    p.add_argument("--part", default="all", choices=["all", "fwd32", "adj32"],
                    help="fwd32: run only the FP32 forward steps (profiling driver); prints a "
                         "short line that is not a bench result")
     return p.parse_args()
@@ -302,6 +302,11 @@ def run_ours(args):
     t_adj = time_events(lambda: sm.step_adjoint(seg, grad), 1, stream)
     t_adj = barrier_max(t_adj, world)
     adj = world * cells * seg / t_adj / 1e9
+    if args.part == "adj32":
+        sm.close()
+        if rank == 0:
+            print(json.dumps({"part": "adj32", "gcells_per_s": adj, "ms_per_step": t_adj / seg * 1e3}))
+        return
 
     # --- end to end through the C ABI with host buffers: upload, 100 steps, download
     n_inner = 20
@@ -332,6 +337,10 @@ def run_ours(args):
     fwd64 = world * cells * k64 / t64 / 1e9
     sm64.close()
 
+    # --- dispersion norm + gradient over the 256^3 k-grid (FP64 per point and accumulation)
+    t_norm = time_events(lambda: S.disp_norm(beta, delta, dt, [1, 1, 1], 3, (n, n, n)), 3, stream)
+    norm_rate = cells * 3 / t_norm / 1e9
+
     if rank != 0:
         return
     peak, peak_kind = peaks()
@@ -345,6 +354,8 @@ def run_ours(args):
                    "(state 6 x 4 B x 256^3 = 403 MB per copy)", "parallelism": f"replicas x{world}"},
         "adjoint": {"value": adj, "unit": "Gcell-updates/s", "steps": seg,
                     "roofline_frac": BYTES_ADJ32 * cells * seg / t_adj / 1e9 / peak},
+        "dispersion_norm": {"value": norm_rate, "unit": "Gpoint/s", "grid": [n, n, n],
+                            "note": "value and 13-entry gradient, FP64"},
         "fp64_forward": {"value": fwd64, "unit": "Gcell-updates/s",
                          "roofline_frac": BYTES_FWD64 * cells * k64 / t64 / 1e9 / peak},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",

@@ -68,69 +68,87 @@ __device__ __forceinline__ void dcoef(const T* __restrict__ F, long long c, long
 constexpr int ADJ_THREADS = 256;
 
 int adjoint_B_blocks(const Geom& g) {
-    const long long cells = (long long)g.nx * g.ny * g.nz;
-    long long b = (cells + ADJ_THREADS - 1) / ADJ_THREADS;
+    long long b = (long long)g.ny * g.nz;   // one x-row per block and sweep
     if (b > 152 * 8) b = 152 * 8;
     return (int)b;
 }
 
 // partials layout: [block][9] = per axis a (x, y, z): d/d delta_a, d/d beta_a,b1, d/d beta_a,b2
 // with b1 < b2 the two other axes.  Accumulated across steps (+=) by the owning block.
+// A block walks whole x-rows (j, k); each thread sums at most ADJ_FLUSH cell terms in the
+// field precision before adding them to its FP64 accumulators, so the FP64 pipe (slow on
+// this part) sees one add per ADJ_FLUSH cells; block and grid totals are FP64.
+constexpr int ADJ_FLUSH = 16;
+
 template <typename T>
 __global__ void __launch_bounds__(ADJ_THREADS)
 adjoint_B_kernel(Geom g, Mult<T> m, FieldSet<T> lam, const T* __restrict__ Ex,
                  const T* __restrict__ Ey, const T* __restrict__ Ez, const T* __restrict__ spy,
                  const T* __restrict__ spz, double* __restrict__ partials) {
     double acc[9];
+    T racc[9];
 #pragma unroll
-    for (int q = 0; q < 9; ++q) acc[q] = 0.0;
-    const long long cells = (long long)g.nx * g.ny * g.nz;
+    for (int q = 0; q < 9; ++q) {
+        acc[q] = 0.0;
+        racc[q] = T(0);
+    }
+    int cnt = 0;
+    const int rows = g.ny * g.nz;
     const long long Y = g.nxp;
-    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < cells;
-         t += (long long)gridDim.x * blockDim.x) {
-        const int i = (int)(t % g.nx);
-        const long long r = t / g.nx;
-        const int j = (int)(r % g.ny);
-        const int k = (int)(r / g.ny);
-        const long long c = pidx(g, i, j, k);
+    const T* lEx = lam.c[0];
+    const T* lEy = lam.c[1];
+    const T* lEz = lam.c[2];
+    for (int r = blockIdx.x; r < rows; r += gridDim.x) {
+        const int j = r % g.ny, k = r / g.ny;
+        const long long rowbase = pidx(g, 0, j, k);
         const long long zp1 = zoff_a(g, k, 1), zm1 = zoff_a(g, k, -1), zp2 = zoff_a(g, k, 2);
-        const T* lEx = lam.c[0];
-        const T* lEy = lam.c[1];
-        const T* lEz = lam.c[2];
         // l_E = S lambda_E at the cell and its +x, +y, +z neighbours
         const T s0 = sp_at(g, spy, spz, j, k);
         const T sxp = s0;
         const T syp = sp_at(g, spy, spz, j + 1, k);
         const T szp = sp_at(g, spy, spz, j, k + 1);
-        const T ex0 = s0 * lEx[c], ey0 = s0 * lEy[c], ez0 = s0 * lEz[c];
-        // G^T l_E (transposed backward differences = forward differences with a minus sign)
-        T nx_ = lam.c[3][c] + (m.cE[2] * (ey0 - szp * lEy[c + zp1]) - m.cE[1] * (ez0 - syp * lEz[c + Y]));
-        T ny_ = lam.c[4][c] + (m.cE[0] * (ez0 - sxp * lEz[c + 1]) - m.cE[2] * (ex0 - szp * lEx[c + zp1]));
-        T nz_ = lam.c[5][c] + (m.cE[1] * (ex0 - syp * lEx[c + Y]) - m.cE[0] * (ey0 - sxp * lEy[c + 1]));
-        const T mux = s0 * nx_, muy = s0 * ny_, muz = s0 * nz_;
-        // gradient: axis x appears as +mu_y D*_x E_z - mu_z D*_x E_y
-        T d0, d1, d2, e0, e1, e2;
-        dcoef(Ez, c, 1, 2, -1, Y, -Y, zp1, zm1, d0, d1, d2);
-        dcoef(Ey, c, 1, 2, -1, Y, -Y, zp1, zm1, e0, e1, e2);
-        acc[0] += (double)(muy * d0) - (double)(muz * e0);
-        acc[1] += (double)(muy * d1) - (double)(muz * e1);
-        acc[2] += (double)(muy * d2) - (double)(muz * e2);
-        // axis y: +mu_z D*_y E_x - mu_x D*_y E_z   (transverse order x, z)
-        dcoef(Ex, c, Y, 2 * Y, -Y, 1, -1, zp1, zm1, d0, d1, d2);
-        dcoef(Ez, c, Y, 2 * Y, -Y, 1, -1, zp1, zm1, e0, e1, e2);
-        acc[3] += (double)(muz * d0) - (double)(mux * e0);
-        acc[4] += (double)(muz * d1) - (double)(mux * e1);
-        acc[5] += (double)(muz * d2) - (double)(mux * e2);
-        // axis z: +mu_x D*_z E_y - mu_y D*_z E_x   (transverse order x, y)
-        dcoef(Ey, c, zp1, zp2, zm1, 1, -1, Y, -Y, d0, d1, d2);
-        dcoef(Ex, c, zp1, zp2, zm1, 1, -1, Y, -Y, e0, e1, e2);
-        acc[6] += (double)(mux * d0) - (double)(muy * e0);
-        acc[7] += (double)(mux * d1) - (double)(muy * e1);
-        acc[8] += (double)(mux * d2) - (double)(muy * e2);
-        store_images_a(g, lam.c[3], i, j, k, mux);
-        store_images_a(g, lam.c[4], i, j, k, muy);
-        store_images_a(g, lam.c[5], i, j, k, muz);
+        for (int i = threadIdx.x; i < g.nx; i += blockDim.x) {
+            const long long c = rowbase + i;
+            const T ex0 = s0 * lEx[c], ey0 = s0 * lEy[c], ez0 = s0 * lEz[c];
+            // G^T l_E (transposed backward differences = forward differences with a minus sign)
+            T nx_ = lam.c[3][c] + (m.cE[2] * (ey0 - szp * lEy[c + zp1]) - m.cE[1] * (ez0 - syp * lEz[c + Y]));
+            T ny_ = lam.c[4][c] + (m.cE[0] * (ez0 - sxp * lEz[c + 1]) - m.cE[2] * (ex0 - szp * lEx[c + zp1]));
+            T nz_ = lam.c[5][c] + (m.cE[1] * (ex0 - syp * lEx[c + Y]) - m.cE[0] * (ey0 - sxp * lEy[c + 1]));
+            const T mux = s0 * nx_, muy = s0 * ny_, muz = s0 * nz_;
+            // gradient: axis x appears as +mu_y D*_x E_z - mu_z D*_x E_y
+            T d0, d1, d2, e0, e1, e2;
+            dcoef(Ez, c, 1, 2, -1, Y, -Y, zp1, zm1, d0, d1, d2);
+            dcoef(Ey, c, 1, 2, -1, Y, -Y, zp1, zm1, e0, e1, e2);
+            racc[0] += muy * d0 - muz * e0;
+            racc[1] += muy * d1 - muz * e1;
+            racc[2] += muy * d2 - muz * e2;
+            // axis y: +mu_z D*_y E_x - mu_x D*_y E_z   (transverse order x, z)
+            dcoef(Ex, c, Y, 2 * Y, -Y, 1, -1, zp1, zm1, d0, d1, d2);
+            dcoef(Ez, c, Y, 2 * Y, -Y, 1, -1, zp1, zm1, e0, e1, e2);
+            racc[3] += muz * d0 - mux * e0;
+            racc[4] += muz * d1 - mux * e1;
+            racc[5] += muz * d2 - mux * e2;
+            // axis z: +mu_x D*_z E_y - mu_y D*_z E_x   (transverse order x, y)
+            dcoef(Ey, c, zp1, zp2, zm1, 1, -1, Y, -Y, d0, d1, d2);
+            dcoef(Ex, c, zp1, zp2, zm1, 1, -1, Y, -Y, e0, e1, e2);
+            racc[6] += mux * d0 - muy * e0;
+            racc[7] += mux * d1 - muy * e1;
+            racc[8] += mux * d2 - muy * e2;
+            if (++cnt == ADJ_FLUSH) {
+#pragma unroll
+                for (int q = 0; q < 9; ++q) {
+                    acc[q] += (double)racc[q];
+                    racc[q] = T(0);
+                }
+                cnt = 0;
+            }
+            store_images_a(g, lam.c[3], i, j, k, mux);
+            store_images_a(g, lam.c[4], i, j, k, muy);
+            store_images_a(g, lam.c[5], i, j, k, muz);
+        }
     }
+#pragma unroll
+    for (int q = 0; q < 9; ++q) acc[q] += (double)racc[q];
     __shared__ double red[ADJ_THREADS / 32][9];
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
 #pragma unroll

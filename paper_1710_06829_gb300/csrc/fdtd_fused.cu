@@ -290,6 +290,11 @@ static bool encode(CUtensorMap* map, const Geom& g, T* base, int bw, int bh) {
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// E^n box (72 x 12, FP32) of one padded array, as the adjoint kernel reads it
+bool encode_ebox_f32(CUtensorMap* map, const Geom& g, float* base) {
+    return encode<float>(map, g, base, Layout<float>::EW, Layout<float>::EH);
+}
+
 template <typename T>
 FusedPlan* fused_plan_create(const Geom& g, T* const set0[6], T* const set1[6]) {
     if (!fused_supported<T>(g)) return nullptr;

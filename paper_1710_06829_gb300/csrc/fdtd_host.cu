@@ -12,9 +12,10 @@
 #include <cstring>
 #include <mutex>
 #include <new>
+#include <type_traits>
 #include <vector>
 
-#include "fdtd_internal.cuh"
+#include "fdtd_tma.cuh"
 
 namespace fdtd {
 
@@ -35,6 +36,13 @@ void launch_disp_norm(const double alpha[3], const double beta[3][3], const doub
                       double wparam, double* scratch, double** out_dev, cudaStream_t st);
 size_t norm_scratch_doubles(const int N[3], long long npts);
 int diag_blocks(const Geom& g);
+bool encode_ebox_f32(CUtensorMap* map, const Geom& g, float* base);
+bool adjoint32_supported(const Geom& g);
+int adjoint32_blocks(const Geom& g);
+bool adjoint32_prepare();
+void launch_adjoint32_B(const FusedMaps& maps, const Geom& g, const Mult<float>& m,
+                        FieldSet<float> lam, const float* spy, const float* spz, double* partials,
+                        int* err, cudaStream_t st);
 template <typename T>
 void launch_energy(const Geom& g, FieldSet<T> s, int x_lo, int x_len, int my, int mz, double dV,
                    double* part, double* out, cudaStream_t st);
@@ -230,6 +238,7 @@ struct fdtd_handle {
     long long step;
     int use_fused;
     double* dpart;      // diagnostics partials (2 per block)
+    std::vector<FusedMaps> hist_maps;   // TMA descriptors of each history snapshot (FP32 adjoint)
     FusedPlan* plan;    // TMA descriptors of both state sets (nullptr: reference-form kernels)
     int* err_dev;       // raised by a kernel whose bounded wait expired
 
@@ -554,9 +563,19 @@ int fdtd_get_adjoint(fdtd_handle* h, void* const fields[6], int32_t mem) {
 static int ensure_hist(fdtd_handle* h, int snaps) {
     if (h->hist_cap >= snaps) return FDTD_OK;
     if (h->hist) { cudaFree(h->hist); h->hist = nullptr; h->hist_cap = 0; }
+    h->hist_maps.clear();
     const size_t arr = (size_t)h->g.total * h->esz;
     CK(cudaMalloc(&h->hist, (size_t)snaps * 3 * arr));
     h->hist_cap = snaps;
+    if (h->grid.dtype == FDTD_F32 && h->plan && adjoint32_supported(h->g) && adjoint32_prepare()) {
+        h->hist_maps.resize(snaps);
+        for (int s = 0; s < snaps; ++s)
+            for (int c = 0; c < 3; ++c)
+                if (!encode_ebox_f32(&h->hist_maps[s].e[c], h->g, (float*)h->hist_arr(s, c))) {
+                    h->hist_maps.clear();
+                    return FDTD_OK;   // the reference-form adjoint kernels will be used
+                }
+    }
     return FDTD_OK;
 }
 
@@ -720,7 +739,8 @@ static int adjoint_impl(fdtd_handle* h, int n, const fdtd_probe* probe, double* 
     }
     int rc = ensure_lam(h);
     if (rc) return rc;
-    const int nblk = adjoint_B_blocks(g);
+    const bool staged = std::is_same<T, float>::value && !h->hist_maps.empty();
+    const int nblk = staged ? adjoint32_blocks(g) : adjoint_B_blocks(g);
     if (h->npart < nblk) {
         if (h->partials) cudaFree(h->partials);
         h->partials = nullptr;
@@ -742,7 +762,15 @@ static int adjoint_impl(fdtd_handle* h, int n, const fdtd_probe* probe, double* 
         }
         const T* E[3] = {(const T*)h->hist_arr(snap_before, 0), (const T*)h->hist_arr(snap_before, 1),
                          (const T*)h->hist_arr(snap_before, 2)};
-        launch_adjoint_B_v0<T>(g, m, lam, E, spy, spz, h->partials, nblk, h->stream);
+        if constexpr (std::is_same<T, float>::value) {
+            if (staged)
+                launch_adjoint32_B(h->hist_maps[snap_before], g, m, lam, spy, spz, h->partials,
+                                   h->err_dev, h->stream);
+            else
+                launch_adjoint_B_v0<T>(g, m, lam, E, spy, spz, h->partials, nblk, h->stream);
+        } else {
+            launch_adjoint_B_v0<T>(g, m, lam, E, spy, spz, h->partials, nblk, h->stream);
+        }
         launch_adjoint_E_v0<T>(g, m, lam, spy, spz, h->stream);
         CK(cudaGetLastError());
     }

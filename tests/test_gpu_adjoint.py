@@ -182,3 +182,64 @@ def test_batched_2d_adjoint_gradient_is_the_sum_over_members():
     assert np.max(np.abs(g[9:] - gd_sum)) <= 1e-11 * scale
     # entries of the absent z axis are exactly zero
     assert g[2] == 0 and g[5] == 0 and g[6] == 0 and g[7] == 0 and g[11] == 0
+
+
+@pytest.mark.parametrize("shape,sponge", [((64, 16, 12), False), ((128, 24, 40), True), ((64, 8, 1), False)])
+def test_adjoint_fp32_staged_kernel_matches_oracle(shape, sponge):
+    """FP32 adjoint on TMA-eligible grids (nx % 64 == 0, ny % 8 == 0) vs the oracle adjoint run
+    with the FP32-rounded multipliers; 40 planes leave a ragged last z-chunk."""
+    beta, delta = admissible_theta(9)
+    dx = [1.0, 1.0, 1.0]
+    dt = 0.9 * D.dt_max(beta, delta, dx, 3)
+    fields = [f.astype(np.float32) for f in inputs.random_fields(shape, 41)]
+    lam0 = [f.astype(np.float32) for f in inputs.random_fields(shape, 42)]
+    n = 6
+    nx, ny, nz = shape
+    kw = dict(absorb_cells=4, absorb_sigma=0.3) if sponge else {}
+    sp = F.sponge_factor((nz, ny, nx), 4, 0.3).astype(np.float32).astype(np.float64) if sponge else None
+    rng = np.random.default_rng(5)
+    probe = (0, 9, rng.standard_normal((n, nz, ny)).astype(np.float32))
+    lam, gb, gd = gpu_adjoint(shape, dx, dt, beta, delta, "f32", fields, lam0, n, probe, **kw)
+    f64 = [f.astype(np.float64) for f in fields]
+    l64 = [f.astype(np.float64) for f in lam0]
+    rlam, rgb, rgd = oracle_adjoint(rounded_coeffs(beta, delta, dx, dt, 3, np.float32), f64, l64, n,
+                                    sp, (probe[0], probe[1], probe[2].astype(np.float64)))
+    assert rel_l2(lam, rlam) <= 5e-6
+    scale = max(np.abs(rgb).max(), np.abs(rgd).max())
+    assert np.max(np.abs(gb - rgb)) <= 2e-5 * scale
+    assert np.max(np.abs(gd - rgd)) <= 2e-5 * scale
+
+
+def test_adjoint_fp32_staged_vs_fp64_finite_differences():
+    """FP32 fields + FP64 gradient reduction on a TMA-eligible grid vs FP64 central differences."""
+    shape = (64, 16, 16)
+    beta, delta = admissible_theta(8)
+    dx = [1.0, 1.0, 1.0]
+    dt = 0.9 * D.dt_max(beta, delta, dx, 3)
+    fields = inputs.random_fields(shape, 21)
+    n = 10
+    nx, ny, nz = shape
+    tgt = np.zeros((n, nz, ny))
+    lam0 = [np.zeros((nz, ny, nx))] * 6
+    lam, gb, gd = gpu_adjoint(shape, dx, dt, beta, delta, "f32",
+                              [f.astype(np.float32) for f in fields], lam0, n, (2, 5, tgt))
+
+    def loss(b, d):
+        s = F.State(fields[:3], fields[3:])
+        c = exact_coeffs(b, d, dx, dt, 3)
+        tot = 0.0
+        for m in range(n):
+            F.step(s, c)
+            tot += float(np.sum((s.E[2][:, :, 5] - tgt[m]) ** 2))
+        return tot
+    h = 1e-4
+    for (i, j) in [(0, 1), (1, 2), (2, 0)]:
+        bp, bm = beta.copy(), beta.copy()
+        bp[i, j] += h
+        bm[i, j] -= h
+        assert gb[i, j] == pytest.approx((loss(bp, delta) - loss(bm, delta)) / (2 * h), rel=1e-4)
+    for i in range(3):
+        dp, dm = delta.copy(), delta.copy()
+        dp[i] += h
+        dm[i] -= h
+        assert gd[i] == pytest.approx((loss(beta, dp) - loss(beta, dm)) / (2 * h), rel=1e-4)
