@@ -332,7 +332,7 @@ def run_ours(args):
     sm64.set_state([torch.from_numpy(f) for f in fields64])
     for _ in range(3):
         sm64.step(1)
-    k64 = max(3, args.steps // 5)
+    k64 = max(3, args.steps // 50)
     t64 = barrier_max(time_events(lambda: sm64.step(1), k64, stream), world)
     fwd64 = world * cells * k64 / t64 / 1e9
     sm64.close()

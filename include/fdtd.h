@@ -202,6 +202,13 @@ int disp_norm_eval(const fdtd_coeffs* coeffs, double dt, const double dx[3], int
                    const int32_t N[3], int32_t weight, double weight_param, double* out,
                    void* stream);
 
+/* omega(k) of Eq. (dispersion_relation), omega = (2/dt) asin(dt sqrt(sum_i s_i^2 A_i)), at n
+ * wave vectors (k_dev: device, n x 3 doubles, row-major; axes beyond dims ignored) into
+ * omega_dev (device, n doubles).  FP64.  Validates Eq. (constraints) like disp_norm_eval.
+ * Phase velocity is omega/|k| (Sec. 5); asynchronous on `stream`. */
+int disp_omega_eval(const fdtd_coeffs* coeffs, double dt, const double dx[3], int32_t dims,
+                    const double* k_dev, int32_t n, double* omega_dev, void* stream);
+
 /* disp_norm_eval without any device allocation.  The paper has no counterpart:
  * this is a library service for callers that may not allocate device memory
  * when they need the norm (for instance while another stream of the device is

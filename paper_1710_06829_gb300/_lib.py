@@ -45,7 +45,7 @@ STATUS_NAMES = {0: "FDTD_OK", -1: "FDTD_EINVAL", -2: "FDTD_EUNSTABLE", -3: "FDTD
 EXPORTS = ["fdtd_create", "fdtd_set_coeffs", "fdtd_set_state", "fdtd_get_state", "fdtd_get_step",
            "fdtd_step", "fdtd_checkpoint", "fdtd_set_adjoint", "fdtd_get_adjoint",
            "fdtd_step_adjoint", "fdtd_diagnostic", "fdtd_divergence", "fdtd_sync", "fdtd_destroy", "disp_norm_eval",
-           "disp_norm_eval_noalloc", "fdtd_coeff_update", "fdtd_dt_max", "fdtd_last_error"]
+           "disp_norm_eval_noalloc", "disp_omega_eval", "fdtd_coeff_update", "fdtd_dt_max", "fdtd_last_error"]
 
 
 class FdtdError(RuntimeError):
@@ -110,6 +110,7 @@ def load():
     lib.disp_norm_eval.argtypes = [C.POINTER(fdtd_coeffs), D, pd, I32, C.POINTER(I32), I32, D,
                                    pd, P]
     lib.disp_norm_eval_noalloc.argtypes = lib.disp_norm_eval.argtypes
+    lib.disp_omega_eval.argtypes = [C.POINTER(fdtd_coeffs), D, pd, I32, P, I32, P, P]
     lib.fdtd_coeff_update.argtypes = [I32, pd, pd, pd, pd, D, pd, pd, P, P]
     lib.fdtd_dt_max.argtypes = [C.POINTER(fdtd_coeffs), pd, I32, pd, pd, pd]
     lib.fdtd_last_error.restype = C.c_char_p
@@ -230,6 +231,11 @@ def disp_norm_eval_noalloc(coeffs, dt, dx, dims, N, weight=FDTD_W_UNIFORM, weigh
     check(load().disp_norm_eval_noalloc(C.byref(coeffs), float(dt), _d3(dx), int(dims), n3,
                                         int(weight), float(weight_param), out, C.c_void_p(stream)))
     return list(out)
+
+
+def disp_omega_eval(coeffs, dt, dx, dims, k_dev, n, omega_dev, stream=0):
+    check(load().disp_omega_eval(C.byref(coeffs), float(dt), _d3(dx), int(dims), C.c_void_p(k_dev),
+                                 int(n), C.c_void_p(omega_dev), C.c_void_p(stream)))
 
 
 def fdtd_coeff_update(theta, grad13, T, c0, eta, lo, hi, out_dev, stream=0):

@@ -32,7 +32,8 @@ class ProbeLossProblem:
             self.sim = S.Simulation(self.shape, self.dx, self.dt, beta, delta, dims=self.dims,
                                     dtype=self.dtype, absorb_cells=self.absorb[0],
                                     absorb_sigma=self.absorb[1])
-            self.probe = S.Probe(self.component, self.x_index, self.target)
+            self.probe = S.Probe(self.component, self.x_index,
+                                 self.target.to(device="cuda", dtype=self.sim.tdtype).contiguous())
         else:
             self.sim.set_coeffs(self.dt, beta, delta)
         return self.sim

@@ -199,3 +199,44 @@ void launch_disp_norm(const double alpha[3], const double beta[3][3], const doub
 }
 
 }  // namespace fdtd
+
+namespace fdtd {
+
+// omega(k) of Eq. (dispersion_relation) at n arbitrary wave vectors (FP64 per point).
+__global__ void omega_kernel(NormParams p, double dx0, double dx1, double dx2,
+                             const double* __restrict__ k, int n, double* __restrict__ out) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const double dxa[3] = {dx0, dx1, dx2};
+    double s2[3], c[3];
+    for (int i = 0; i < 3; ++i) {
+        const double ki = i < p.dims ? k[3 * t + i] : 0.0;
+        const double sn = sin(0.5 * ki * dxa[i]) / dxa[i];
+        s2[i] = sn * sn;
+        c[i] = cos(ki * dxa[i]);
+    }
+    double S = 0.0;
+    for (int i = 0; i < 3; ++i) {
+        double A = p.alpha[i] + p.delta[i] * (1.0 + 2.0 * c[i]);
+        for (int j = 0; j < 3; ++j)
+            if (j != i) A += 2.0 * p.beta[i][j] * c[j];
+        S += s2[i] * A;
+    }
+    out[t] = 2.0 / p.dt * asin(p.dt * sqrt(S));
+}
+
+void launch_omega(const double alpha[3], const double beta[3][3], const double delta[3], double dt,
+                  const double dx[3], int dims, const double* k_dev, int n, double* out_dev,
+                  cudaStream_t st) {
+    NormParams p;
+    for (int i = 0; i < 3; ++i) {
+        p.alpha[i] = alpha[i];
+        p.delta[i] = delta[i];
+        for (int j = 0; j < 3; ++j) p.beta[i][j] = beta[i][j];
+    }
+    p.dt = dt;
+    p.dims = dims;
+    omega_kernel<<<(n + 127) / 128, 128, 0, st>>>(p, dx[0], dx[1], dx[2], k_dev, n, out_dev);
+}
+
+}  // namespace fdtd

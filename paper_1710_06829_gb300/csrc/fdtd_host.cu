@@ -36,6 +36,9 @@ void launch_disp_norm(const double alpha[3], const double beta[3][3], const doub
                       double wparam, double* scratch, double** out_dev, cudaStream_t st);
 size_t norm_scratch_doubles(const int N[3], long long npts);
 int diag_blocks(const Geom& g);
+void launch_omega(const double alpha[3], const double beta[3][3], const double delta[3], double dt,
+                  const double dx[3], int dims, const double* k_dev, int n, double* out_dev,
+                  cudaStream_t st);
 bool encode_ebox_f32(CUtensorMap* map, const Geom& g, float* base);
 bool adjoint32_supported(const Geom& g);
 int adjoint32_blocks(const Geom& g);
@@ -937,6 +940,23 @@ int disp_norm_eval(const fdtd_coeffs* coeffs, double dt, const double dx[3], int
     return FDTD_OK;
 }
 
+
+int disp_omega_eval(const fdtd_coeffs* coeffs, double dt, const double dx[3], int32_t dims,
+                    const double* k_dev, int32_t n, double* omega_dev, void* stream) {
+    if (!coeffs || !dx || !k_dev || !omega_dev || n < 0 || dims < 1 || dims > 3) {
+        set_error("disp_omega_eval: bad argument");
+        return FDTD_EINVAL;
+    }
+    for (int i = 0; i < 3; ++i)
+        if (!(dx[i] > 0)) { set_error("dx must be positive"); return FDTD_EINVAL; }
+    Clean cc = clean_coeffs(coeffs, dims);
+    int rc = validate(cc, dx, dims, dt);
+    if (rc) return rc;
+    if (n == 0) return FDTD_OK;
+    launch_omega(cc.alpha, cc.beta, cc.delta, dt, dx, dims, k_dev, n, omega_dev, (cudaStream_t)stream);
+    CK(cudaGetLastError());
+    return FDTD_OK;
+}
 
 // ---------------------------------------------------------------------------
 // disp_norm_eval_noalloc: the dispersion norm without any device allocation.

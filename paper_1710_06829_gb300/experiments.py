@@ -1,0 +1,302 @@
+"""Measurement drivers for the workloads shaped like the paper's (all inputs synthetic, seeded).
+
+    python -m paper_1710_06829_gb300.experiments dispersion      # 256^3 plane waves
+    python -m paper_1710_06829_gb300.experiments cherenkov       # 512x256x256 rigid bunch
+    python -m paper_1710_06829_gb300.experiments differentiable  # 128^3 checkpointed gradient
+    python -m paper_1710_06829_gb300.experiments optimize        # coefficient minimisation
+
+Each prints one JSON object.  Every number comes from libfdtd's kernels; closed forms used
+for comparison (omega(k), its k-gradient) are evaluated here in FP64 from Eq. (dispersion_
+relation) only to report the deviation of the simulated values from them.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import time
+
+import numpy as np
+import torch
+
+from . import _lib as L
+from . import inputs
+from . import optimize as O
+from . import sim as S
+
+
+def seeded_theta(seed):
+    """First admissible draw (min S >= 0) of the seeded coefficient generator."""
+    s = seed
+    while True:
+        beta, delta = inputs.random_theta(s, 3)
+        _, smin, _ = S.dt_max(beta, delta, [1, 1, 1], 3)
+        if smin >= 0:
+            return beta, delta
+        s += 1000
+
+
+def omega_closed(kvec, beta, delta, dt, dx):
+    """omega(k) of Eq. (dispersion_relation), evaluated by libfdtd (disp_omega_eval)."""
+    return float(S.omega(beta, delta, dt, dx, 3, np.asarray(kvec).reshape(1, 3))[0])
+
+
+def measure_omega(sm, comp, kvec, nsteps):
+    """omega from the simulated plane-wave amplitudes: a_{s+1} + a_{s-1} = 2 cos(omega dt) a_s."""
+    amps = torch.empty((nsteps + 1, 2), dtype=torch.float64, device="cuda")
+    for s in range(nsteps + 1):
+        sm.plane_wave(comp, kvec, out=amps[s])
+        if s < nsteps:
+            sm.step(1)
+    a = amps.cpu().numpy()
+    a = a[:, 0] + 1j * a[:, 1]
+    lhs, rhs = a[2:] + a[:-2], 2 * a[1:-1]
+    cw = float(np.real(np.vdot(rhs, lhs) / np.vdot(rhs, rhs)))
+    return math.acos(max(-1.0, min(1.0, cw))) / sm.dt
+
+
+# ---------------------------------------------------------------- plane waves (phase / group)
+
+def dispersion(n=256, nsteps=400):
+    dx = [1.0, 1.0, 1.0]
+    sets = {"yee": (np.zeros((3, 3)), np.zeros(3))}
+    for seed in (0, 1, 2):
+        sets[f"seed{seed}"] = seeded_theta(seed)
+    dirs = {"x": ((1, 0, 0), (0, 0, 1)), "xy": ((1, 1, 0), (0, 0, 1)), "xyz": ((1, 1, 1), (1, -1, 0))}
+    rows = []
+    for name, (beta, delta) in sets.items():
+        dtm, _, _ = S.dt_max(beta, delta, dx, 3)
+        dt = 0.95 * dtm
+        sm = S.Simulation((n, n, n), dx, dt, beta, delta, dims=3, dtype="f32")
+        for dname, (d, pol) in dirs.items():
+            dvec = np.array(d, dtype=np.float64)
+            for lam in (4, 8, 16, 32):
+                m = max(1, round(n / (lam * np.linalg.norm(dvec))))
+                res = {}
+                for mm in (m, m + 1):   # neighbouring commensurate wavenumbers -> group velocity
+                    kvec = dvec * 2 * math.pi * mm / n
+                    fields = inputs.plane_wave((n, n, n), kvec, pol, dx)
+                    sm.set_state([torch.from_numpy(f.astype(np.float32)) for f in fields])
+                    res[mm] = (kvec, measure_omega(sm, int(np.argmax(np.abs(pol))), kvec, nsteps))
+                (k0, w0), (k1, w1) = res[m], res[m + 1]
+                kn0, kn1 = np.linalg.norm(k0), np.linalg.norm(k1)
+                wc0 = omega_closed(k0, beta, delta, dt, dx)
+                wc1 = omega_closed(k1, beta, delta, dt, dx)
+                rows.append({
+                    "coeffs": name, "dir": dname, "lambda": n / (m * np.linalg.norm(dvec)),
+                    "vph_sim": w0 / kn0, "vph_closed": wc0 / kn0, "omega_rel_err": w0 / wc0 - 1,
+                    "vg_sim": (w1 - w0) / (kn1 - kn0), "vg_closed_fd": (wc1 - wc0) / (kn1 - kn0)})
+        sm.close()
+    worst = max(abs(r["omega_rel_err"]) for r in rows)
+    return {"experiment": "dispersion", "grid": [n, n, n], "dtype": "f32", "steps": nsteps,
+            "courant": "0.95 of dt_max", "worst_omega_rel_err": worst, "rows": rows}
+
+
+# ---------------------------------------------------------------- rigid bunch (Cherenkov)
+
+def cherenkov(nsteps=2000, every=50, shape=(512, 256, 256)):
+    """Rigid bunch along +x (stand-in for the PIC beam of Sec. 6); field energy in the window
+    [x_c - 192, x_c - 20) behind the bunch, 16 cells away from the absorbing layers.  The fields
+    start at zero, so a static field of the image charge -rho^0 stays around x0 (identical for
+    all schemes): samples whose window comes within 64 cells of x0 are left out."""
+    nx, ny, nz = shape
+    dx = [1.0, 1.0, 1.0]
+    x0 = 64.0
+    schemes = {"yee": (np.zeros((3, 3)), np.zeros(3)),
+               # isotropic 3D lift of Table 1's min.1 (beta_xy = beta_yx = 0.110, delta = -0.125)
+               "min1_lift": inputs.isotropic_theta(-0.125, -0.125, 0.110, 0.110)}
+    out = {"experiment": "cherenkov", "grid": list(shape), "dtype": "f32", "steps": nsteps,
+           "bunch": {"q": 1.0, "v": 0.999, "sigma_par": 4, "sigma_perp": 8, "x0": x0},
+           "absorber": {"cells": 16, "sigma": 0.1},
+           "window": "[x_c-192, x_c-20), margin 16; samples within 64 cells of x0 excluded",
+           "courant": "0.95 of dt_max", "series": {}}
+
+    def clear_of_image(lo, length):
+        for i in range(length):
+            d = ((lo + i) - x0 + nx / 2) % nx - nx / 2
+            if abs(d) < 64:
+                return False
+        return True
+
+    for name, (beta, delta) in schemes.items():
+        dtm, smin, _ = S.dt_max(beta, delta, dx, 3)
+        if smin < 0:
+            continue
+        dt = 0.95 * dtm
+        sm = S.Simulation(shape, dx, dt, beta, delta, dims=3, dtype="f32", absorb_cells=16,
+                          absorb_sigma=0.1)
+        sm.set_state([None] * 6)
+        bunch = S.Bunch(1.0, 0.999, x0, ny / 2, nz / 2, 4.0, 8.0)
+        series = []
+        t0 = time.perf_counter()
+        for s in range(0, nsteps, every):
+            sm.step(every, source=bunch)
+            xc = x0 + 0.999 * dt * (s + every)
+            x_lo = int(math.floor(xc - 192))
+            if clear_of_image(x_lo, 172):
+                e = float(sm.energy(x_lo, 172, 16).item())
+                series.append({"step": s + every, "x_c": xc, "energy_behind": e})
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        sm.sync()
+        sm.close()
+        late = [r["energy_behind"] for r in series if r["step"] > nsteps // 2]
+        out["series"][name] = {"dt": dt, "seconds": el, "gcells_per_s": nx * ny * nz * nsteps / el / 1e9,
+                               "mean_energy_second_half": float(np.mean(late)) if late else None,
+                               "energy": series}
+    ys, ms = out["series"].get("yee"), out["series"].get("min1_lift")
+    if ys and ms and ys["mean_energy_second_half"] and ms["mean_energy_second_half"] is not None:
+        out["ratio_min1_over_yee"] = ms["mean_energy_second_half"] / ys["mean_energy_second_half"]
+    return out
+
+
+# ---------------------------------------------------------------- differentiable FDTD
+
+def differentiable(n=128, nsteps=500, every=50, h=1e-4):
+    from .autograd import FdtdProbeLoss, ProbeLossProblem, tied_coefficients
+    shape = (n, n, n)
+    dx = [1.0, 1.0, 1.0]
+    theta0 = torch.tensor([-0.065, -0.065, -0.065, -0.065], dtype=torch.float64)   # min.3 lifted
+    b0, d0 = inputs.isotropic_theta(*theta0.tolist())
+    dtm, _, _ = S.dt_max(b0, d0, dx, 3)
+    dt = 0.95 * dtm
+    Ez = inputs.pulse_ez_3d(shape, dx, 32.0, 8.0, 16.0, 16.0)
+    z = np.zeros_like(Ez)
+    init = [torch.from_numpy(a) for a in (z, z, Ez, z, z, z)]
+    xp = 96
+    tgt = inputs.vacuum_probe_target(Ez, dx, dt, nsteps, xp)
+    out = {"experiment": "differentiable", "grid": list(shape), "steps": nsteps, "checkpoint": every,
+           "probe_x": xp, "theta0": theta0.tolist(), "dt": dt}
+    res = {}
+    for dtype in ("f32", "f64"):
+        prob = ProbeLossProblem(shape, dx, dt, init, 2, xp, torch.from_numpy(tgt).cuda(), nsteps,
+                                every, dtype=dtype)
+        theta = theta0.clone().requires_grad_(True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        beta, delta = tied_coefficients(theta)
+        loss = FdtdProbeLoss.apply(beta, delta, prob)
+        loss.backward()
+        torch.cuda.synchronize()
+        res[dtype] = (float(loss.detach()), theta.grad.numpy().copy(), time.perf_counter() - t0, prob)
+    # central differences of the FP64 GPU forward
+    prob64 = res["f64"][3]
+
+    def fwd(th):
+        b, d = tied_coefficients(th)
+        return float(FdtdProbeLoss.apply(b, d, prob64))
+    fd = np.zeros(4)
+    for i in range(4):
+        tp, tm = theta0.clone(), theta0.clone()
+        tp[i] += h
+        tm[i] -= h
+        fd[i] = (fwd(tp) - fwd(tm)) / (2 * h)
+    g32, g64 = res["f32"][1], res["f64"][1]
+    out.update({"loss_f32": res["f32"][0], "loss_f64": res["f64"][0], "grad_f32": g32.tolist(),
+                "grad_f64": g64.tolist(), "grad_fd_f64": fd.tolist(),
+                "max_rel_err_f32_vs_fd": float(np.max(np.abs(g32 - fd) / np.abs(fd))),
+                "max_rel_err_f64_vs_fd": float(np.max(np.abs(g64 - fd) / np.abs(fd))),
+                "seconds_loss_and_grad_f32": res["f32"][2], "seconds_loss_and_grad_f64": res["f64"][2]})
+    for v in res.values():
+        v[3].sim.close()
+    return out
+
+
+# ---------------------------------------------------------------- coefficient optimisation
+
+def optimize(n=256, iters=50, batch=32, n2d=512, steps2d=256, every2d=32, mu=0.0):
+    """Norm minimisation on the GPU (uniform and 30-degree cone weight about +x), optionally with
+    mu * mean propagation loss of `batch` 2D TE runs (pulses at angles 0..87 degrees)."""
+    beta0, delta0 = np.zeros((3, 3)), np.zeros(3)
+    dtm, _, _ = S.dt_max(beta0, delta0, [1, 1, 1], 3)
+    dt = 0.5 * dtm
+    tie = O.Tying.isotropic_3d(dt)
+    lo, hi = np.full(4, -0.125), np.full(4, 0.125)
+    out = {"experiment": "optimize", "kgrid": [n, n, n], "iters": iters, "dt": dt, "runs": {}}
+    prop = None
+    if mu != 0.0:
+        prop = batched_propagation(batch, n2d, steps2d, every2d, dt)
+    for wname, (w, wp) in {"uniform": (L.FDTD_W_UNIFORM, 0.0),
+                           "cone30": (L.FDTD_W_CONE_X, math.radians(30))}.items():
+        obj = O.NormObjective([1, 1, 1], 3, (n, n, n), w, wp, prop=prop, mu=mu)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        theta, c, J, hist = O.minimise(obj, tie, np.zeros(4), lo, hi, iters=iters)
+        el = time.perf_counter() - t0
+        out["runs"][wname] = {"theta": theta.tolist(), "J": J, "J0": hist[0][1], "seconds": el,
+                              "norm_evaluations": obj.evals, "seconds_per_iteration": el / max(1, len(hist) - 1)}
+    if prop is not None:
+        out["propagation"] = {"batch": batch, "grid2d": n2d, "steps": steps2d, "checkpoint": every2d,
+                              "mu": mu, "evaluations": prop.calls}
+    return out
+
+
+class batched_propagation:
+    """mean_b of the probe misfit of `batch` 2D TE runs (one batched launch per step) and its
+    coefficient gradient (adjoint with checkpoints), as a callable (beta, delta, dt) -> (L, g13)."""
+
+    def __init__(self, batch, n, steps, every, dt):
+        self.batch, self.n, self.steps, self.every, self.dt = batch, n, steps, every, dt
+        self.calls = 0
+        nx = ny = n
+        # TE packets (E_x, E_y) at angles 0..87 degrees, lambda = 16, centred at (n/4, n/4);
+        # target: E_y of the exact vacuum propagation on the probe plane x = 3n/4
+        Ex = np.zeros((batch, ny, nx))
+        Ey = np.zeros((batch, ny, nx))
+        tgt = np.zeros((steps, batch, ny))
+        self.xp = 3 * n // 4
+        for b in range(batch):
+            ang = math.radians(87.0 * b / max(1, batch - 1))
+            Ex[b], Ey[b] = inputs.angled_te_packet(nx, ny, ang, 16.0, 24.0, 32.0, (nx / 4, ny / 4))
+            tgt[:, b, :] = inputs.vacuum_target_2d(Ey[b], [1.0, 1.0], dt, steps, self.xp)
+        self.init = [torch.from_numpy(Ex), torch.from_numpy(Ey), None, None, None, None]
+        self.target = torch.from_numpy(tgt).to("cuda", torch.float32).contiguous()
+        self.sim = None
+
+    def __call__(self, beta, delta, dt):
+        self.calls += 1
+        b2 = np.array(beta, dtype=np.float64).copy()
+        d2 = np.array(delta, dtype=np.float64).copy()
+        if self.sim is None:
+            self.sim = S.Simulation((self.n, self.n, self.batch), [1, 1, 1], dt, b2, d2, dims=2,
+                                    dtype="f32", batched=True)
+            self.probe = S.Probe(1, self.xp, self.target)
+        else:
+            self.sim.set_coeffs(dt, b2, d2)
+        sm = self.sim
+        sm.set_state(self.init)
+        loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+        segs = [(s, min(self.every, self.steps - s)) for s in range(0, self.steps, self.every)]
+        for slot, (_, k) in enumerate(segs):
+            sm.checkpoint_save(slot)
+            sm.step(k, probe=self.probe, loss=loss)
+        sm.set_adjoint(None)
+        grad = torch.zeros(12, dtype=torch.float64, device="cuda")
+        for slot in range(len(segs) - 1, -1, -1):
+            sm.checkpoint_restore(slot)
+            sm.step(segs[slot][1], record=True)
+            sm.step_adjoint(segs[slot][1], grad, probe=self.probe)
+        g = np.zeros(13)
+        g[:12] = grad.cpu().numpy() / self.batch
+        return float(loss.item()) / self.batch, g
+
+
+def main():
+    p = argparse.ArgumentParser()
+    p.add_argument("what", choices=["dispersion", "cherenkov", "differentiable", "optimize"])
+    p.add_argument("--mu", type=float, default=0.0)
+    p.add_argument("--iters", type=int, default=50)
+    a = p.parse_args()
+    if a.what == "dispersion":
+        r = dispersion()
+    elif a.what == "cherenkov":
+        r = cherenkov()
+    elif a.what == "differentiable":
+        r = differentiable()
+    else:
+        r = optimize(iters=a.iters, mu=a.mu)
+    print(json.dumps(r))
+
+
+if __name__ == "__main__":
+    main()

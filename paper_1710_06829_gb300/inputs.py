@@ -108,3 +108,73 @@ def te_pulse(shape_xy, dx, center, waist, wavelength, dt, seed=0, noise=1e-3):
     Bz = prof(x + 0.5 * dt, y) + noise * rng.standard_normal(x.shape)
     zero = np.zeros((1, ny, nx))
     return [zero, Ey, zero.copy(), zero.copy(), zero.copy(), Bz]
+
+
+def vacuum_probe_target(Ez0, dx, dt, nsteps, x_index):
+    """Probe-plane target for the differentiable run: E_z(x_index, y, z, s dt), s = 1..nsteps, of
+    the exact continuum (c = 1) vacuum solution that starts from E = (0, 0, Ez0), B = 0 on the
+    periodic box.  Per Fourier mode the transverse part oscillates as cos(|k| t) and the
+    longitudinal part stays; evaluated with FP64 FFTs.  Returns an array [nsteps, nz, ny]."""
+    nz, ny, nx = Ez0.shape
+    kx = 2 * math.pi * np.fft.fftfreq(nx, d=dx[0])
+    ky = 2 * math.pi * np.fft.fftfreq(ny, d=dx[1])
+    kz = 2 * math.pi * np.fft.fftfreq(nz, d=dx[2])
+    KZ, KY, KX = np.meshgrid(kz, ky, kx, indexing="ij")
+    k2 = KX ** 2 + KY ** 2 + KZ ** 2
+    kn = np.sqrt(k2)
+    with np.errstate(invalid="ignore", divide="ignore"):
+        long_frac = np.where(k2 > 0, KZ ** 2 / k2, 1.0)   # z-component of the longitudinal projector
+    F = np.fft.fftn(Ez0)
+    # E_z at x = x_index for all (y, z): sum over k_x with the phase of the probe plane
+    phase_x = np.exp(1j * kx * x_index * dx[0]) / nx
+    out = np.empty((nsteps, nz, ny))
+    A = F * (1.0 - long_frac)      # transverse part
+    Bl = F * long_frac             # static longitudinal part
+    static = np.tensordot(Bl, phase_x, axes=([2], [0]))
+    for s in range(1, nsteps + 1):
+        t = s * dt
+        dyn = np.tensordot(A * np.cos(kn * t), phase_x, axes=([2], [0]))   # [nz, ny] in (kz, ky)
+        plane = np.fft.ifft2(dyn + static, axes=(0, 1)) * 1.0
+        out[s - 1] = plane.real
+    return out
+
+
+def angled_te_packet(nx, ny, angle, wavelength, sigma_u, sigma_v, center, dx=(1.0, 1.0)):
+    """2D TE packet travelling at `angle` (radians from +x), continuum divergence-free:
+    E = curl(psi z) = (d_y psi, -d_x psi) with psi = exp(-u^2/su^2 - v^2/sv^2) sin(k0 u)/k0,
+    u, v the coordinates along / across the direction of travel, evaluated analytically at the
+    E_x (i+1/2, j) and E_y (i, j+1/2) positions.  Returns (Ex, Ey), each [ny, nx]."""
+    k0 = 2 * math.pi / wavelength
+    ca, sa = math.cos(angle), math.sin(angle)
+
+    def grads(x, y):
+        u = (x - center[0]) * ca + (y - center[1]) * sa
+        v = -(x - center[0]) * sa + (y - center[1]) * ca
+        env = np.exp(-(u / sigma_u) ** 2 - (v / sigma_v) ** 2)
+        psi_u = env * (np.cos(k0 * u) - 2 * u / sigma_u ** 2 * np.sin(k0 * u) / k0)
+        psi_v = env * (-2 * v / sigma_v ** 2) * np.sin(k0 * u) / k0
+        return psi_u * ca - psi_v * sa, psi_u * sa + psi_v * ca   # d/dx, d/dy
+
+    y, x = np.meshgrid(np.arange(ny) * dx[1], (np.arange(nx) + 0.5) * dx[0], indexing="ij")
+    _, dpsi_dy = grads(x, y)
+    y, x = np.meshgrid((np.arange(ny) + 0.5) * dx[1], np.arange(nx) * dx[0], indexing="ij")
+    dpsi_dx, _ = grads(x, y)
+    return dpsi_dy, -dpsi_dx
+
+
+def vacuum_target_2d(F0, dx, dt, nsteps, x_index):
+    """One component of a continuum divergence-free 2D field under vacuum propagation
+    (c = 1, initial B = 0): every Fourier mode oscillates as cos(|k| t).  Returns the values on
+    the plane x = x_index for t = s dt, s = 1..nsteps: array [nsteps, ny]."""
+    ny, nx = F0.shape
+    kx = 2 * math.pi * np.fft.fftfreq(nx, d=dx[0])
+    ky = 2 * math.pi * np.fft.fftfreq(ny, d=dx[1])
+    KY, KX = np.meshgrid(ky, kx, indexing="ij")
+    kn = np.sqrt(KX ** 2 + KY ** 2)
+    F = np.fft.fft2(F0)
+    phase_x = np.exp(1j * kx * x_index * dx[0]) / nx
+    out = np.empty((nsteps, ny))
+    for s in range(1, nsteps + 1):
+        col = (F * np.cos(kn * s * dt)) @ phase_x     # [ny] in k_y
+        out[s - 1] = np.fft.ifft(col).real
+    return out

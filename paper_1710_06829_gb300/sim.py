@@ -5,6 +5,7 @@ allocates tensors, passes their pointers and reads results back.
 """
 from __future__ import annotations
 
+import numpy as np
 import torch
 
 from . import _lib as L
@@ -38,6 +39,7 @@ class Probe:
     """Probe-plane misfit of E_component at x = x_index against target[(steps), nz, ny]."""
 
     def __init__(self, component, x_index, target: torch.Tensor):
+        """target must be a contiguous CUDA tensor of the simulation's dtype."""
         assert target.is_cuda and target.is_contiguous() and target.dim() == 3
         self.target = target
         self.s = L.fdtd_probe(int(component), int(x_index), target.data_ptr(), target.shape[0])
@@ -112,6 +114,8 @@ class Simulation:
     # -- stepping ------------------------------------------------------------
     def step(self, n, source: Bunch | None = None, probe: Probe | None = None, loss=None,
              record=False):
+        if probe is not None and probe.target.dtype != self.tdtype:
+            raise TypeError("probe target dtype does not match the simulation dtype")
         L.fdtd_step(self.h, n, source.s if source is not None else None,
                     probe.s if probe is not None else None,
                     loss.data_ptr() if loss is not None else None, 1 if record else 0)
@@ -144,6 +148,8 @@ class Simulation:
     def step_adjoint(self, n, grad: torch.Tensor, probe: Probe | None = None):
         """grad: float64 CUDA tensor of 12 entries (beta 3x3 row-major, delta 3), accumulated."""
         assert grad.is_cuda and grad.dtype == torch.float64 and grad.numel() >= 12
+        if probe is not None and probe.target.dtype != self.tdtype:
+            raise TypeError("probe target dtype does not match the simulation dtype")
         L.fdtd_step_adjoint(self.h, n, probe.s if probe is not None else None, grad.data_ptr())
 
     # -- diagnostics -----------------------------------------------------------
@@ -179,3 +185,12 @@ def disp_norm(beta, delta, dt, dx, dims, N, weight=L.FDTD_W_UNIFORM, weight_para
                            _stream_ptr(stream))
     gb = [out[1:4], out[4:7], out[7:10]]
     return out[0], gb, out[10:13], out[13]
+
+
+def omega(beta, delta, dt, dx, dims, k, stream=None):
+    """omega(k) of the scheme (Eq. dispersion_relation) on the GPU for an (n, 3) array of k."""
+    kt = torch.as_tensor(np.asarray(k, dtype=np.float64).reshape(-1, 3)).cuda().contiguous()
+    out = torch.empty(kt.shape[0], dtype=torch.float64, device="cuda")
+    L.disp_omega_eval(coeffs_struct(beta, delta), dt, dx, dims, kt.data_ptr(), kt.shape[0],
+                      out.data_ptr(), _stream_ptr(stream))
+    return out.cpu().numpy()

@@ -61,3 +61,28 @@ def test_rejects_unstable():
     beta = np.zeros((3, 3))
     with pytest.raises(L.FdtdError):
         S.disp_norm(beta, np.zeros(3), 0.8, [1, 1, 1], 2, (16, 16, 1))
+
+
+def test_omega_eval_matches_oracle_and_table3(golden):
+    rng = np.random.default_rng(3)
+    beta, delta = inputs.random_theta(11, 3)
+    dx = [1.0, 1.2, 0.9]
+    dt = 0.9 * D.dt_max(beta, delta, dx, 3)
+    k = rng.uniform(0, 1, (500, 3)) * np.pi / np.array(dx)
+    got = S.omega(beta, delta, dt, dx, 3, k)
+    ref = D.omega(k[:, 0], k[:, 1], k[:, 2], beta, delta, dt, dx, 3)
+    assert np.allclose(got, ref, rtol=1e-13, atol=0)
+    # Table 3 extremes of v_ph from GPU omega on a 512^2 grid (2D, dx = dy)
+    t1 = {r[0]: r for r in golden("table1_uniform_norms.txt")}
+    n = 512
+    kk = np.arange(1, n + 1) * np.pi / n
+    KY, KX = np.meshgrid(kk, kk, indexing="ij")
+    K = np.stack([KX.ravel(), KY.ravel(), np.zeros(KX.size)], axis=1)
+    for name, vmin, vmax in golden("table3_phase_velocity.txt"):
+        _, nu, b, dxx, dyy, _ = t1[name]
+        be = np.zeros((3, 3))
+        be[0, 1] = be[1, 0] = float(b)
+        de = np.array([float(dxx), float(dyy), 0.0])
+        w = S.omega(be, de, float(nu), [1, 1, 1], 2, K)
+        v = w / np.linalg.norm(K, axis=1)
+        assert abs(v.min() - float(vmin)) <= 0.015 and abs(v.max() - float(vmax)) <= 0.015, name
