@@ -1,114 +1,137 @@
-// FP32 fused leapfrog step with 4-cell x-segments per thread.
+// FP32 fused leapfrog step (one launch per leapfrog step).
 //
-// Same schedule as the generic fused kernel (fdtd_fused.cu): a CTA owns a
-// 64 x 8 (x, y) tile and marches a chunk of 32 planes; E^n planes arrive by TMA
-// as 72 x 12 boxes into a ring of shared-memory slots (one plane ahead of use,
-// mbarrier completion); for each plane p the CTA forms B^{n+1/2}(p) on the
-// tile plus the halo row y0-1 and halo column x0-1, then E^{n+1}(p).
+// A CTA owns a 64 x 8 (x, y) tile and a chunk of 32 planes and marches through it.  E^n planes
+// arrive by TMA (cp.async.bulk.tensor.3d) as 72 x 12 boxes (x0-4 .., y0-2 ..) into a ring of five
+// shared-memory slots, one plane ahead of use, completion signalled on mbarriers.  Iteration `it`
+// forms B^{n+1/2} on plane p = z0-1+it (tile, halo row y0-1, halo column x0-1) and E^{n+1} on
+// plane p-1, so one block barrier per plane suffices; B^{n+1/2} lives in a small shared ring
+// (B_x, B_y: 3 planes, B_z: 2 planes).  B^{n-1/2} is not staged: each thread prefetches its
+// own segment of the next plane from HBM into registers while the current plane is computed.
 //
-// What differs is the work per thread.  Each thread owns four consecutive
-// cells in x and reads every stencil row it needs as 16-byte shared-memory
-// vectors (a row window of 12 values covers the x reach -1 .. +5 of four
-// cells), so one load serves up to four taps.  B^{n-1/2} is not staged: each
-// thread prefetches its own 16-byte segment of the next plane from HBM into
-// registers while the current plane is computed.  Owned results leave as
-// 16-byte stores; a segment at the edge of the domain also writes its periodic
-// images (the padded layout's ghosts).
+// Work per thread: W consecutive cells of one row.  Every stencil row a thread needs is read as
+// W-wide shared-memory vectors (a window of 3W values covers the x reach -1 .. W+1), so one
+// load serves several taps; a warp covers whole rows, so a vector load of a warp never
+// conflicts.  Owned results leave as W-wide stores; a segment at the edge of the domain also
+// writes its periodic images (the ghosts of the padded layout).  Plane bookkeeping uses
+// counters (no integer division in the loop).
 //
-// The per-cell arithmetic is dstar_taps / ampere_comp with the same operands in
-// the same order as the reference-form kernels: the fields are bitwise equal.
-// Every mbarrier wait is bounded (see fdtd_tma.cuh); on expiry the CTA raises
-// *err, drains its copies in flight (bounded) and returns.
+// Per-cell arithmetic is dstar_taps / ampere_comp with the same operands in the same order as
+// the reference-form kernels: the fields are bitwise equal.  Every mbarrier wait is bounded
+// (fdtd_tma.cuh); on expiry the CTA raises *err, drains its copies in flight (bounded) and
+// returns.
 #include "fdtd_tma.cuh"
 
 namespace fdtd {
 namespace f32seg {
 
-constexpr int TX = 64, TY = 8, TZ = 32, D = 1, NT = 160;
-constexpr int EW = TX + 8, EH = TY + 4, EPL = EW * EH;       // E box 72 x 12 (x0-4.., y0-2..)
-constexpr int ESLOT = ((EPL * 4 + 127) / 128) * 128 / 4;       // floats per E slot
-constexpr int BW = TX + 4, BH = TY + 1, BPL = BW * BH;        // B^{n+1/2} plane: x0-4.., y0-1..
+constexpr int W = 4;                                            // cells per thread (along x)
+constexpr int TX = 64, TY = 8, TZ = 32, D = 1;
+constexpr int NSEG = TX / W;                                    // segments per row
+constexpr int NT = ((NSEG * (TY + 1) + TY + 1 + 31) / 32) * 32;  // B tasks + halo column
+constexpr int EW = TX + 8, EH = TY + 4, EPL = EW * EH;        // E box 72 x 12 (x0-4.., y0-2..)
+constexpr int ESLOT = ((EPL * 4 + 127) / 128) * 128 / 4;        // floats per E slot
+constexpr int BW = TX + 4, BH = TY + 1, BPL = BW * BH;         // B^{n+1/2} plane: x0-4.., y0-1..
 constexpr int BSLOT = ((BPL * 4 + 127) / 128) * 128 / 4;
 constexpr int NE = D + 4, NS = D + 1;
-constexpr int NSEG = TX / 4;                                   // segments per row (16)
 constexpr size_t OFF_E = 0;
-constexpr size_t OFF_BN = OFF_E + (size_t)NE * 3 * ESLOT * 4;  // Bx[3], By[3], Bz[2]
+constexpr size_t OFF_BN = OFF_E + (size_t)NE * 3 * ESLOT * 4;   // Bx[3], By[3], Bz[2]
 constexpr size_t OFF_BAR = OFF_BN + (size_t)8 * BSLOT * 4;
 constexpr size_t SMEM = OFF_BAR + (size_t)(NS + 1) * 8;
 constexpr uint32_t UNIT_BYTES = 3u * EPL * 4;
 constexpr uint32_t PRO_BYTES = 9u * EPL * 4;
 
-struct Win {
-    float v[12];   // v[k] = F[idx - 4 + k]
+// W-wide vector of floats (8 bytes for W = 2, 16 bytes for W = 4)
+template <int N>
+struct VecT;
+template <>
+struct VecT<2> {
+    using type = float2;
 };
+template <>
+struct VecT<4> {
+    using type = float4;
+};
+using Vec = typename VecT<W>::type;
 
-__device__ __forceinline__ float4 ld4(const float* s, int idx) {
-    return *reinterpret_cast<const float4*>(s + idx);
+__device__ __forceinline__ void unpackv(const float2& a, float* o) { o[0] = a.x; o[1] = a.y; }
+__device__ __forceinline__ void unpackv(const float4& a, float* o) {
+    o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w;
 }
+__device__ __forceinline__ void packv(const float* o, float2& a) { a.x = o[0]; a.y = o[1]; }
+__device__ __forceinline__ void packv(const float* o, float4& a) {
+    a.x = o[0]; a.y = o[1]; a.z = o[2]; a.w = o[3];
+}
+
+__device__ __forceinline__ void ldv(const float* s, int idx, float* o) {
+    unpackv(*reinterpret_cast<const Vec*>(s + idx), o);
+}
+
+struct Win {
+    float v[3 * W];   // v[k] = F[idx - W + k]
+};
 
 __device__ __forceinline__ Win win(const float* s, int idx) {
     Win w;
-    const float4 a = ld4(s, idx - 4), b = ld4(s, idx), c = ld4(s, idx + 4);
-    w.v[0] = a.x; w.v[1] = a.y; w.v[2] = a.z; w.v[3] = a.w;
-    w.v[4] = b.x; w.v[5] = b.y; w.v[6] = b.z; w.v[7] = b.w;
-    w.v[8] = c.x; w.v[9] = c.y; w.v[10] = c.z; w.v[11] = c.w;
+    ldv(s, idx - W, w.v);
+    ldv(s, idx, w.v + W);
+    ldv(s, idx + W, w.v + 2 * W);
     return w;
 }
 
-// D*_a (times dt) on the four cells starting at in-plane index e, for the field whose
+// D*_a (times dt) on the W cells starting at in-plane index e, for the field whose
 // plane slots are Fm (p-1), F0 (p), F1 (p+1), F2 (p+2).  Tap order as dstar_taps expects.
 template <int A>
-__device__ __forceinline__ void dstar4(const float* Fm, const float* F0, const float* F1,
+__device__ __forceinline__ void dstarw(const float* Fm, const float* F0, const float* F1,
                                        const float* F2, int e, float cA, float cD, float cBb,
-                                       float cBc, float out[4]) {
+                                       float cBc, float out[W]) {
     if constexpr (A == 0) {   // axis x; transverse y, then z
         const Win w0 = win(F0, e), wyp = win(F0, e + EW), wym = win(F0, e - EW);
         const Win w1 = win(F1, e), wm = win(Fm, e);
 #pragma unroll
-        for (int u = 0; u < 4; ++u)
-            out[u] = dstar_taps(w0.v[5 + u], w0.v[4 + u], w0.v[6 + u], w0.v[3 + u], wyp.v[5 + u],
-                                wyp.v[4 + u], wym.v[5 + u], wym.v[4 + u], w1.v[5 + u], w1.v[4 + u],
-                                wm.v[5 + u], wm.v[4 + u], cA, cD, cBb, cBc);
+        for (int u = 0; u < W; ++u)
+            out[u] = dstar_taps(w0.v[W + 1 + u], w0.v[W + u], w0.v[W + 2 + u], w0.v[W - 1 + u],
+                                wyp.v[W + 1 + u], wyp.v[W + u], wym.v[W + 1 + u], wym.v[W + u],
+                                w1.v[W + 1 + u], w1.v[W + u], wm.v[W + 1 + u], wm.v[W + u], cA, cD,
+                                cBb, cBc);
     } else if constexpr (A == 1) {   // axis y; transverse x, then z
         const Win w0 = win(F0, e), wyp = win(F0, e + EW);
-        const float4 yp2 = ld4(F0, e + 2 * EW), ym = ld4(F0, e - EW);
-        const float4 z1 = ld4(F1, e), z1p = ld4(F1, e + EW), zm = ld4(Fm, e), zmp = ld4(Fm, e + EW);
-        const float a2[4] = {yp2.x, yp2.y, yp2.z, yp2.w};
-        const float am[4] = {ym.x, ym.y, ym.z, ym.w};
-        const float c1[4] = {z1.x, z1.y, z1.z, z1.w};
-        const float c1p[4] = {z1p.x, z1p.y, z1p.z, z1p.w};
-        const float cm[4] = {zm.x, zm.y, zm.z, zm.w};
-        const float cmp[4] = {zmp.x, zmp.y, zmp.z, zmp.w};
+        float a2[W], am[W], c1[W], c1p[W], cm[W], cmp[W];
+        ldv(F0, e + 2 * EW, a2);
+        ldv(F0, e - EW, am);
+        ldv(F1, e, c1);
+        ldv(F1, e + EW, c1p);
+        ldv(Fm, e, cm);
+        ldv(Fm, e + EW, cmp);
 #pragma unroll
-        for (int u = 0; u < 4; ++u)
-            out[u] = dstar_taps(wyp.v[4 + u], w0.v[4 + u], a2[u], am[u], wyp.v[5 + u], w0.v[5 + u],
-                                wyp.v[3 + u], w0.v[3 + u], c1p[u], c1[u], cmp[u], cm[u], cA, cD,
-                                cBb, cBc);
+        for (int u = 0; u < W; ++u)
+            out[u] = dstar_taps(wyp.v[W + u], w0.v[W + u], a2[u], am[u], wyp.v[W + 1 + u],
+                                w0.v[W + 1 + u], wyp.v[W - 1 + u], w0.v[W - 1 + u], c1p[u], c1[u],
+                                cmp[u], cm[u], cA, cD, cBb, cBc);
     } else {   // axis z; transverse x, then y
         const Win w1 = win(F1, e), w0 = win(F0, e);
-        const float4 z2 = ld4(F2, e), zm = ld4(Fm, e);
-        const float4 w1p = ld4(F1, e + EW), w0p = ld4(F0, e + EW);
-        const float4 w1m = ld4(F1, e - EW), w0m = ld4(F0, e - EW);
-        const float a2[4] = {z2.x, z2.y, z2.z, z2.w};
-        const float am[4] = {zm.x, zm.y, zm.z, zm.w};
-        const float p1[4] = {w1p.x, w1p.y, w1p.z, w1p.w};
-        const float p0[4] = {w0p.x, w0p.y, w0p.z, w0p.w};
-        const float m1[4] = {w1m.x, w1m.y, w1m.z, w1m.w};
-        const float m0[4] = {w0m.x, w0m.y, w0m.z, w0m.w};
+        float a2[W], am[W], p1[W], p0[W], m1[W], m0[W];
+        ldv(F2, e, a2);
+        ldv(Fm, e, am);
+        ldv(F1, e + EW, p1);
+        ldv(F0, e + EW, p0);
+        ldv(F1, e - EW, m1);
+        ldv(F0, e - EW, m0);
 #pragma unroll
-        for (int u = 0; u < 4; ++u)
-            out[u] = dstar_taps(w1.v[4 + u], w0.v[4 + u], a2[u], am[u], w1.v[5 + u], w0.v[5 + u],
-                                w1.v[3 + u], w0.v[3 + u], p1[u], p0[u], m1[u], m0[u], cA, cD, cBb,
-                                cBc);
+        for (int u = 0; u < W; ++u)
+            out[u] = dstar_taps(w1.v[W + u], w0.v[W + u], a2[u], am[u], w1.v[W + 1 + u],
+                                w0.v[W + 1 + u], w1.v[W - 1 + u], w0.v[W - 1 + u], p1[u], p0[u],
+                                m1[u], m0[u], cA, cD, cBb, cBc);
     }
 }
 
-__device__ __forceinline__ void st4(float* F, long long idx, float4 v) {
-    *reinterpret_cast<float4*>(F + idx) = v;
+__device__ __forceinline__ void stv(float* F, long long idx, const float* v) {
+    Vec a;
+    packv(v, a);
+    *reinterpret_cast<Vec*>(F + idx) = a;
 }
 
-// Destination of one 4-cell segment (i0 .. i0+3, j, k) and of its periodic images
-// (the images exist only for segments at the domain edge; needs nx >= 8, ny >= 4).
+// Destination of one W-cell segment (i0 .. i0+W-1, j, k) and of its periodic images
+// (images exist only for segments within PX of the x ends or PY of the y ends).
 struct SegDst {
     long long o1, o2;   // owned row offset; image row offset (valid if yimg)
     bool xl, xr, yimg;
@@ -118,8 +141,8 @@ __device__ __forceinline__ SegDst seg_dst(const Geom& g, int i0, int j, int k, b
     SegDst d;
     const long long rowk = (long long)k * g.nyp;
     d.o1 = (rowk + j + PY) * g.nxp + PX + i0;
-    d.xl = edge_tile && i0 == 0;
-    d.xr = edge_tile && i0 == g.nx - 4;
+    d.xl = edge_tile && i0 < PX;
+    d.xr = edge_tile && i0 >= g.nx - PX;
     d.yimg = false;
     d.o2 = 0;
     if (edge_tile) {
@@ -132,15 +155,15 @@ __device__ __forceinline__ SegDst seg_dst(const Geom& g, int i0, int j, int k, b
 }
 
 __device__ __forceinline__ void put_seg(float* F, const SegDst& d, int nx, bool edge_tile,
-                                        float4 v) {
-    st4(F, d.o1, v);
+                                        const float* v) {
+    stv(F, d.o1, v);
     if (edge_tile) {
-        if (d.xl) st4(F, d.o1 + nx, v);
-        if (d.xr) st4(F, d.o1 - nx, v);
+        if (d.xl) stv(F, d.o1 + nx, v);
+        if (d.xr) stv(F, d.o1 - nx, v);
         if (d.yimg) {
-            st4(F, d.o2, v);
-            if (d.xl) st4(F, d.o2 + nx, v);
-            if (d.xr) st4(F, d.o2 - nx, v);
+            stv(F, d.o2, v);
+            if (d.xl) stv(F, d.o2 + nx, v);
+            if (d.xr) stv(F, d.o2 - nx, v);
         }
     }
 }
@@ -187,7 +210,7 @@ step_kernel(const __grid_constant__ FusedMaps maps, Geom g, Mult<float> m, Field
     //   tid in [144, 153): halo column cell (bx = -1, by = tid - 145)
     const bool bseg = tid < NSEG * (TY + 1);
     const bool bcol = !bseg && tid < NSEG * (TY + 1) + TY + 1;
-    const int b_bx = bseg ? 4 * (tid % NSEG) : -1;
+    const int b_bx = bseg ? W * (tid % NSEG) : -1;
     const int b_by = bseg ? tid / NSEG - 1 : tid - NSEG * (TY + 1) - 1;
     const long long b_off = (long long)(y0 + b_by + PY) * g.nxp + (x0 + b_bx + PX);
     int b_y = y0 + b_by;
@@ -211,24 +234,26 @@ step_kernel(const __grid_constant__ FusedMaps maps, Geom g, Mult<float> m, Field
     }
 
     // B^{n-1/2} of this thread's task, prefetched one plane ahead
-    float4 bo[3] = {make_float4(0, 0, 0, 0), make_float4(0, 0, 0, 0), make_float4(0, 0, 0, 0)};
-    auto load_bold = [&](int q) {
-        const long long o = (long long)wrapz(q) * g.plane + b_off;
+    float bo[3][W];
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int u = 0; u < W; ++u) bo[c][u] = 0.0f;
+    float bn[3][W];   // next plane's B^{n-1/2}, loaded at the start of the current B phase
+    auto load_bold = [&](int qw, float (&dst)[3][W]) {   // qw: wrapped plane index
+        const long long o = (long long)qw * g.plane + b_off;
         if (bseg) {
 #pragma unroll
-            for (int c = 0; c < 3; ++c) bo[c] = __ldg(reinterpret_cast<const float4*>(in.c[3 + c] + o));
+            for (int c = 0; c < 3; ++c) unpackv(__ldg(reinterpret_cast<const Vec*>(in.c[3 + c] + o)), dst[c]);
         } else if (bcol) {
 #pragma unroll
-            for (int c = 0; c < 3; ++c) bo[c].x = __ldg(in.c[3 + c] + o);
+            for (int c = 0; c < 3; ++c) dst[c][0] = __ldg(in.c[3 + c] + o);
         }
     };
-    load_bold(z0 - 1);
+    load_bold(wrapz(z0 - 1), bo);
 
     const float mdt = -m.dt;
-    // B^{n+1/2} ring: B_x, B_y keep planes p, p-1, p-2; B_z keeps p, p-1.
-    auto sBx = [&](int q) { return sB + ((q + 6) % 3) * BSLOT; };
-    auto sBy = [&](int q) { return sB + (3 + (q + 6) % 3) * BSLOT; };
-    auto sBz = [&](int q) { return sB + (6 + (q + 6) % 2) * BSLOT; };
+    // B^{n+1/2} ring: B_x, B_y keep planes p, p-1, p-2 (slot (p+6) mod 3); B_z keeps p, p-1.
     // Iteration it forms B^{n+1/2} on plane p = z0 - 1 + it (it < niter) and E^{n+1} on
     // plane p - 1 (when z0 <= p - 1 < zend).  One block barrier per iteration.
     // Thread 0 waits for each plane's copies before the block barrier that precedes the
@@ -240,10 +265,17 @@ step_kernel(const __grid_constant__ FusedMaps maps, Geom g, Mult<float> m, Field
         if (tid == 0) ok0 = mbar_wait(&bar[NS], 0) && mbar_wait(&bar[0], 0);
         failed = __syncthreads_or(!ok0);
     }
-    for (; !failed && it <= niter; ++it) {
+    // plane bookkeeping by counters (no integer division in the loop):
+    //   pw = p mod nz, qw = (p-1) mod nz, s_m = ring slot of plane p-1 = it mod NE,
+    //   r3 = (p+6) mod 3 (B_x / B_y ring), r2 = (p+6) mod 2 (B_z ring)
+    int pw = wrapz(z0 - 1), qw = wrapz(z0 - 2);
+    int s_m = 0;
+    int r3 = (z0 + 5) % 3, r2 = (z0 + 5) % 2;
+    for (; !failed && it <= niter; ++it, qw = pw, pw = (pw + 1 == g.nz ? 0 : pw + 1),
+                                   s_m = (s_m + 1 == NE ? 0 : s_m + 1), r3 = (r3 == 2 ? 0 : r3 + 1),
+                                   r2 ^= 1) {
         const int p = z0 - 1 + it;
         // E^n ring slots of planes p-1 .. p+2
-        const int s_m = eslot(p - 1);
         const int s_0 = s_m + 1 == NE ? 0 : s_m + 1;
         const int s_1 = s_0 + 1 == NE ? 0 : s_0 + 1;
         const int s_2 = s_1 + 1 == NE ? 0 : s_1 + 1;
@@ -257,58 +289,52 @@ step_kernel(const __grid_constant__ FusedMaps maps, Geom g, Mult<float> m, Field
             ok = ok && mbar_wait(&bar[it % NS], (uint32_t)((it / NS) & 1));
         }
         // ---- B^{n+1/2}(p)
+        // B^{n+1/2} ring slots: plane p (current), p-1, p-2
+        const int r3m = r3 == 0 ? 2 : r3 - 1, r3mm = r3m == 0 ? 2 : r3m - 1;
         if (ok && it < niter) {
-            const int pw = wrapz(p);
-            float* Bxc = sBx(p);
-            float* Byc = sBy(p);
-            float* Bzc = sBz(p);
+            // issue the next plane's B^{n-1/2} loads first: they complete during this plane's work
+            if (it + 1 < niter) load_bold(pw + 1 == g.nz ? 0 : pw + 1, bn);
+            float* Bxc = sB + r3 * BSLOT;
+            float* Byc = sB + (3 + r3) * BSLOT;
+            float* Bzc = sB + (6 + r2) * BSLOT;
             if (bseg) {
                 const int e = (b_by + 2) * EW + (b_bx + 4);
-                float dz[4], dy[4], bxv[4], byv[4], bzv[4];
+                float dz[W], dy[W], bxv[W], byv[W], bzv[W];
                 // B_x = B_x + (D*_z E_y - D*_y E_z)
-                dstar4<2>((Pm + 1 * ESLOT), (P0 + 1 * ESLOT), (P1 + 1 * ESLOT), (P2 + 1 * ESLOT), e, m.cA[2], m.cD[2],
-                          m.cB[2][0], m.cB[2][1], dz);
-                dstar4<1>((Pm + 2 * ESLOT), (P0 + 2 * ESLOT), (P1 + 2 * ESLOT), nullptr, e, m.cA[1], m.cD[1],
-                          m.cB[1][0], m.cB[1][2], dy);
-                bxv[0] = bo[0].x + (dz[0] - dy[0]);
-                bxv[1] = bo[0].y + (dz[1] - dy[1]);
-                bxv[2] = bo[0].z + (dz[2] - dy[2]);
-                bxv[3] = bo[0].w + (dz[3] - dy[3]);
+                dstarw<2>((Pm + 1 * ESLOT), (P0 + 1 * ESLOT), (P1 + 1 * ESLOT), (P2 + 1 * ESLOT), e,
+                          m.cA[2], m.cD[2], m.cB[2][0], m.cB[2][1], dz);
+                dstarw<1>((Pm + 2 * ESLOT), (P0 + 2 * ESLOT), (P1 + 2 * ESLOT), nullptr, e, m.cA[1],
+                          m.cD[1], m.cB[1][0], m.cB[1][2], dy);
+#pragma unroll
+                for (int u = 0; u < W; ++u) bxv[u] = bo[0][u] + (dz[u] - dy[u]);
                 // B_y = B_y + (D*_x E_z - D*_z E_x)
-                dstar4<0>((Pm + 2 * ESLOT), (P0 + 2 * ESLOT), (P1 + 2 * ESLOT), nullptr, e, m.cA[0], m.cD[0],
-                          m.cB[0][1], m.cB[0][2], dy);
-                dstar4<2>((Pm + 0 * ESLOT), (P0 + 0 * ESLOT), (P1 + 0 * ESLOT), (P2 + 0 * ESLOT), e, m.cA[2], m.cD[2],
-                          m.cB[2][0], m.cB[2][1], dz);
-                byv[0] = bo[1].x + (dy[0] - dz[0]);
-                byv[1] = bo[1].y + (dy[1] - dz[1]);
-                byv[2] = bo[1].z + (dy[2] - dz[2]);
-                byv[3] = bo[1].w + (dy[3] - dz[3]);
+                dstarw<0>((Pm + 2 * ESLOT), (P0 + 2 * ESLOT), (P1 + 2 * ESLOT), nullptr, e, m.cA[0],
+                          m.cD[0], m.cB[0][1], m.cB[0][2], dy);
+                dstarw<2>((Pm + 0 * ESLOT), (P0 + 0 * ESLOT), (P1 + 0 * ESLOT), (P2 + 0 * ESLOT), e,
+                          m.cA[2], m.cD[2], m.cB[2][0], m.cB[2][1], dz);
+#pragma unroll
+                for (int u = 0; u < W; ++u) byv[u] = bo[1][u] + (dy[u] - dz[u]);
                 // B_z = B_z + (D*_y E_x - D*_x E_y)
-                dstar4<1>((Pm + 0 * ESLOT), (P0 + 0 * ESLOT), (P1 + 0 * ESLOT), nullptr, e, m.cA[1], m.cD[1],
-                          m.cB[1][0], m.cB[1][2], dy);
-                dstar4<0>((Pm + 1 * ESLOT), (P0 + 1 * ESLOT), (P1 + 1 * ESLOT), nullptr, e, m.cA[0], m.cD[0],
-                          m.cB[0][1], m.cB[0][2], dz);
-                bzv[0] = bo[2].x + (dy[0] - dz[0]);
-                bzv[1] = bo[2].y + (dy[1] - dz[1]);
-                bzv[2] = bo[2].z + (dy[2] - dz[2]);
-                bzv[3] = bo[2].w + (dy[3] - dz[3]);
+                dstarw<1>((Pm + 0 * ESLOT), (P0 + 0 * ESLOT), (P1 + 0 * ESLOT), nullptr, e, m.cA[1],
+                          m.cD[1], m.cB[1][0], m.cB[1][2], dy);
+                dstarw<0>((Pm + 1 * ESLOT), (P0 + 1 * ESLOT), (P1 + 1 * ESLOT), nullptr, e, m.cA[0],
+                          m.cD[0], m.cB[0][1], m.cB[0][2], dz);
+#pragma unroll
+                for (int u = 0; u < W; ++u) bzv[u] = bo[2][u] + (dy[u] - dz[u]);
                 if (spy != nullptr) {
                     const float f = spy[b_y] * spz[pw];
 #pragma unroll
-                    for (int u = 0; u < 4; ++u) { bxv[u] *= f; byv[u] *= f; bzv[u] *= f; }
+                    for (int u = 0; u < W; ++u) { bxv[u] *= f; byv[u] *= f; bzv[u] *= f; }
                 }
                 const int bi = (b_by + 1) * BW + (b_bx + 4);
-                const float4 vx = make_float4(bxv[0], bxv[1], bxv[2], bxv[3]);
-                const float4 vy = make_float4(byv[0], byv[1], byv[2], byv[3]);
-                const float4 vz = make_float4(bzv[0], bzv[1], bzv[2], bzv[3]);
-                *reinterpret_cast<float4*>(Bxc + bi) = vx;
-                *reinterpret_cast<float4*>(Byc + bi) = vy;
-                *reinterpret_cast<float4*>(Bzc + bi) = vz;
+                stv(Bxc, bi, bxv);
+                stv(Byc, bi, byv);
+                stv(Bzc, bi, bzv);
                 if (p >= z0 && b_by >= 0) {
                     const SegDst d = seg_dst(g, x0 + b_bx, y0 + b_by, pw, edge);
-                    put_seg(out.c[3], d, g.nx, edge, vx);
-                    put_seg(out.c[4], d, g.nx, edge, vy);
-                    put_seg(out.c[5], d, g.nx, edge, vz);
+                    put_seg(out.c[3], d, g.nx, edge, bxv);
+                    put_seg(out.c[4], d, g.nx, edge, byv);
+                    put_seg(out.c[5], d, g.nx, edge, bzv);
                 }
             } else if (bcol) {
                 // halo column x0-1: one cell, scalar taps (not stored to HBM)
@@ -329,9 +355,9 @@ step_kernel(const __grid_constant__ FusedMaps maps, Geom g, Mult<float> m, Field
     dstar_taps(E1[c][e], E0[c][e], E2[c][e], Em[c][e], E1[c][e + 1], E0[c][e + 1],             \
                E1[c][e - 1], E0[c][e - 1], E1[c][e + EW], E0[c][e + EW], E1[c][e - EW],        \
                E0[c][e - EW], m.cA[2], m.cD[2], m.cB[2][0], m.cB[2][1])
-                float bxs = bo[0].x + (DZ(1) - DY(2));
-                float bys = bo[1].x + (DX(2) - DZ(0));
-                float bzs = bo[2].x + (DY(0) - DX(1));
+                float bxs = bo[0][0] + (DZ(1) - DY(2));
+                float bys = bo[1][0] + (DX(2) - DZ(0));
+                float bzs = bo[2][0] + (DY(0) - DX(1));
 #undef DX
 #undef DY
 #undef DZ
@@ -347,65 +373,67 @@ step_kernel(const __grid_constant__ FusedMaps maps, Geom g, Mult<float> m, Field
                 Bzc[bi] = bzs;
             }
             // prefetch next plane's B^{n-1/2} while E is formed
-            if (it + 1 < niter) load_bold(p + 1);
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+#pragma unroll
+                for (int u = 0; u < W; ++u) bo[c][u] = bn[c][u];
         }
         // ---- E^{n+1}(p - 1)
         const int q = p - 1;
         if (ok && q >= z0 && q < zend && tid < NSEG * TY) {
-            const int qw = wrapz(q);
-            const int by = tid / NSEG, bx = 4 * (tid % NSEG);
+            const int by = tid / NSEG, bx = W * (tid % NSEG);
             const int e = (by + 2) * EW + (bx + 4);
             const int bi = (by + 1) * BW + (bx + 4);
-            const float* Bxc = sBx(q);
-            const float* Byc = sBy(q);
-            const float* Bzc = sBz(q);
-            const float* Bxp = sBx(q - 1);
-            const float* Byp = sBy(q - 1);
-            const float4 ex4 = ld4((Pm + 0 * ESLOT), e), ey4 = ld4((Pm + 1 * ESLOT), e), ez4 = ld4((Pm + 2 * ESLOT), e);
-            const float4 bz0 = ld4(Bzc, bi), bzym = ld4(Bzc, bi - BW), bzxm = ld4(Bzc, bi - 4);
-            const float4 by0 = ld4(Byc, bi), byzm = ld4(Byp, bi), byxm = ld4(Byc, bi - 4);
-            const float4 bx0 = ld4(Bxc, bi), bxzm = ld4(Bxp, bi), bxym = ld4(Bxc, bi - BW);
-            const float E0x[4] = {ex4.x, ex4.y, ex4.z, ex4.w};
-            const float E0y[4] = {ey4.x, ey4.y, ey4.z, ey4.w};
-            const float E0z[4] = {ez4.x, ez4.y, ez4.z, ez4.w};
-            const float Bz[5] = {bzxm.w, bz0.x, bz0.y, bz0.z, bz0.w};   // Bz[1 + u + dx]
-            const float Bzy[4] = {bzym.x, bzym.y, bzym.z, bzym.w};
-            const float By[5] = {byxm.w, by0.x, by0.y, by0.z, by0.w};
-            const float Byz[4] = {byzm.x, byzm.y, byzm.z, byzm.w};
-            const float Bx[4] = {bx0.x, bx0.y, bx0.z, bx0.w};
-            const float Bxz[4] = {bxzm.x, bxzm.y, bxzm.z, bxzm.w};
-            const float Bxy[4] = {bxym.x, bxym.y, bxym.z, bxym.w};
-            float ex[4], ey[4], ez[4];
+            const float* Bxc = sB + r3m * BSLOT;
+            const float* Byc = sB + (3 + r3m) * BSLOT;
+            const float* Bzc = sB + (6 + (r2 ^ 1)) * BSLOT;
+            const float* Bxp = sB + r3mm * BSLOT;
+            const float* Byp = sB + (3 + r3mm) * BSLOT;
+            float E0x[W], E0y[W], E0z[W];
+            ldv(Pm + 0 * ESLOT, e, E0x);
+            ldv(Pm + 1 * ESLOT, e, E0y);
+            ldv(Pm + 2 * ESLOT, e, E0z);
+            float Bz[W + 1], By[W + 1], tmp[W];   // [0] = value at x-1, [1 + u] = cell u
+            float Bzy[W], Byz[W], Bx[W], Bxz[W], Bxy[W];
+            ldv(Bzc, bi, Bz + 1);
+            ldv(Bzc, bi - W, tmp);
+            Bz[0] = tmp[W - 1];
+            ldv(Bzc, bi - BW, Bzy);
+            ldv(Byc, bi, By + 1);
+            ldv(Byc, bi - W, tmp);
+            By[0] = tmp[W - 1];
+            ldv(Byp, bi, Byz);
+            ldv(Bxc, bi, Bx);
+            ldv(Bxp, bi, Bxz);
+            ldv(Bxc, bi - BW, Bxy);
+            float ex[W], ey[W], ez[W];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
+            for (int u = 0; u < W; ++u) {
                 ex[u] = ampere_comp(E0x[u], Bz[1 + u], Bzy[u], By[1 + u], Byz[u], m.cE[1], m.cE[2]);
                 ey[u] = ampere_comp(E0y[u], Bx[u], Bxz[u], Bz[1 + u], Bz[u], m.cE[2], m.cE[0]);
                 ez[u] = ampere_comp(E0z[u], By[1 + u], By[u], Bx[u], Bxy[u], m.cE[0], m.cE[1]);
             }
             const int i0 = x0 + bx, j = y0 + by;
             if (jx_row != nullptr) {
-                const float4 j4 = __ldg(reinterpret_cast<const float4*>(jx_row + i0));
-                const float jv[4] = {j4.x, j4.y, j4.z, j4.w};
+                float jv[W];
+                unpackv(__ldg(reinterpret_cast<const Vec*>(jx_row + i0)), jv);
                 const float sy = jyz[j], sz = jyz[g.ny + qw];
 #pragma unroll
-                for (int u = 0; u < 4; ++u) ex[u] = fma(mdt, (jv[u] * sy) * sz, ex[u]);
+                for (int u = 0; u < W; ++u) ex[u] = fma(mdt, (jv[u] * sy) * sz, ex[u]);
             }
             if (spy != nullptr) {
                 const float f = spy[j] * spz[qw];
 #pragma unroll
-                for (int u = 0; u < 4; ++u) { ex[u] *= f; ey[u] *= f; ez[u] *= f; }
+                for (int u = 0; u < W; ++u) { ex[u] *= f; ey[u] *= f; ez[u] *= f; }
             }
-            const float4 vx = make_float4(ex[0], ex[1], ex[2], ex[3]);
-            const float4 vy = make_float4(ey[0], ey[1], ey[2], ey[3]);
-            const float4 vz = make_float4(ez[0], ez[1], ez[2], ez[3]);
             const SegDst d = seg_dst(g, i0, j, qw, edge);
-            put_seg(out.c[0], d, g.nx, edge, vx);
-            put_seg(out.c[1], d, g.nx, edge, vy);
-            put_seg(out.c[2], d, g.nx, edge, vz);
+            put_seg(out.c[0], d, g.nx, edge, ex);
+            put_seg(out.c[1], d, g.nx, edge, ey);
+            put_seg(out.c[2], d, g.nx, edge, ez);
             if (h0 != nullptr) {
-                put_seg(h0, d, g.nx, edge, vx);
-                put_seg(h1, d, g.nx, edge, vy);
-                put_seg(h2, d, g.nx, edge, vz);
+                put_seg(h0, d, g.nx, edge, ex);
+                put_seg(h1, d, g.nx, edge, ey);
+                put_seg(h2, d, g.nx, edge, ez);
             }
         }
         bool ok_next = true;
