@@ -17,7 +17,7 @@
 namespace fdtd {
 namespace adj32 {
 
-constexpr int TX = 64, TY = 8, TZ = 32, D = 1, NT = 128;
+constexpr int TX = 64, TY = 8, D = 1, NT = 128;   // z-chunk length: launch parameter
 constexpr int EW = TX + 8, EH = TY + 4, EPL = EW * EH;
 constexpr int ESLOT = ((EPL * 4 + 127) / 128) * 128 / 4;
 constexpr int NE = D + 4, NS = D + 1;
@@ -106,7 +106,7 @@ __device__ __forceinline__ void st4(float* F, long long idx, float4 v) {
 __global__ void __launch_bounds__(NT, 3)
 adjB_kernel(const __grid_constant__ FusedMaps maps, Geom g, Mult<float> m, FieldSet<float> lam,
             const float* __restrict__ spy, const float* __restrict__ spz,
-            double* __restrict__ partials, int* __restrict__ err) {
+            double* __restrict__ partials, int tz, int* __restrict__ err) {
     extern __shared__ __align__(128) unsigned char smem[];
     float* sE = reinterpret_cast<float*>(smem);
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem + OFF_BAR);
@@ -117,8 +117,8 @@ adjB_kernel(const __grid_constant__ FusedMaps maps, Geom g, Mult<float> m, Field
     w /= ntx;
     const int ty = w % nty;
     const int zc = w / nty;
-    const int x0 = tx * TX, y0 = ty * TY, z0 = zc * TZ;
-    const int zend = min(z0 + TZ, g.nz);
+    const int x0 = tx * TX, y0 = ty * TY, z0 = zc * tz;
+    const int zend = min(z0 + tz, g.nz);
     const int niter = zend - z0;
     const int tid = threadIdx.x;
     const bool edge = (x0 < PX) || (x0 + TX > g.nx - PX) || (y0 < PY) || (y0 + TY > g.ny - PY);
@@ -315,8 +315,16 @@ bool adjoint32_supported(const Geom& g) {
            g.ny >= adj32::TY;
 }
 
+static int adjoint32_tz(const Geom& g) {
+    static int slots = -1;
+    if (slots < 0) slots = resident_slots((const void*)adj32::adjB_kernel, adj32::NT, adj32::SMEM);
+    // shorter chunks suit this kernel: at 256^3, 19 planes 0.37 ms, 26: 0.38, 37: 0.42
+    return zchunk_len((g.nx / adj32::TX) * (g.ny / adj32::TY), g.nz, slots, 16, 24);
+}
+
 int adjoint32_blocks(const Geom& g) {
-    return (g.nx / adj32::TX) * (g.ny / adj32::TY) * ((g.nz + adj32::TZ - 1) / adj32::TZ);
+    const int tz = adjoint32_tz(g);
+    return (g.nx / adj32::TX) * (g.ny / adj32::TY) * ((g.nz + tz - 1) / tz);
 }
 
 bool adjoint32_prepare() {
@@ -327,8 +335,8 @@ bool adjoint32_prepare() {
 void launch_adjoint32_B(const FusedMaps& maps, const Geom& g, const Mult<float>& m,
                         FieldSet<float> lam, const float* spy, const float* spz, double* partials,
                         int* err, cudaStream_t st) {
-    adj32::adjB_kernel<<<adjoint32_blocks(g), adj32::NT, adj32::SMEM, st>>>(maps, g, m, lam, spy,
-                                                                             spz, partials, err);
+    adj32::adjB_kernel<<<adjoint32_blocks(g), adj32::NT, adj32::SMEM, st>>>(
+        maps, g, m, lam, spy, spz, partials, adjoint32_tz(g), err);
 }
 
 }  // namespace fdtd

@@ -25,7 +25,7 @@ namespace fdtd {
 namespace f32seg {
 
 constexpr int W = 4;                                            // cells per thread (along x)
-constexpr int TX = 64, TY = 8, TZ = 32, D = 1;
+constexpr int TX = 64, TY = 8, D = 1;   // z-chunk length: launch parameter (zchunk_len)
 constexpr int NSEG = TX / W;                                    // segments per row
 constexpr int NT = ((NSEG * (TY + 1) + TY + 1 + 31) / 32) * 32;  // B tasks + halo column
 constexpr int EW = TX + 8, EH = TY + 4, EPL = EW * EH;        // E box 72 x 12 (x0-4.., y0-2..)
@@ -124,46 +124,46 @@ __device__ __forceinline__ void dstarw(const float* Fm, const float* F0, const f
     }
 }
 
-__device__ __forceinline__ void stv(float* F, long long idx, const float* v) {
+__device__ __forceinline__ void stv(float* F, unsigned idx, const float* v) {
     Vec a;
     packv(v, a);
     *reinterpret_cast<Vec*>(F + idx) = a;
 }
 
-// Destination of one W-cell segment (i0 .. i0+W-1, j, k) and of its periodic images
-// (images exist only for segments within PX of the x ends or PY of the y ends).
-struct SegDst {
-    long long o1, o2;   // owned row offset; image row offset (valid if yimg)
-    bool xl, xr, yimg;
+// Destination of one W-cell segment (i0 .. i0+W-1, j) in every plane, fixed for the whole
+// launch: the in-plane offset of the owned cells and, for a segment within PX of the x ends or
+// PY of the y ends, the offsets of its periodic images (the ghosts of the padded layout).
+// All offsets are 32-bit element offsets (the padded array has fewer than 2^31 elements).
+struct SegOut {
+    unsigned ro;   // in-plane offset of cell i0
+    int xi, yi;    // x image offset (+-nx or 0), y image offset (+-ny nxp or 0)
+    bool img;
 };
 
-__device__ __forceinline__ SegDst seg_dst(const Geom& g, int i0, int j, int k, bool edge_tile) {
-    SegDst d;
-    const long long rowk = (long long)k * g.nyp;
-    d.o1 = (rowk + j + PY) * g.nxp + PX + i0;
-    d.xl = edge_tile && i0 < PX;
-    d.xr = edge_tile && i0 >= g.nx - PX;
-    d.yimg = false;
-    d.o2 = 0;
+__device__ __forceinline__ SegOut seg_out(const Geom& g, int i0, int j, bool edge_tile) {
+    SegOut d;
+    d.ro = (unsigned)((j + PY) * g.nxp + PX + i0);
+    d.xi = 0;
+    d.yi = 0;
     if (edge_tile) {
-        int jj = 0;
-        if (j < PY) { jj = j + g.ny; d.yimg = true; }
-        else if (j >= g.ny - PY) { jj = j - g.ny; d.yimg = true; }
-        d.o2 = (rowk + jj + PY) * g.nxp + PX + i0;
+        if (i0 < PX) d.xi = g.nx;
+        else if (i0 >= g.nx - PX) d.xi = -g.nx;
+        if (j < PY) d.yi = g.ny * g.nxp;
+        else if (j >= g.ny - PY) d.yi = -g.ny * g.nxp;
     }
+    d.img = (d.xi | d.yi) != 0;
     return d;
 }
 
-__device__ __forceinline__ void put_seg(float* F, const SegDst& d, int nx, bool edge_tile,
-                                        const float* v) {
-    stv(F, d.o1, v);
-    if (edge_tile) {
-        if (d.xl) stv(F, d.o1 + nx, v);
-        if (d.xr) stv(F, d.o1 - nx, v);
-        if (d.yimg) {
-            stv(F, d.o2, v);
-            if (d.xl) stv(F, d.o2 + nx, v);
-            if (d.xr) stv(F, d.o2 - nx, v);
+// store a segment at plane offset `po` (plane index x padded plane size) and its images
+__device__ __forceinline__ void put_seg(float* F, unsigned po, const SegOut& d, const float* v) {
+    const unsigned o = po + d.ro;
+    stv(F, o, v);
+    if (d.img) {
+        if (d.xi) stv(F, o + d.xi, v);
+        if (d.yi) {
+            stv(F, o + d.yi, v);
+            if (d.xi) stv(F, o + d.yi + d.xi, v);
         }
     }
 }
@@ -172,7 +172,7 @@ __global__ void __launch_bounds__(NT, 3)
 step_kernel(const __grid_constant__ FusedMaps maps, Geom g, Mult<float> m, FieldSet<float> in,
             FieldSet<float> out, const float* __restrict__ spy, const float* __restrict__ spz,
             const float* __restrict__ jyz, const float* __restrict__ jx_row,
-            float* __restrict__ h0, float* __restrict__ h1, float* __restrict__ h2,
+            float* __restrict__ h0, float* __restrict__ h1, float* __restrict__ h2, int tz,
             int* __restrict__ err) {
     extern __shared__ __align__(128) unsigned char smem[];
     float* sE = reinterpret_cast<float*>(smem + OFF_E);
@@ -185,8 +185,8 @@ step_kernel(const __grid_constant__ FusedMaps maps, Geom g, Mult<float> m, Field
     w /= ntx;
     const int ty = w % nty;
     const int zc = w / nty;
-    const int x0 = tx * TX, y0 = ty * TY, z0 = zc * TZ;
-    const int zend = min(z0 + TZ, g.nz);
+    const int x0 = tx * TX, y0 = ty * TY, z0 = zc * tz;
+    const int zend = min(z0 + tz, g.nz);
     const int niter = zend - z0 + 1;   // B planes z0-1 .. zend-1
     const int tid = threadIdx.x;
     // tiles that own cells with periodic images (the ghosts of the padded layout)
@@ -212,9 +212,14 @@ step_kernel(const __grid_constant__ FusedMaps maps, Geom g, Mult<float> m, Field
     const bool bcol = !bseg && tid < NSEG * (TY + 1) + TY + 1;
     const int b_bx = bseg ? W * (tid % NSEG) : -1;
     const int b_by = bseg ? tid / NSEG - 1 : tid - NSEG * (TY + 1) - 1;
-    const long long b_off = (long long)(y0 + b_by + PY) * g.nxp + (x0 + b_bx + PX);
+    const unsigned b_off = (unsigned)((y0 + b_by + PY) * g.nxp + (x0 + b_bx + PX));
+    const unsigned plane = (unsigned)g.plane;
     int b_y = y0 + b_by;
     if (b_y < 0) b_y += g.ny;
+    // owned-cell destinations of this thread's B segment and E segment
+    const SegOut b_dst = seg_out(g, x0 + b_bx, y0 + (b_by < 0 ? 0 : b_by), edge);
+    const int e_by = tid / NSEG, e_bx = W * (tid % NSEG);
+    const SegOut e_dst = seg_out(g, x0 + e_bx, y0 + (e_by < TY ? e_by : 0), edge);
 
     if (tid == 0) {
         for (int s = 0; s <= NS; ++s) mbar_init(&bar[s], 1);
@@ -241,7 +246,7 @@ step_kernel(const __grid_constant__ FusedMaps maps, Geom g, Mult<float> m, Field
         for (int u = 0; u < W; ++u) bo[c][u] = 0.0f;
     float bn[3][W];   // next plane's B^{n-1/2}, loaded at the start of the current B phase
     auto load_bold = [&](int qw, float (&dst)[3][W]) {   // qw: wrapped plane index
-        const long long o = (long long)qw * g.plane + b_off;
+        const unsigned o = (unsigned)qw * plane + b_off;
         if (bseg) {
 #pragma unroll
             for (int c = 0; c < 3; ++c) unpackv(__ldg(reinterpret_cast<const Vec*>(in.c[3 + c] + o)), dst[c]);
@@ -331,10 +336,10 @@ step_kernel(const __grid_constant__ FusedMaps maps, Geom g, Mult<float> m, Field
                 stv(Byc, bi, byv);
                 stv(Bzc, bi, bzv);
                 if (p >= z0 && b_by >= 0) {
-                    const SegDst d = seg_dst(g, x0 + b_bx, y0 + b_by, pw, edge);
-                    put_seg(out.c[3], d, g.nx, edge, bxv);
-                    put_seg(out.c[4], d, g.nx, edge, byv);
-                    put_seg(out.c[5], d, g.nx, edge, bzv);
+                    const unsigned po = (unsigned)pw * plane;
+                    put_seg(out.c[3], po, b_dst, bxv);
+                    put_seg(out.c[4], po, b_dst, byv);
+                    put_seg(out.c[5], po, b_dst, bzv);
                 }
             } else if (bcol) {
                 // halo column x0-1: one cell, scalar taps (not stored to HBM)
@@ -381,7 +386,7 @@ step_kernel(const __grid_constant__ FusedMaps maps, Geom g, Mult<float> m, Field
         // ---- E^{n+1}(p - 1)
         const int q = p - 1;
         if (ok && q >= z0 && q < zend && tid < NSEG * TY) {
-            const int by = tid / NSEG, bx = W * (tid % NSEG);
+            const int by = e_by, bx = e_bx;
             const int e = (by + 2) * EW + (bx + 4);
             const int bi = (by + 1) * BW + (bx + 4);
             const float* Bxc = sB + r3m * BSLOT;
@@ -426,14 +431,14 @@ step_kernel(const __grid_constant__ FusedMaps maps, Geom g, Mult<float> m, Field
 #pragma unroll
                 for (int u = 0; u < W; ++u) { ex[u] *= f; ey[u] *= f; ez[u] *= f; }
             }
-            const SegDst d = seg_dst(g, i0, j, qw, edge);
-            put_seg(out.c[0], d, g.nx, edge, ex);
-            put_seg(out.c[1], d, g.nx, edge, ey);
-            put_seg(out.c[2], d, g.nx, edge, ez);
+            const unsigned po = (unsigned)qw * plane;
+            put_seg(out.c[0], po, e_dst, ex);
+            put_seg(out.c[1], po, e_dst, ey);
+            put_seg(out.c[2], po, e_dst, ez);
             if (h0 != nullptr) {
-                put_seg(h0, d, g.nx, edge, ex);
-                put_seg(h1, d, g.nx, edge, ey);
-                put_seg(h2, d, g.nx, edge, ez);
+                put_seg(h0, po, e_dst, ex);
+                put_seg(h1, po, e_dst, ey);
+                put_seg(h2, po, e_dst, ez);
             }
         }
         bool ok_next = true;
@@ -463,8 +468,9 @@ step_kernel(const __grid_constant__ FusedMaps maps, Geom g, Mult<float> m, Field
 }  // namespace f32seg
 
 bool fused32_supported(const Geom& g) {
+    // 32-bit element offsets inside the kernel
     return g.nx % f32seg::TX == 0 && g.ny % f32seg::TY == 0 && g.nx >= f32seg::TX &&
-           g.ny >= f32seg::TY;
+           g.ny >= f32seg::TY && g.total < (1LL << 31);
 }
 
 bool fused32_prepare() {
@@ -472,13 +478,54 @@ bool fused32_prepare() {
                                 (int)f32seg::SMEM) == cudaSuccess;
 }
 
+int resident_slots(const void* kernel, int threads, size_t smem) {
+    int dev = 0, sms = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) != cudaSuccess ||
+        sms <= 0 || per_sm <= 0)
+        return 0;
+    return sms * per_sm;
+}
+
+int zchunk_len(int tiles_xy, int nz, int slots, int tz_min, int tz_max) {
+    // A CTA marches tz planes plus about two planes of fixed cost (the z-halo B plane and the
+    // prologue copies); CTAs run in waves of `slots`.  Minimise waves x (tz + 2) over chunk
+    // lengths tz_min..tz_max; ties go to the longer chunk.
+    const int hi = nz < tz_max ? nz : tz_max;
+    if (slots <= 0) return hi;
+    int best = hi;
+    long long best_cost = -1;
+    for (int tz = hi; tz >= tz_min || tz == nz; --tz) {
+        const long long ctas = (long long)tiles_xy * ((nz + tz - 1) / tz);
+        const long long waves = (ctas + slots - 1) / slots;
+        const long long cost = waves * (tz + 2);
+        if (best_cost < 0 || cost < best_cost) {
+            best_cost = cost;
+            best = tz;
+        }
+        if (tz <= 1) break;
+    }
+    return best;
+}
+
+static int fused32_tz(const Geom& g) {
+    using namespace f32seg;
+    static int slots = -1;
+    if (slots < 0) slots = resident_slots((const void*)step_kernel, NT, SMEM);
+    // measured at 256^3 (456 resident CTAs): 37-plane chunks (2 full waves) 0.218 ms per step,
+    // 32-plane chunks (2.25 waves) 0.269 ms
+    return zchunk_len((g.nx / TX) * (g.ny / TY), g.nz, slots, 16, 64);
+}
+
 void launch_fused32(const FusedMaps& maps, FieldSet<float> in, const Geom& g, const Mult<float>& m,
                     FieldSet<float> out, const float* spy, const float* spz, const float* jyz,
                     const float* jx_row, float* hist_E[3], int* err, cudaStream_t st) {
     using namespace f32seg;
-    const int nblk = (g.nx / TX) * (g.ny / TY) * ((g.nz + TZ - 1) / TZ);
+    const int tz = fused32_tz(g);
+    const int nblk = (g.nx / TX) * (g.ny / TY) * ((g.nz + tz - 1) / tz);
     step_kernel<<<nblk, NT, SMEM, st>>>(maps, g, m, in, out, spy, spz, jyz, jx_row, hist_E[0],
-                                        hist_E[1], hist_E[2], err);
+                                        hist_E[1], hist_E[2], tz, err);
 }
 
 }  // namespace fdtd

@@ -130,6 +130,12 @@ struct GradScale {
 void launch_reduce_grad(const double* part, int nblocks, GradScale sc, double* grad12,
                         cudaStream_t st);
 
+// Resident CTAs of `kernel` on the whole device (SMs x CTAs per SM; 0 if unknown), and the
+// z-chunk length in [tz_min, tz_max] of a tiled plane-marching kernel with `tiles_xy` CTAs per
+// z-chunk that fills whole waves of `slots` CTAs best.
+int resident_slots(const void* kernel, int threads, size_t smem);
+int zchunk_len(int tiles_xy, int nz, int slots, int tz_min, int tz_max);
+
 // thread-local error message
 void set_error(const char* fmt, ...);
 
