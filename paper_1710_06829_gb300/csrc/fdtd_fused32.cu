@@ -1,171 +1,136 @@
 // FP32 fused leapfrog step (one launch per leapfrog step).
 //
-// A CTA owns a 64 x 8 (x, y) tile and a chunk of 32 planes and marches through it.  E^n planes
-// arrive by TMA (cp.async.bulk.tensor.3d) as 72 x 12 boxes (x0-4 .., y0-2 ..) into a ring of five
-// shared-memory slots, one plane ahead of use, completion signalled on mbarriers.  Iteration `it`
-// forms B^{n+1/2} on plane p = z0-1+it (tile, halo row y0-1, halo column x0-1) and E^{n+1} on
-// plane p-1, so one block barrier per plane suffices; B^{n+1/2} lives in a small shared ring
-// (B_x, B_y: 3 planes, B_z: 2 planes).  B^{n-1/2} is not staged: each thread prefetches its
-// own segment of the next plane from HBM into registers while the current plane is computed.
+// A CTA owns a 64 x 8 (x, y) tile and a chunk of tz planes (a launch parameter) and marches
+// through it.  E^n planes arrive by TMA (cp.async.bulk.tensor.3d) as 72 x 12 boxes (x0-4 ..,
+// y0-2 ..) into a ring of five shared-memory slots, one plane ahead of use, completion signalled
+// on mbarriers.  Iteration `it` forms B^{n+1/2} on plane p = z0-1+it (tile, halo row y0-1, halo
+// column x0-1) and E^{n+1} on plane p-1, so one block barrier per plane suffices; B^{n+1/2}
+// lives in a small shared ring (B_x, B_y: 3 planes, B_z: 2 planes).  B^{n-1/2} is not staged:
+// each thread prefetches its own segment of the next plane from HBM into registers while the
+// current plane is computed.
 //
-// Work per thread: W consecutive cells of one row.  Every stencil row a thread needs is read as
-// W-wide shared-memory vectors (a window of 3W values covers the x reach -1 .. W+1), so one
-// load serves several taps; a warp covers whole rows, so a vector load of a warp never
-// conflicts.  Owned results leave as W-wide stores; a segment at the edge of the domain also
-// writes its periodic images (the ghosts of the padded layout).  Plane bookkeeping uses
-// counters (no integer division in the loop).
+// Work per thread: W = 4 consecutive cells of one row, the same row in the B and the E phase.
+// A warp covers two whole rows.  Each stencil row a thread needs is read once as a 16-byte
+// shared-memory vector of its own four cells; the values one cell beyond the segment (x-1,
+// x+4, x+5) come from the neighbouring lanes by warp shuffle, and only the lanes at the ends
+// of a row (and the halo-column lanes) read them from shared memory.  Differences along an
+// axis are formed once per cell and shared with the neighbouring cells (dstar_diff), which
+// halves the shared-memory traffic of the stencil compared with reading three-vector windows.
+// Owned results leave as 16-byte stores; a segment at the edge of the domain also writes its
+// periodic images (the ghosts of the padded layout).  Plane bookkeeping uses counters (no
+// integer division in the loop).
 //
-// Per-cell arithmetic is dstar_taps / ampere_comp with the same operands in the same order as
-// the reference-form kernels: the fields are bitwise equal.  Every mbarrier wait is bounded
-// (fdtd_tma.cuh); on expiry the CTA raises *err, drains its copies in flight (bounded) and
-// returns.
-#include "fdtd_tma.cuh"
+// Per-cell arithmetic is dstar_diff / ampere_comp on the same differences in the same order as
+// the reference-form kernels (dstar_taps): the fields are bitwise equal.  Every mbarrier wait is
+// bounded (fdtd_tma.cuh); on expiry the CTA raises *err, drains its copies in flight (bounded)
+// and returns.
+#include "fdtd_seg.cuh"
 
 namespace fdtd {
 namespace f32seg {
 
+using namespace seg;
+
 constexpr int W = 4;                                            // cells per thread (along x)
 constexpr int TX = 64, TY = 8, D = 1;   // z-chunk length: launch parameter (zchunk_len)
 constexpr int NSEG = TX / W;                                    // segments per row
-constexpr int NT = ((NSEG * (TY + 1) + TY + 1 + 31) / 32) * 32;  // B tasks + halo column
+constexpr int NBT = NSEG * (TY + 1) + TY + 1;                   // B tasks: rows + halo column
+constexpr int NT = ((NBT + 31) / 32) * 32;
 constexpr int EW = TX + 8, EH = TY + 4, EPL = EW * EH;        // E box 72 x 12 (x0-4.., y0-2..)
 constexpr int ESLOT = ((EPL * 4 + 127) / 128) * 128 / 4;        // floats per E slot
 constexpr int BW = TX + 4, BH = TY + 1, BPL = BW * BH;         // B^{n+1/2} plane: x0-4.., y0-1..
 constexpr int BSLOT = ((BPL * 4 + 127) / 128) * 128 / 4;
 constexpr int NE = D + 4, NS = D + 1;
-constexpr size_t OFF_E = 0;
+constexpr size_t OFF_E = 128;
 constexpr size_t OFF_BN = OFF_E + (size_t)NE * 3 * ESLOT * 4;   // Bx[3], By[3], Bz[2]
 constexpr size_t OFF_BAR = OFF_BN + (size_t)8 * BSLOT * 4;
 constexpr size_t SMEM = OFF_BAR + (size_t)(NS + 1) * 8;
 constexpr uint32_t UNIT_BYTES = 3u * EPL * 4;
 constexpr uint32_t PRO_BYTES = 9u * EPL * 4;
+static_assert(W == 4, "the segment code below is written for 16-byte vectors of four cells");
 
-// W-wide vector of floats (8 bytes for W = 2, 16 bytes for W = 4)
-template <int N>
-struct VecT;
-template <>
-struct VecT<2> {
-    using type = float2;
-};
-template <>
-struct VecT<4> {
-    using type = float4;
-};
-using Vec = typename VecT<W>::type;
+// The three D* operators (times dt) on the four cells at in-plane index e of a field whose
+// plane slots are Fm (p-1), F0 (p), F1 (p+1), F2 (p+2).  lb / rb: this lane has no left /
+// right neighbour lane in its row, so it reads the values beyond its segment itself.
+// Differences are taken in the order of dstar_taps (same rounding).
 
-__device__ __forceinline__ void unpackv(const float2& a, float* o) { o[0] = a.x; o[1] = a.y; }
-__device__ __forceinline__ void unpackv(const float4& a, float* o) {
-    o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w;
-}
-__device__ __forceinline__ void packv(const float* o, float2& a) { a.x = o[0]; a.y = o[1]; }
-__device__ __forceinline__ void packv(const float* o, float4& a) {
-    a.x = o[0]; a.y = o[1]; a.z = o[2]; a.w = o[3];
-}
-
-__device__ __forceinline__ void ldv(const float* s, int idx, float* o) {
-    unpackv(*reinterpret_cast<const Vec*>(s + idx), o);
-}
-
-struct Win {
-    float v[3 * W];   // v[k] = F[idx - W + k]
-};
-
-__device__ __forceinline__ Win win(const float* s, int idx) {
-    Win w;
-    ldv(s, idx - W, w.v);
-    ldv(s, idx, w.v + W);
-    ldv(s, idx + W, w.v + 2 * W);
-    return w;
-}
-
-// D*_a (times dt) on the W cells starting at in-plane index e, for the field whose
-// plane slots are Fm (p-1), F0 (p), F1 (p+1), F2 (p+2).  Tap order as dstar_taps expects.
-template <int A>
-__device__ __forceinline__ void dstarw(const float* Fm, const float* F0, const float* F1,
-                                       const float* F2, int e, float cA, float cD, float cBb,
-                                       float cBc, float out[W]) {
-    if constexpr (A == 0) {   // axis x; transverse y, then z
-        const Win w0 = win(F0, e), wyp = win(F0, e + EW), wym = win(F0, e - EW);
-        const Win w1 = win(F1, e), wm = win(Fm, e);
+// D*_z: transverse x, then y
+__device__ __forceinline__ void dstar_z(const float* Fm, const float* F0, const float* F1,
+                                        const float* F2, int e, bool lb, bool rb, float cA,
+                                        float cD, float cBx, float cBy, float out[4]) {
+    const Q4 c1 = ldq(F1, e), c0 = ldq(F0, e), c2 = ldq(F2, e), cm = ldq(Fm, e);
+    const Q4 p1 = ldq(F1, e + EW), p0 = ldq(F0, e + EW), m1 = ldq(F1, e - EW),
+             m0 = ldq(F0, e - EW);
+    float d[6];   // d[k] = F1 - F0 at x-1+k
 #pragma unroll
-        for (int u = 0; u < W; ++u)
-            out[u] = dstar_taps(w0.v[W + 1 + u], w0.v[W + u], w0.v[W + 2 + u], w0.v[W - 1 + u],
-                                wyp.v[W + 1 + u], wyp.v[W + u], wym.v[W + 1 + u], wym.v[W + u],
-                                w1.v[W + 1 + u], w1.v[W + u], wm.v[W + 1 + u], wm.v[W + u], cA, cD,
-                                cBb, cBc);
-    } else if constexpr (A == 1) {   // axis y; transverse x, then z
-        const Win w0 = win(F0, e), wyp = win(F0, e + EW);
-        float a2[W], am[W], c1[W], c1p[W], cm[W], cmp[W];
-        ldv(F0, e + 2 * EW, a2);
-        ldv(F0, e - EW, am);
-        ldv(F1, e, c1);
-        ldv(F1, e + EW, c1p);
-        ldv(Fm, e, cm);
-        ldv(Fm, e + EW, cmp);
+    for (int u = 0; u < 4; ++u) d[1 + u] = c1.v[u] - c0.v[u];
+    d[0] = from_left(d[4]);
+    d[5] = from_right(d[1]);
+    if (lb) d[0] = F1[e - 1] - F0[e - 1];
+    if (rb) d[5] = F1[e + 4] - F0[e + 4];
 #pragma unroll
-        for (int u = 0; u < W; ++u)
-            out[u] = dstar_taps(wyp.v[W + u], w0.v[W + u], a2[u], am[u], wyp.v[W + 1 + u],
-                                w0.v[W + 1 + u], wyp.v[W - 1 + u], w0.v[W - 1 + u], c1p[u], c1[u],
-                                cmp[u], cm[u], cA, cD, cBb, cBc);
-    } else {   // axis z; transverse x, then y
-        const Win w1 = win(F1, e), w0 = win(F0, e);
-        float a2[W], am[W], p1[W], p0[W], m1[W], m0[W];
-        ldv(F2, e, a2);
-        ldv(Fm, e, am);
-        ldv(F1, e + EW, p1);
-        ldv(F0, e + EW, p0);
-        ldv(F1, e - EW, m1);
-        ldv(F0, e - EW, m0);
+    for (int u = 0; u < 4; ++u)
+        out[u] = dstar_diff(d[1 + u], c2.v[u], cm.v[u], d[2 + u], d[u], p1.v[u] - p0.v[u],
+                            m1.v[u] - m0.v[u], cA, cD, cBx, cBy);
+}
+
+// D*_y: transverse x, then z
+__device__ __forceinline__ void dstar_y(const float* Fm, const float* F0, const float* F1, int e,
+                                        bool lb, bool rb, float cA, float cD, float cBx,
+                                        float cBz, float out[4]) {
+    const Q4 a0 = ldq(F0, e), a1 = ldq(F0, e + EW), a2 = ldq(F0, e + 2 * EW),
+             am = ldq(F0, e - EW);
+    const Q4 b1 = ldq(F1, e), b1p = ldq(F1, e + EW), bm = ldq(Fm, e), bmp = ldq(Fm, e + EW);
+    float d[6];   // d[k] = F0(y+1) - F0(y) at x-1+k
 #pragma unroll
-        for (int u = 0; u < W; ++u)
-            out[u] = dstar_taps(w1.v[W + u], w0.v[W + u], a2[u], am[u], w1.v[W + 1 + u],
-                                w0.v[W + 1 + u], w1.v[W - 1 + u], w0.v[W - 1 + u], p1[u], p0[u],
-                                m1[u], m0[u], cA, cD, cBb, cBc);
-    }
+    for (int u = 0; u < 4; ++u) d[1 + u] = a1.v[u] - a0.v[u];
+    d[0] = from_left(d[4]);
+    d[5] = from_right(d[1]);
+    if (lb) d[0] = F0[e + EW - 1] - F0[e - 1];
+    if (rb) d[5] = F0[e + EW + 4] - F0[e + 4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+        out[u] = dstar_diff(d[1 + u], a2.v[u], am.v[u], d[2 + u], d[u], b1p.v[u] - b1.v[u],
+                            bmp.v[u] - bm.v[u], cA, cD, cBx, cBz);
 }
 
-__device__ __forceinline__ void stv(float* F, unsigned idx, const float* v) {
-    Vec a;
-    packv(v, a);
-    *reinterpret_cast<Vec*>(F + idx) = a;
-}
-
-// Destination of one W-cell segment (i0 .. i0+W-1, j) in every plane, fixed for the whole
-// launch: the in-plane offset of the owned cells and, for a segment within PX of the x ends or
-// PY of the y ends, the offsets of its periodic images (the ghosts of the padded layout).
-// All offsets are 32-bit element offsets (the padded array has fewer than 2^31 elements).
-struct SegOut {
-    unsigned ro;   // in-plane offset of cell i0
-    int xi, yi;    // x image offset (+-nx or 0), y image offset (+-ny nxp or 0)
-    bool img;
-};
-
-__device__ __forceinline__ SegOut seg_out(const Geom& g, int i0, int j, bool edge_tile) {
-    SegOut d;
-    d.ro = (unsigned)((j + PY) * g.nxp + PX + i0);
-    d.xi = 0;
-    d.yi = 0;
-    if (edge_tile) {
-        if (i0 < PX) d.xi = g.nx;
-        else if (i0 >= g.nx - PX) d.xi = -g.nx;
-        if (j < PY) d.yi = g.ny * g.nxp;
-        else if (j >= g.ny - PY) d.yi = -g.ny * g.nxp;
+// D*_x: transverse y, then z
+__device__ __forceinline__ void dstar_x(const float* Fm, const float* F0, const float* F1, int e,
+                                        bool lb, bool rb, float cA, float cD, float cBy,
+                                        float cBz, float out[4]) {
+    const Q4 R = ldq(F0, e), Yp = ldq(F0, e + EW), Ym = ldq(F0, e - EW), Z1 = ldq(F1, e),
+             Zm = ldq(Fm, e);
+    float r[7];                           // F0 at x-1 .. x+5
+    float yp[5], ym[5], z1[5], zm[5];     // x .. x+4
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        r[1 + u] = R.v[u];
+        yp[u] = Yp.v[u];
+        ym[u] = Ym.v[u];
+        z1[u] = Z1.v[u];
+        zm[u] = Zm.v[u];
     }
-    d.img = (d.xi | d.yi) != 0;
-    return d;
-}
-
-// store a segment at plane offset `po` (plane index x padded plane size) and its images
-__device__ __forceinline__ void put_seg(float* F, unsigned po, const SegOut& d, const float* v) {
-    const unsigned o = po + d.ro;
-    stv(F, o, v);
-    if (d.img) {
-        if (d.xi) stv(F, o + d.xi, v);
-        if (d.yi) {
-            stv(F, o + d.yi, v);
-            if (d.xi) stv(F, o + d.yi + d.xi, v);
-        }
+    r[0] = from_left(R.v[3]);
+    r[5] = from_right(R.v[0]);
+    r[6] = from_right(R.v[1]);
+    yp[4] = from_right(Yp.v[0]);
+    ym[4] = from_right(Ym.v[0]);
+    z1[4] = from_right(Z1.v[0]);
+    zm[4] = from_right(Zm.v[0]);
+    if (lb) r[0] = F0[e - 1];
+    if (rb) {
+        r[5] = F0[e + 4];
+        r[6] = F0[e + 5];
+        yp[4] = F0[e + EW + 4];
+        ym[4] = F0[e - EW + 4];
+        z1[4] = F1[e + 4];
+        zm[4] = Fm[e + 4];
     }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+        out[u] = dstar_diff(r[u + 2] - r[u + 1], r[u + 3], r[u], yp[u + 1] - yp[u],
+                            ym[u + 1] - ym[u], z1[u + 1] - z1[u], zm[u + 1] - zm[u], cA, cD, cBy,
+                            cBz);
 }
 
 __global__ void __launch_bounds__(NT, 3)
@@ -205,21 +170,28 @@ step_kernel(const __grid_constant__ FusedMaps maps, Geom g, Mult<float> m, Field
         for (int c = 0; c < 3; ++c) tma_load_3d(Ep(qe, c), &maps.e[c], x0, y0, wrapz(qe), b);
     };
 
-    // ---- task of this thread in the B phase
-    //   tid <  144: segment (bx = 4 (tid % 16), by = tid / 16 - 1), by in [-1, TY)
-    //   tid in [144, 153): halo column cell (bx = -1, by = tid - 145)
-    const bool bseg = tid < NSEG * (TY + 1);
-    const bool bcol = !bseg && tid < NSEG * (TY + 1) + TY + 1;
-    const int b_bx = bseg ? W * (tid % NSEG) : -1;
-    const int b_by = bseg ? tid / NSEG - 1 : tid - NSEG * (TY + 1) - 1;
+    // ---- task of this thread.  All NT threads run the B phase, so that every warp shuffle
+    // sees a full warp; the E phase is run by the threads of the owned rows.
+    //   tid <  128: owned row by = tid / 16, segment bx = 4 (tid % 16) (B and E)
+    //   tid in [128, 144): halo row by = -1, bx = 4 (tid % 16)
+    //   tid in [144, 153): halo-column segment bx = -4, by = tid - 145; of its cells only
+    //   x0-1 is used (by the E update of column x0), the other three are discarded
+    //   tid in [153, NT): idle copies of the last halo-column task (results dropped)
+    const int b_bx = tid < NSEG * (TY + 1) ? W * (tid % NSEG) : -W;
+    const int b_by = tid < NSEG * TY ? tid / NSEG
+                     : tid < NSEG * (TY + 1) ? -1 : min(tid - NSEG * (TY + 1) - 1, TY - 1);
+    const bool b_store = tid < NBT;      // writes its B^{n+1/2} segment to the shared ring
+    const bool b_own = tid < NSEG * TY;  // owned cells: stored to HBM, E phase
+    const bool lb = b_bx <= 0;           // no left neighbour lane in the row
+    const bool rb = b_bx < 0 || b_bx == TX - W;
+    const int e = (b_by + 2) * EW + (b_bx + 4);   // in-plane index of the segment, E box
+    const int bi = (b_by + 1) * BW + (b_bx + 4);  // in-plane index of the segment, B ring
     const unsigned b_off = (unsigned)((y0 + b_by + PY) * g.nxp + (x0 + b_bx + PX));
     const unsigned plane = (unsigned)g.plane;
     int b_y = y0 + b_by;
     if (b_y < 0) b_y += g.ny;
-    // owned-cell destinations of this thread's B segment and E segment
-    const SegOut b_dst = seg_out(g, x0 + b_bx, y0 + (b_by < 0 ? 0 : b_by), edge);
-    const int e_by = tid / NSEG, e_bx = W * (tid % NSEG);
-    const SegOut e_dst = seg_out(g, x0 + e_bx, y0 + (e_by < TY ? e_by : 0), edge);
+    // owned-cell destinations of this thread's segment
+    const SegOut dst = seg_out(g, x0 + (b_bx < 0 ? 0 : b_bx), y0 + (b_by < 0 ? 0 : b_by), edge);
 
     if (tid == 0) {
         for (int s = 0; s <= NS; ++s) mbar_init(&bar[s], 1);
@@ -238,24 +210,22 @@ step_kernel(const __grid_constant__ FusedMaps maps, Geom g, Mult<float> m, Field
         }
     }
 
-    // B^{n-1/2} of this thread's task, prefetched one plane ahead
+    // B^{n-1/2} of this thread's task, prefetched one plane ahead: bn is loaded at the start of
+    // a B phase for the next plane and moved to bo at the start of the next B phase (after a
+    // whole E phase and a block barrier, so the copy does not wait on the loads)
     float bo[3][W];
+    float bn[3][W];
 #pragma unroll
     for (int c = 0; c < 3; ++c)
 #pragma unroll
-        for (int u = 0; u < W; ++u) bo[c][u] = 0.0f;
-    float bn[3][W];   // next plane's B^{n-1/2}, loaded at the start of the current B phase
-    auto load_bold = [&](int qw, float (&dst)[3][W]) {   // qw: wrapped plane index
+        for (int u = 0; u < W; ++u) bn[c][u] = 0.0f;
+    auto load_bold = [&](int qw, float (&to)[3][W]) {   // qw: wrapped plane index
         const unsigned o = (unsigned)qw * plane + b_off;
-        if (bseg) {
 #pragma unroll
-            for (int c = 0; c < 3; ++c) unpackv(__ldg(reinterpret_cast<const Vec*>(in.c[3 + c] + o)), dst[c]);
-        } else if (bcol) {
-#pragma unroll
-            for (int c = 0; c < 3; ++c) dst[c][0] = __ldg(in.c[3 + c] + o);
-        }
+        for (int c = 0; c < 3; ++c)
+            unpackv(__ldg(reinterpret_cast<const float4*>(in.c[3 + c] + o)), to[c]);
     };
-    load_bold(wrapz(z0 - 1), bo);
+    load_bold(wrapz(z0 - 1), bn);
 
     const float mdt = -m.dt;
     // B^{n+1/2} ring: B_x, B_y keep planes p, p-1, p-2 (slot (p+6) mod 3); B_z keeps p, p-1.
@@ -293,135 +263,89 @@ step_kernel(const __grid_constant__ FusedMaps maps, Geom g, Mult<float> m, Field
             if (it == 0) ok = mbar_wait(&bar[NS], 0);
             ok = ok && mbar_wait(&bar[it % NS], (uint32_t)((it / NS) & 1));
         }
+        ok = __all_sync(FULL, ok);   // keeps the shuffles below warp-uniform
         // ---- B^{n+1/2}(p)
         // B^{n+1/2} ring slots: plane p (current), p-1, p-2
         const int r3m = r3 == 0 ? 2 : r3 - 1, r3mm = r3m == 0 ? 2 : r3m - 1;
         if (ok && it < niter) {
-            // issue the next plane's B^{n-1/2} loads first: they complete during this plane's work
-            if (it + 1 < niter) load_bold(pw + 1 == g.nz ? 0 : pw + 1, bn);
-            float* Bxc = sB + r3 * BSLOT;
-            float* Byc = sB + (3 + r3) * BSLOT;
-            float* Bzc = sB + (6 + r2) * BSLOT;
-            if (bseg) {
-                const int e = (b_by + 2) * EW + (b_bx + 4);
-                float dz[W], dy[W], bxv[W], byv[W], bzv[W];
-                // B_x = B_x + (D*_z E_y - D*_y E_z)
-                dstarw<2>((Pm + 1 * ESLOT), (P0 + 1 * ESLOT), (P1 + 1 * ESLOT), (P2 + 1 * ESLOT), e,
-                          m.cA[2], m.cD[2], m.cB[2][0], m.cB[2][1], dz);
-                dstarw<1>((Pm + 2 * ESLOT), (P0 + 2 * ESLOT), (P1 + 2 * ESLOT), nullptr, e, m.cA[1],
-                          m.cD[1], m.cB[1][0], m.cB[1][2], dy);
-#pragma unroll
-                for (int u = 0; u < W; ++u) bxv[u] = bo[0][u] + (dz[u] - dy[u]);
-                // B_y = B_y + (D*_x E_z - D*_z E_x)
-                dstarw<0>((Pm + 2 * ESLOT), (P0 + 2 * ESLOT), (P1 + 2 * ESLOT), nullptr, e, m.cA[0],
-                          m.cD[0], m.cB[0][1], m.cB[0][2], dy);
-                dstarw<2>((Pm + 0 * ESLOT), (P0 + 0 * ESLOT), (P1 + 0 * ESLOT), (P2 + 0 * ESLOT), e,
-                          m.cA[2], m.cD[2], m.cB[2][0], m.cB[2][1], dz);
-#pragma unroll
-                for (int u = 0; u < W; ++u) byv[u] = bo[1][u] + (dy[u] - dz[u]);
-                // B_z = B_z + (D*_y E_x - D*_x E_y)
-                dstarw<1>((Pm + 0 * ESLOT), (P0 + 0 * ESLOT), (P1 + 0 * ESLOT), nullptr, e, m.cA[1],
-                          m.cD[1], m.cB[1][0], m.cB[1][2], dy);
-                dstarw<0>((Pm + 1 * ESLOT), (P0 + 1 * ESLOT), (P1 + 1 * ESLOT), nullptr, e, m.cA[0],
-                          m.cD[0], m.cB[0][1], m.cB[0][2], dz);
-#pragma unroll
-                for (int u = 0; u < W; ++u) bzv[u] = bo[2][u] + (dy[u] - dz[u]);
-                if (spy != nullptr) {
-                    const float f = spy[b_y] * spz[pw];
-#pragma unroll
-                    for (int u = 0; u < W; ++u) { bxv[u] *= f; byv[u] *= f; bzv[u] *= f; }
-                }
-                const int bi = (b_by + 1) * BW + (b_bx + 4);
-                stv(Bxc, bi, bxv);
-                stv(Byc, bi, byv);
-                stv(Bzc, bi, bzv);
-                if (p >= z0 && b_by >= 0) {
-                    const unsigned po = (unsigned)pw * plane;
-                    put_seg(out.c[3], po, b_dst, bxv);
-                    put_seg(out.c[4], po, b_dst, byv);
-                    put_seg(out.c[5], po, b_dst, bzv);
-                }
-            } else if (bcol) {
-                // halo column x0-1: one cell, scalar taps (not stored to HBM)
-                const int e = (b_by + 2) * EW + 3;
-                const float* Em[3] = {(Pm + 0 * ESLOT), (Pm + 1 * ESLOT), (Pm + 2 * ESLOT)};
-                const float* E0[3] = {(P0 + 0 * ESLOT), (P0 + 1 * ESLOT), (P0 + 2 * ESLOT)};
-                const float* E1[3] = {(P1 + 0 * ESLOT), (P1 + 1 * ESLOT), (P1 + 2 * ESLOT)};
-                const float* E2[3] = {(P2 + 0 * ESLOT), (P2 + 1 * ESLOT), (P2 + 2 * ESLOT)};
-#define DX(c)                                                                                   \
-    dstar_taps(E0[c][e + 1], E0[c][e], E0[c][e + 2], E0[c][e - 1], E0[c][e + 1 + EW],          \
-               E0[c][e + EW], E0[c][e + 1 - EW], E0[c][e - EW], E1[c][e + 1], E1[c][e],         \
-               Em[c][e + 1], Em[c][e], m.cA[0], m.cD[0], m.cB[0][1], m.cB[0][2])
-#define DY(c)                                                                                   \
-    dstar_taps(E0[c][e + EW], E0[c][e], E0[c][e + 2 * EW], E0[c][e - EW], E0[c][e + EW + 1],   \
-               E0[c][e + 1], E0[c][e + EW - 1], E0[c][e - 1], E1[c][e + EW], E1[c][e],         \
-               Em[c][e + EW], Em[c][e], m.cA[1], m.cD[1], m.cB[1][0], m.cB[1][2])
-#define DZ(c)                                                                                   \
-    dstar_taps(E1[c][e], E0[c][e], E2[c][e], Em[c][e], E1[c][e + 1], E0[c][e + 1],             \
-               E1[c][e - 1], E0[c][e - 1], E1[c][e + EW], E0[c][e + EW], E1[c][e - EW],        \
-               E0[c][e - EW], m.cA[2], m.cD[2], m.cB[2][0], m.cB[2][1])
-                float bxs = bo[0][0] + (DZ(1) - DY(2));
-                float bys = bo[1][0] + (DX(2) - DZ(0));
-                float bzs = bo[2][0] + (DY(0) - DX(1));
-#undef DX
-#undef DY
-#undef DZ
-                if (spy != nullptr) {
-                    const float f = spy[b_y] * spz[pw];
-                    bxs *= f;
-                    bys *= f;
-                    bzs *= f;
-                }
-                const int bi = (b_by + 1) * BW + 3;
-                Bxc[bi] = bxs;
-                Byc[bi] = bys;
-                Bzc[bi] = bzs;
-            }
-            // prefetch next plane's B^{n-1/2} while E is formed
 #pragma unroll
             for (int c = 0; c < 3; ++c)
 #pragma unroll
                 for (int u = 0; u < W; ++u) bo[c][u] = bn[c][u];
+            // issue the next plane's B^{n-1/2} loads first: they complete during this plane's work
+            if (it + 1 < niter) load_bold(pw + 1 == g.nz ? 0 : pw + 1, bn);
+            float dz[W], dy[W], bxv[W], byv[W], bzv[W];
+            // B_x = B_x + (D*_z E_y - D*_y E_z)
+            dstar_z(Pm + ESLOT, P0 + ESLOT, P1 + ESLOT, P2 + ESLOT, e, lb, rb, m.cA[2], m.cD[2],
+                    m.cB[2][0], m.cB[2][1], dz);
+            dstar_y(Pm + 2 * ESLOT, P0 + 2 * ESLOT, P1 + 2 * ESLOT, e, lb, rb, m.cA[1], m.cD[1],
+                    m.cB[1][0], m.cB[1][2], dy);
+#pragma unroll
+            for (int u = 0; u < W; ++u) bxv[u] = bo[0][u] + (dz[u] - dy[u]);
+            // B_y = B_y + (D*_x E_z - D*_z E_x)
+            dstar_x(Pm + 2 * ESLOT, P0 + 2 * ESLOT, P1 + 2 * ESLOT, e, lb, rb, m.cA[0], m.cD[0],
+                    m.cB[0][1], m.cB[0][2], dy);
+            dstar_z(Pm, P0, P1, P2, e, lb, rb, m.cA[2], m.cD[2], m.cB[2][0], m.cB[2][1], dz);
+#pragma unroll
+            for (int u = 0; u < W; ++u) byv[u] = bo[1][u] + (dy[u] - dz[u]);
+            // B_z = B_z + (D*_y E_x - D*_x E_y)
+            dstar_y(Pm, P0, P1, e, lb, rb, m.cA[1], m.cD[1], m.cB[1][0], m.cB[1][2], dy);
+            dstar_x(Pm + ESLOT, P0 + ESLOT, P1 + ESLOT, e, lb, rb, m.cA[0], m.cD[0], m.cB[0][1],
+                    m.cB[0][2], dz);
+#pragma unroll
+            for (int u = 0; u < W; ++u) bzv[u] = bo[2][u] + (dy[u] - dz[u]);
+            if (spy != nullptr) {
+                const float f = spy[b_y] * spz[pw];
+#pragma unroll
+                for (int u = 0; u < W; ++u) { bxv[u] *= f; byv[u] *= f; bzv[u] *= f; }
+            }
+            if (b_store) {
+                stv(sB + r3 * BSLOT, bi, bxv);
+                stv(sB + (3 + r3) * BSLOT, bi, byv);
+                stv(sB + (6 + r2) * BSLOT, bi, bzv);
+            }
+            if (p >= z0 && b_own) {
+                const unsigned po = (unsigned)pw * plane;
+                put_seg(out.c[3], po, dst, bxv);
+                put_seg(out.c[4], po, dst, byv);
+                put_seg(out.c[5], po, dst, bzv);
+            }
         }
-        // ---- E^{n+1}(p - 1)
+        // ---- E^{n+1}(p - 1): warps of the owned rows (warp-uniform condition)
         const int q = p - 1;
-        if (ok && q >= z0 && q < zend && tid < NSEG * TY) {
-            const int by = e_by, bx = e_bx;
-            const int e = (by + 2) * EW + (bx + 4);
-            const int bi = (by + 1) * BW + (bx + 4);
+        if (ok && q >= z0 && q < zend && b_own) {
             const float* Bxc = sB + r3m * BSLOT;
             const float* Byc = sB + (3 + r3m) * BSLOT;
             const float* Bzc = sB + (6 + (r2 ^ 1)) * BSLOT;
             const float* Bxp = sB + r3mm * BSLOT;
             const float* Byp = sB + (3 + r3mm) * BSLOT;
-            float E0x[W], E0y[W], E0z[W];
-            ldv(Pm + 0 * ESLOT, e, E0x);
-            ldv(Pm + 1 * ESLOT, e, E0y);
-            ldv(Pm + 2 * ESLOT, e, E0z);
-            float Bz[W + 1], By[W + 1], tmp[W];   // [0] = value at x-1, [1 + u] = cell u
-            float Bzy[W], Byz[W], Bx[W], Bxz[W], Bxy[W];
-            ldv(Bzc, bi, Bz + 1);
-            ldv(Bzc, bi - W, tmp);
-            Bz[0] = tmp[W - 1];
-            ldv(Bzc, bi - BW, Bzy);
-            ldv(Byc, bi, By + 1);
-            ldv(Byc, bi - W, tmp);
-            By[0] = tmp[W - 1];
-            ldv(Byp, bi, Byz);
-            ldv(Bxc, bi, Bx);
-            ldv(Bxp, bi, Bxz);
-            ldv(Bxc, bi - BW, Bxy);
+            const Q4 E0x = ldq(Pm, e), E0y = ldq(Pm + ESLOT, e), E0z = ldq(Pm + 2 * ESLOT, e);
+            const Q4 Bz4 = ldq(Bzc, bi), By4 = ldq(Byc, bi);
+            const Q4 Bzy = ldq(Bzc, bi - BW), Byz = ldq(Byp, bi), Bx = ldq(Bxc, bi),
+                     Bxz = ldq(Bxp, bi), Bxy = ldq(Bxc, bi - BW);
+            float Bz[W + 1], By[W + 1];   // [0] = value at x-1, [1 + u] = cell u
+#pragma unroll
+            for (int u = 0; u < W; ++u) {
+                Bz[1 + u] = Bz4.v[u];
+                By[1 + u] = By4.v[u];
+            }
+            Bz[0] = from_left(Bz4.v[3]);
+            By[0] = from_left(By4.v[3]);
+            if (lb) {
+                Bz[0] = Bzc[bi - 1];
+                By[0] = Byc[bi - 1];
+            }
             float ex[W], ey[W], ez[W];
 #pragma unroll
             for (int u = 0; u < W; ++u) {
-                ex[u] = ampere_comp(E0x[u], Bz[1 + u], Bzy[u], By[1 + u], Byz[u], m.cE[1], m.cE[2]);
-                ey[u] = ampere_comp(E0y[u], Bx[u], Bxz[u], Bz[1 + u], Bz[u], m.cE[2], m.cE[0]);
-                ez[u] = ampere_comp(E0z[u], By[1 + u], By[u], Bx[u], Bxy[u], m.cE[0], m.cE[1]);
+                ex[u] = ampere_comp(E0x.v[u], Bz[1 + u], Bzy.v[u], By[1 + u], Byz.v[u], m.cE[1], m.cE[2]);
+                ey[u] = ampere_comp(E0y.v[u], Bx.v[u], Bxz.v[u], Bz[1 + u], Bz[u], m.cE[2], m.cE[0]);
+                ez[u] = ampere_comp(E0z.v[u], By[1 + u], By[u], Bx.v[u], Bxy.v[u], m.cE[0], m.cE[1]);
             }
-            const int i0 = x0 + bx, j = y0 + by;
+            const int i0 = x0 + b_bx, j = y0 + b_by;
             if (jx_row != nullptr) {
                 float jv[W];
-                unpackv(__ldg(reinterpret_cast<const Vec*>(jx_row + i0)), jv);
+                unpackv(__ldg(reinterpret_cast<const float4*>(jx_row + i0)), jv);
                 const float sy = jyz[j], sz = jyz[g.ny + qw];
 #pragma unroll
                 for (int u = 0; u < W; ++u) ex[u] = fma(mdt, (jv[u] * sy) * sz, ex[u]);
@@ -432,13 +356,13 @@ step_kernel(const __grid_constant__ FusedMaps maps, Geom g, Mult<float> m, Field
                 for (int u = 0; u < W; ++u) { ex[u] *= f; ey[u] *= f; ez[u] *= f; }
             }
             const unsigned po = (unsigned)qw * plane;
-            put_seg(out.c[0], po, e_dst, ex);
-            put_seg(out.c[1], po, e_dst, ey);
-            put_seg(out.c[2], po, e_dst, ez);
+            put_seg(out.c[0], po, dst, ex);
+            put_seg(out.c[1], po, dst, ey);
+            put_seg(out.c[2], po, dst, ez);
             if (h0 != nullptr) {
-                put_seg(h0, po, e_dst, ex);
-                put_seg(h1, po, e_dst, ey);
-                put_seg(h2, po, e_dst, ez);
+                put_seg(h0, po, dst, ex);
+                put_seg(h1, po, dst, ey);
+                put_seg(h2, po, dst, ez);
             }
         }
         bool ok_next = true;

@@ -46,6 +46,11 @@ bool adjoint32_prepare();
 void launch_adjoint32_B(const FusedMaps& maps, const Geom& g, const Mult<float>& m,
                         FieldSet<float> lam, const float* spy, const float* spz, double* partials,
                         int* err, cudaStream_t st);
+bool adjoint32e_supported(const Geom& g);
+bool adjoint32e_prepare();
+void launch_adjoint32_E(const FusedMaps& maps, const Geom& g, const Mult<float>& m,
+                        FieldSet<float> lam, const float* spy, const float* spz, int* err,
+                        cudaStream_t st);
 template <typename T>
 void launch_energy(const Geom& g, FieldSet<T> s, int x_lo, int x_len, int my, int mz, double dV,
                    double* part, double* out, cudaStream_t st);
@@ -242,6 +247,8 @@ struct fdtd_handle {
     int use_fused;
     double* dpart;      // diagnostics partials (2 per block)
     std::vector<FusedMaps> hist_maps;   // TMA descriptors of each history snapshot (FP32 adjoint)
+    FusedMaps lam_maps;                 // .e[c]: TMA descriptors of lambda_B component c (FP32)
+    bool lam_staged = false;            // lam_maps valid: the staged FP32 adjoint E kernel runs
     FusedPlan* plan;    // TMA descriptors of both state sets (nullptr: reference-form kernels)
     int* err_dev;       // raised by a kernel whose bounded wait expired
 
@@ -526,6 +533,13 @@ static int ensure_lam(fdtd_handle* h) {
     const size_t arr = (size_t)h->g.total * h->esz;
     CK(cudaMalloc(&h->lam, 6 * arr));
     CK(cudaMemsetAsync(h->lam, 0, 6 * arr, h->stream));
+    h->lam_staged = false;
+    if (h->grid.dtype == FDTD_F32 && h->plan && adjoint32e_supported(h->g) && adjoint32e_prepare()) {
+        bool ok = true;
+        for (int c = 0; c < 3; ++c)
+            ok = ok && encode_ebox_f32(&h->lam_maps.e[c], h->g, (float*)h->lam_arr(3 + c));
+        h->lam_staged = ok;   // otherwise the reference-form adjoint E kernel runs
+    }
     return FDTD_OK;
 }
 
@@ -774,7 +788,14 @@ static int adjoint_impl(fdtd_handle* h, int n, const fdtd_probe* probe, double* 
         } else {
             launch_adjoint_B_v0<T>(g, m, lam, E, spy, spz, h->partials, nblk, h->stream);
         }
-        launch_adjoint_E_v0<T>(g, m, lam, spy, spz, h->stream);
+        if constexpr (std::is_same<T, float>::value) {
+            if (staged && h->lam_staged)
+                launch_adjoint32_E(h->lam_maps, g, m, lam, spy, spz, h->err_dev, h->stream);
+            else
+                launch_adjoint_E_v0<T>(g, m, lam, spy, spz, h->stream);
+        } else {
+            launch_adjoint_E_v0<T>(g, m, lam, spy, spz, h->stream);
+        }
         CK(cudaGetLastError());
     }
     // scale of each partial: dt/dx_a, zero for entries that refer to an absent axis

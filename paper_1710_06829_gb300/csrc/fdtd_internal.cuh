@@ -56,15 +56,25 @@ struct Mult {
 // every kernel (so all step kernels give bitwise-identical B):
 //   cA (F[+a] - F[0]) + cD (F[+2a] - F[-a]) + cBb ((F[+a+b] - F[+b]) + (F[+a-b] - F[-b]))
 //                                          + cBc ((F[+a+c] - F[+c]) + (F[+a-c] - F[-c]))
+// dstar_diff takes the five differences along a already formed (d_a = F[+a] - F[0],
+// d_bp = F[+a+b] - F[+b], ...), so a kernel can form each difference once and share it between
+// neighbouring cells; dstar_taps forms them from the 12 tap values.  Both round identically.
+template <typename T>
+__device__ __forceinline__ T dstar_diff(T d_a, T f_a2, T f_am1, T d_bp, T d_bm, T d_cp, T d_cm,
+                                        T cA, T cD, T cBb, T cBc) {
+    T v = cA * d_a;
+    v = fma(cD, f_a2 - f_am1, v);
+    v = fma(cBb, d_bp + d_bm, v);
+    v = fma(cBc, d_cp + d_cm, v);
+    return v;
+}
+
 template <typename T>
 __device__ __forceinline__ T dstar_taps(T f_a1, T f_0, T f_a2, T f_am1, T f_a1bp, T f_bp, T f_a1bm,
                                         T f_bm, T f_a1cp, T f_cp, T f_a1cm, T f_cm, T cA, T cD,
                                         T cBb, T cBc) {
-    T v = cA * (f_a1 - f_0);
-    v = fma(cD, f_a2 - f_am1, v);
-    v = fma(cBb, (f_a1bp - f_bp) + (f_a1bm - f_bm), v);
-    v = fma(cBc, (f_a1cp - f_cp) + (f_a1cm - f_cm), v);
-    return v;
+    return dstar_diff(f_a1 - f_0, f_a2, f_am1, f_a1bp - f_bp, f_a1bm - f_bm, f_a1cp - f_cp,
+                      f_a1cm - f_cm, cA, cD, cBb, cBc);
 }
 
 // One Ampere component: E + (c1 (P - P[-a1]) - c2 (Q - Q[-a2])), in a fixed rounding order.
