@@ -7,15 +7,18 @@
 // eliminated by Eq. alpha).  The brackets need E^n at x-1..x+2, y-1..y+2, z-1..z+2 around the
 // cell: E^n planes arrive by TMA as 72 x 12 boxes into a five-slot shared ring (same schedule
 // as the fused forward step), and each thread evaluates the brackets of four consecutive
-// cells from 16-byte shared-memory row windows.  lambda_E (own cell and its +x, +y, +z
+// cells from one 16-byte shared-memory vector per stencil row, the values beyond its segment
+// coming from neighbouring lanes by shuffle (seg::taps_*).  lambda_E (own cell and its +x, +y, +z
 // neighbours) and lambda_B (own cell) are read from HBM directly; only mu is written.
 //
 // Every mbarrier wait is bounded; on expiry the CTA raises *err, drains its copies in flight
 // (bounded) and returns.
-#include "fdtd_tma.cuh"
+#include "fdtd_seg.cuh"
 
 namespace fdtd {
 namespace adj32 {
+
+using namespace seg;
 
 constexpr int TX = 64, TY = 8, D = 1, NT = 128;   // z-chunk length: launch parameter
 constexpr int EW = TX + 8, EH = TY + 4, EPL = EW * EH;
@@ -26,82 +29,26 @@ constexpr size_t SMEM = OFF_BAR + (size_t)(NS + 1) * 8;
 constexpr uint32_t UNIT_BYTES = 3u * EPL * 4;
 constexpr uint32_t PRO_BYTES = 9u * EPL * 4;
 
-struct Win {
-    float v[12];   // v[k] = F[idx - 4 + k]
-};
-
-__device__ __forceinline__ float4 ld4(const float* s, int idx) {
-    return *reinterpret_cast<const float4*>(s + idx);
-}
-
-__device__ __forceinline__ Win win(const float* s, int idx) {
-    Win w;
-    const float4 a = ld4(s, idx - 4), b = ld4(s, idx), c = ld4(s, idx + 4);
-    w.v[0] = a.x; w.v[1] = a.y; w.v[2] = a.z; w.v[3] = a.w;
-    w.v[4] = b.x; w.v[5] = b.y; w.v[6] = b.z; w.v[7] = b.w;
-    w.v[8] = c.x; w.v[9] = c.y; w.v[10] = c.z; w.v[11] = c.w;
-    return w;
-}
-
 __device__ __forceinline__ void unpack(float4 a, float o[4]) {
     o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w;
 }
 
-// derivative brackets of D*_A (without 1/dx_A) for four cells at in-plane index e:
-//   dd = (F[+2a] - F[-a]) - 3 ax,  db = (F[+a+b] - F[+b]) + (F[+a-b] - F[-b]) - 2 ax,
-//   dc likewise for the second transverse axis, ax = F[+a] - F[0]
-template <int A>
-__device__ __forceinline__ void brackets4(const float* Fm, const float* F0, const float* F1,
-                                          const float* F2, int e, float dd[4], float db[4],
-                                          float dc[4]) {
-    if constexpr (A == 0) {   // axis x; b = y, c = z
-        const Win w0 = win(F0, e), wyp = win(F0, e + EW), wym = win(F0, e - EW);
-        const Win w1 = win(F1, e), wm = win(Fm, e);
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const float ax = w0.v[5 + u] - w0.v[4 + u];
-            dd[u] = (w0.v[6 + u] - w0.v[3 + u]) - 3.0f * ax;
-            db[u] = (wyp.v[5 + u] - wyp.v[4 + u]) + (wym.v[5 + u] - wym.v[4 + u]) - 2.0f * ax;
-            dc[u] = (w1.v[5 + u] - w1.v[4 + u]) + (wm.v[5 + u] - wm.v[4 + u]) - 2.0f * ax;
-        }
-    } else if constexpr (A == 1) {   // axis y; b = x, c = z
-        const Win w0 = win(F0, e), wyp = win(F0, e + EW);
-        float a2[4], am[4], c1[4], c1p[4], cm[4], cmp[4];
-        unpack(ld4(F0, e + 2 * EW), a2);
-        unpack(ld4(F0, e - EW), am);
-        unpack(ld4(F1, e), c1);
-        unpack(ld4(F1, e + EW), c1p);
-        unpack(ld4(Fm, e), cm);
-        unpack(ld4(Fm, e + EW), cmp);
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const float ax = wyp.v[4 + u] - w0.v[4 + u];
-            dd[u] = (a2[u] - am[u]) - 3.0f * ax;
-            db[u] = (wyp.v[5 + u] - w0.v[5 + u]) + (wyp.v[3 + u] - w0.v[3 + u]) - 2.0f * ax;
-            dc[u] = (c1p[u] - c1[u]) + (cmp[u] - cm[u]) - 2.0f * ax;
-        }
-    } else {   // axis z; b = x, c = y
-        const Win w1 = win(F1, e), w0 = win(F0, e);
-        float a2[4], am[4], p1[4], p0[4], m1[4], m0[4];
-        unpack(ld4(F2, e), a2);
-        unpack(ld4(Fm, e), am);
-        unpack(ld4(F1, e + EW), p1);
-        unpack(ld4(F0, e + EW), p0);
-        unpack(ld4(F1, e - EW), m1);
-        unpack(ld4(F0, e - EW), m0);
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const float ax = w1.v[4 + u] - w0.v[4 + u];
-            dd[u] = (a2[u] - am[u]) - 3.0f * ax;
-            db[u] = (w1.v[5 + u] - w0.v[5 + u]) + (w1.v[3 + u] - w0.v[3 + u]) - 2.0f * ax;
-            dc[u] = (p1[u] - p0[u]) + (m1[u] - m0[u]) - 2.0f * ax;
-        }
+// Gradient brackets (Sec. 2 with alpha eliminated by Eq. alpha; without 1/dx_a) of D*_a at a
+// cell, from the taps of seg::taps_* (d_a = F[+a] - F[0], ...):
+//   d/d delta_a: (F[+2a] - F[-a]) - 3 d_a,   d/d beta_ab: (d_bp + d_bm) - 2 d_a,   likewise c.
+// acc[0..2] += w * (delta, beta_ab, beta_ac brackets)
+template <int EW>
+struct Brackets {
+    float* acc;
+    const float* w;
+    __device__ __forceinline__ void operator()(int u, float da, float a2, float am1, float bp,
+                                               float bm, float cp, float cm) const {
+        acc[0] = fmaf(w[u], (a2 - am1) - 3.0f * da, acc[0]);
+        acc[1] = fmaf(w[u], (bp + bm) - 2.0f * da, acc[1]);
+        acc[2] = fmaf(w[u], (cp + cm) - 2.0f * da, acc[2]);
     }
-}
+};
 
-__device__ __forceinline__ void st4(float* F, long long idx, float4 v) {
-    *reinterpret_cast<float4*>(F + idx) = v;
-}
 
 __global__ void __launch_bounds__(NT, 3)
 adjB_kernel(const __grid_constant__ FusedMaps maps, Geom g, Mult<float> m, FieldSet<float> lam,
@@ -139,6 +86,9 @@ adjB_kernel(const __grid_constant__ FusedMaps maps, Geom g, Mult<float> m, Field
     const int by = tid / 16, bx = 4 * (tid % 16);
     const int i0 = x0 + bx, j = y0 + by;
     const int e = (by + 2) * EW + (bx + 4);
+    const bool lb = bx == 0, rb = bx == TX - 4;   // row-end lanes (no shuffle neighbour)
+    const unsigned plane = (unsigned)g.plane;
+    const SegOut dst = seg_out(g, i0, j, edge);
 
     if (tid == 0) {
         for (int s = 0; s <= NS; ++s) mbar_init(&bar[s], 1);
@@ -167,15 +117,15 @@ adjB_kernel(const __grid_constant__ FusedMaps maps, Geom g, Mult<float> m, Field
     const float* lEx = lam.c[0];
     const float* lEy = lam.c[1];
     const float* lEz = lam.c[2];
-    const long long Y = g.nxp;
+    const int Y = g.nxp;
     // lambda of this thread's cells (own, +x, +y, +z; lambda_B own), prefetched one plane ahead
     struct Lam {
         float ex[5], ey[5], ez[5], exy[4], ezy[4], exz[4], eyz[4], bx[4], by[4], bz[4];
     } L;
     auto load_lam = [&](int q) {
         const int qw = wrapz(q);
-        const long long c = ((long long)qw * g.nyp + j + PY) * g.nxp + PX + i0;
-        const long long zp = (long long)(wrapz(q + 1) - qw) * g.plane;
+        const unsigned c = (unsigned)qw * plane + dst.ro;
+        const int zp = (wrapz(q + 1) - qw) * (int)plane;
         unpack(__ldg(reinterpret_cast<const float4*>(lEx + c)), L.ex);
         unpack(__ldg(reinterpret_cast<const float4*>(lEy + c)), L.ey);
         unpack(__ldg(reinterpret_cast<const float4*>(lEz + c)), L.ez);
@@ -192,21 +142,25 @@ adjB_kernel(const __grid_constant__ FusedMaps maps, Geom g, Mult<float> m, Field
     if (niter > 0) load_lam(z0);
     bool failed = false;
     int it = 0;
-    for (; it < niter; ++it) {
+    // counters: pw = p mod nz, s_m = ring slot of plane p-1 = it mod NE
+    int pw = wrapz(z0), s_m = 0;
+    for (; it < niter; ++it, pw = (pw + 1 == g.nz ? 0 : pw + 1), s_m = (s_m + 1 == NE ? 0 : s_m + 1)) {
         const int p = z0 + it;
+        const int s_0 = s_m + 1 == NE ? 0 : s_m + 1;
+        const int s_1 = s_0 + 1 == NE ? 0 : s_0 + 1;
+        const int s_2 = s_1 + 1 == NE ? 0 : s_1 + 1;
         bool ok = true;
         if (it == 0) ok = mbar_wait(&bar[NS], 0);
         ok = ok && mbar_wait(&bar[it % NS], (uint32_t)((it / NS) & 1));
+        ok = __all_sync(FULL, ok);   // keeps the shuffles below warp-uniform
         if (ok) {
-            const int pw = wrapz(p);
-            const long long c = ((long long)pw * g.nyp + j + PY) * g.nxp + PX + i0;
             // l_E = S lambda_E at the cells and their +x, +y, +z neighbours
             float s0 = 1.0f, syp = 1.0f, szp = 1.0f;
             if (spy != nullptr) {
                 const int jp = j + 1 < g.ny ? j + 1 : 0;
                 s0 = spy[j] * spz[pw];
                 syp = spy[jp] * spz[pw];
-                szp = spy[j] * spz[wrapz(p + 1)];
+                szp = spy[j] * spz[pw + 1 == g.nz ? 0 : pw + 1];
             }
             float mux[4], muy[4], muz[4];
 #pragma unroll
@@ -222,52 +176,37 @@ adjB_kernel(const __grid_constant__ FusedMaps maps, Geom g, Mult<float> m, Field
                 muz[u] = s0 * nz_;
             }
             if (it + 1 < niter) load_lam(p + 1);
-            // gradient brackets from the E^n ring
-            float dd[4], db[4], dc[4], fd[4], fb[4], fc[4];
-            brackets4<0>(Ep(p - 1, 2), Ep(p, 2), Ep(p + 1, 2), nullptr, e, dd, db, dc);   // D*_x E_z
-            brackets4<0>(Ep(p - 1, 1), Ep(p, 1), Ep(p + 1, 1), nullptr, e, fd, fb, fc);   // D*_x E_y
+            // gradient brackets from the E^n ring (planes p-1 .. p+2 in slots s_m .. s_2)
+            const float* Pm = sE + s_m * 3 * ESLOT;
+            const float* P0 = sE + s_0 * 3 * ESLOT;
+            const float* P1 = sE + s_1 * 3 * ESLOT;
+            const float* P2 = sE + s_2 * 3 * ESLOT;
+            float nmux[4], nmuy[4], nmuz[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-                racc[0] += muy[u] * dd[u] - muz[u] * fd[u];
-                racc[1] += muy[u] * db[u] - muz[u] * fb[u];
-                racc[2] += muy[u] * dc[u] - muz[u] * fc[u];
+                nmux[u] = -mux[u];
+                nmuy[u] = -muy[u];
+                nmuz[u] = -muz[u];
             }
-            brackets4<1>(Ep(p - 1, 0), Ep(p, 0), Ep(p + 1, 0), nullptr, e, dd, db, dc);   // D*_y E_x
-            brackets4<1>(Ep(p - 1, 2), Ep(p, 2), Ep(p + 1, 2), nullptr, e, fd, fb, fc);   // D*_y E_z
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                racc[3] += muz[u] * dd[u] - mux[u] * fd[u];
-                racc[4] += muz[u] * db[u] - mux[u] * fb[u];
-                racc[5] += muz[u] * dc[u] - mux[u] * fc[u];
-            }
-            brackets4<2>(Ep(p - 1, 1), Ep(p, 1), Ep(p + 1, 1), Ep(p + 2, 1), e, dd, db, dc);   // D*_z E_y
-            brackets4<2>(Ep(p - 1, 0), Ep(p, 0), Ep(p + 1, 0), Ep(p + 2, 0), e, fd, fb, fc);   // D*_z E_x
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                racc[6] += mux[u] * dd[u] - muy[u] * fd[u];
-                racc[7] += mux[u] * db[u] - muy[u] * fb[u];
-                racc[8] += mux[u] * dc[u] - muy[u] * fc[u];
-            }
+            // B_y gets D*_x E_z, B_z gets -D*_x E_y  (x brackets: racc 0..2)
+            taps_x<EW>(Pm + 2 * ESLOT, P0 + 2 * ESLOT, P1 + 2 * ESLOT, e, lb, rb, Brackets<EW>{racc + 0, muy});
+            taps_x<EW>(Pm + ESLOT, P0 + ESLOT, P1 + ESLOT, e, lb, rb, Brackets<EW>{racc + 0, nmuz});
+            // B_z gets D*_y E_x, B_x gets -D*_y E_z  (y brackets: racc 3..5)
+            taps_y<EW>(Pm, P0, P1, e, lb, rb, Brackets<EW>{racc + 3, muz});
+            taps_y<EW>(Pm + 2 * ESLOT, P0 + 2 * ESLOT, P1 + 2 * ESLOT, e, lb, rb, Brackets<EW>{racc + 3, nmux});
+            // B_x gets D*_z E_y, B_y gets -D*_z E_x  (z brackets: racc 6..8)
+            taps_z<EW>(Pm + ESLOT, P0 + ESLOT, P1 + ESLOT, P2 + ESLOT, e, lb, rb, Brackets<EW>{racc + 6, mux});
+            taps_z<EW>(Pm, P0, P1, P2, e, lb, rb, Brackets<EW>{racc + 6, nmuy});
 #pragma unroll
             for (int q = 0; q < 9; ++q) {   // one FP64 add per 4 cells and coefficient
                 acc[q] += (double)racc[q];
                 racc[q] = 0.0f;
             }
             // mu -> lambda_B (own cells and, at the domain edge, their images)
-            const float4 vx = make_float4(mux[0], mux[1], mux[2], mux[3]);
-            const float4 vy = make_float4(muy[0], muy[1], muy[2], muy[3]);
-            const float4 vz = make_float4(muz[0], muz[1], muz[2], muz[3]);
-            if (!edge) {
-                st4(lam.c[3], c, vx);
-                st4(lam.c[4], c, vy);
-                st4(lam.c[5], c, vz);
-            } else {
-                for (int u = 0; u < 4; ++u) {
-                    store_img(g, lam.c[3], i0 + u, j, pw, mux[u]);
-                    store_img(g, lam.c[4], i0 + u, j, pw, muy[u]);
-                    store_img(g, lam.c[5], i0 + u, j, pw, muz[u]);
-                }
-            }
+            const unsigned po = (unsigned)pw * plane;
+            put_seg(lam.c[3], po, dst, mux);
+            put_seg(lam.c[4], po, dst, muy);
+            put_seg(lam.c[5], po, dst, muz);
         }
         bool ok_next = true;
         if (tid == 0 && it + 1 < niter)

@@ -72,5 +72,90 @@ __device__ __forceinline__ void put_seg(float* F, unsigned po, const SegOut& d, 
     }
 }
 
+// Taps of the extended stencil D*_a (Eq. D*) on the four cells at in-plane index e of a field
+// whose plane slots are Fm (p-1), F0 (p), F1 (p+1), F2 (p+2), in shared memory with rows of EW
+// floats.  For each cell u the consumer receives, in the argument order of dstar_diff,
+//   d_a = F[+a] - F[0], F[+2a], F[-a], d_bp, d_bm, d_cp, d_cm   (b, c: the transverse axes)
+// with d_bp = F[+a+b] - F[+b] etc., the differences taken as dstar_taps takes them.  Each
+// stencil row is one 16-byte load of the lane's own cells; values beyond the segment come from
+// lane -1 / lane +1 by shuffle, and lanes with no neighbour lane in their row (lb / rb) read
+// them from shared memory.  All 32 lanes of the warp must call together.
+
+// D*_z: transverse x, then y
+template <int EW, class Fn>
+__device__ __forceinline__ void taps_z(const float* Fm, const float* F0, const float* F1,
+                                       const float* F2, int e, bool lb, bool rb, Fn&& fn) {
+    const Q4 c1 = ldq(F1, e), c0 = ldq(F0, e), c2 = ldq(F2, e), cm = ldq(Fm, e);
+    const Q4 p1 = ldq(F1, e + EW), p0 = ldq(F0, e + EW), m1 = ldq(F1, e - EW),
+             m0 = ldq(F0, e - EW);
+    float d[6];   // d[k] = F1 - F0 at x-1+k
+#pragma unroll
+    for (int u = 0; u < 4; ++u) d[1 + u] = c1.v[u] - c0.v[u];
+    d[0] = from_left(d[4]);
+    d[5] = from_right(d[1]);
+    if (lb) d[0] = F1[e - 1] - F0[e - 1];
+    if (rb) d[5] = F1[e + 4] - F0[e + 4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+        fn(u, d[1 + u], c2.v[u], cm.v[u], d[2 + u], d[u], p1.v[u] - p0.v[u], m1.v[u] - m0.v[u]);
+}
+
+// D*_y: transverse x, then z
+template <int EW, class Fn>
+__device__ __forceinline__ void taps_y(const float* Fm, const float* F0, const float* F1, int e,
+                                       bool lb, bool rb, Fn&& fn) {
+    const Q4 a0 = ldq(F0, e), a1 = ldq(F0, e + EW), a2 = ldq(F0, e + 2 * EW),
+             am = ldq(F0, e - EW);
+    const Q4 b1 = ldq(F1, e), b1p = ldq(F1, e + EW), bm = ldq(Fm, e), bmp = ldq(Fm, e + EW);
+    float d[6];   // d[k] = F0(y+1) - F0(y) at x-1+k
+#pragma unroll
+    for (int u = 0; u < 4; ++u) d[1 + u] = a1.v[u] - a0.v[u];
+    d[0] = from_left(d[4]);
+    d[5] = from_right(d[1]);
+    if (lb) d[0] = F0[e + EW - 1] - F0[e - 1];
+    if (rb) d[5] = F0[e + EW + 4] - F0[e + 4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+        fn(u, d[1 + u], a2.v[u], am.v[u], d[2 + u], d[u], b1p.v[u] - b1.v[u], bmp.v[u] - bm.v[u]);
+}
+
+// D*_x: transverse y, then z
+template <int EW, class Fn>
+__device__ __forceinline__ void taps_x(const float* Fm, const float* F0, const float* F1, int e,
+                                       bool lb, bool rb, Fn&& fn) {
+    const Q4 R = ldq(F0, e), Yp = ldq(F0, e + EW), Ym = ldq(F0, e - EW), Z1 = ldq(F1, e),
+             Zm = ldq(Fm, e);
+    float r[7];                           // F0 at x-1 .. x+5
+    float yp[5], ym[5], z1[5], zm[5];     // x .. x+4
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        r[1 + u] = R.v[u];
+        yp[u] = Yp.v[u];
+        ym[u] = Ym.v[u];
+        z1[u] = Z1.v[u];
+        zm[u] = Zm.v[u];
+    }
+    r[0] = from_left(R.v[3]);
+    r[5] = from_right(R.v[0]);
+    r[6] = from_right(R.v[1]);
+    yp[4] = from_right(Yp.v[0]);
+    ym[4] = from_right(Ym.v[0]);
+    z1[4] = from_right(Z1.v[0]);
+    zm[4] = from_right(Zm.v[0]);
+    if (lb) r[0] = F0[e - 1];
+    if (rb) {
+        r[5] = F0[e + 4];
+        r[6] = F0[e + 5];
+        yp[4] = F0[e + EW + 4];
+        ym[4] = F0[e - EW + 4];
+        z1[4] = F1[e + 4];
+        zm[4] = Fm[e + 4];
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+        fn(u, r[u + 2] - r[u + 1], r[u + 3], r[u], yp[u + 1] - yp[u], ym[u + 1] - ym[u],
+           z1[u + 1] - z1[u], zm[u + 1] - zm[u]);
+}
+
 }  // namespace seg
 }  // namespace fdtd
