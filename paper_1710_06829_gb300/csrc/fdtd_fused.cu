@@ -263,6 +263,7 @@ static EncodeTiledFn encode_fn() {
 }
 
 bool fused32_supported(const Geom& g);
+int fused32_ebox_w();
 bool fused32_prepare();
 void launch_fused32(const FusedMaps& maps, FieldSet<float> in, const Geom& g, const Mult<float>& m,
                     FieldSet<float> out, const float* spy, const float* spz, const float* jyz,
@@ -304,7 +305,8 @@ FusedPlan* fused_plan_create(const Geom& g, T* const set0[6], T* const set1[6]) 
     for (int s = 0; s < 2; ++s) {
         T* const* set = s == 0 ? set0 : set1;
         for (int c = 0; c < 3; ++c) {
-            if (!encode<T>(&p->maps[s].e[c], g, set[c], Lc::EW, Lc::EH) ||
+            const int ew = std::is_same<T, float>::value ? fused32_ebox_w() : Lc::EW;
+            if (!encode<T>(&p->maps[s].e[c], g, set[c], ew, Lc::EH) ||
                 !encode<T>(&p->maps[s].b[c], g, set[3 + c], Lc::BW, Lc::BH)) {
                 delete p;
                 return nullptr;

@@ -1,7 +1,7 @@
 // FP32 fused leapfrog step (one launch per leapfrog step).
 //
 // A CTA owns a 64 x 8 (x, y) tile and a chunk of tz planes (a launch parameter) and marches
-// through it.  E^n planes arrive by TMA (cp.async.bulk.tensor.3d) as 72 x 12 boxes (x0-4 ..,
+// through it.  E^n planes arrive by TMA (cp.async.bulk.tensor.3d) as 76 x 12 boxes (x0-4 ..,
 // y0-2 ..) into a ring of five shared-memory slots, one plane ahead of use, completion signalled
 // on mbarriers.  Iteration `it` forms B^{n+1/2} on plane p = z0-1+it (tile, halo row y0-1, halo
 // column x0-1) and E^{n+1} on plane p-1, so one block barrier per plane suffices; B^{n+1/2}
@@ -36,7 +36,11 @@ constexpr int TX = 64, TY = 8, D = 1;   // z-chunk length: launch parameter (zch
 constexpr int NSEG = TX / W;                                    // segments per row
 constexpr int NBT = NSEG * (TY + 1) + TY + 1;                   // B tasks: rows + halo column
 constexpr int NT = ((NBT + 31) / 32) * 32;
-constexpr int EW = TX + 8, EH = TY + 4, EPL = EW * EH;        // E box 72 x 12 (x0-4.., y0-2..)
+// E box 76 x 12 (x0-4 .., y0-2 ..): the stencil needs x0-2 .. x0+65 (a 72-wide box); 76 floats
+// = 19 16-byte chunks per row put the halo-column lanes (one segment on each of nine rows) on
+// distinct bank groups, which removed most shared-memory bank conflicts.  In the last tile of a
+// row the box reaches four columns past the padded array; TMA fills them with zeros (unused)
+constexpr int EW = TX + 12, EH = TY + 4, EPL = EW * EH;
 constexpr int ESLOT = ((EPL * 4 + 127) / 128) * 128 / 4;        // floats per E slot
 constexpr int BW = TX + 4, BH = TY + 1, BPL = BW * BH;         // B^{n+1/2} plane: x0-4.., y0-1..
 constexpr int BSLOT = ((BPL * 4 + 127) / 128) * 128 / 4;
@@ -341,6 +345,8 @@ bool fused32_supported(const Geom& g) {
     return g.nx % f32seg::TX == 0 && g.ny % f32seg::TY == 0 && g.nx >= f32seg::TX &&
            g.ny >= f32seg::TY && g.total < (1LL << 31);
 }
+
+int fused32_ebox_w() { return f32seg::EW; }
 
 bool fused32_prepare() {
     return cudaFuncSetAttribute(f32seg::step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
