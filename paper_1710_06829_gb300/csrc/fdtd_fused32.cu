@@ -213,6 +213,8 @@ step_kernel(const __grid_constant__ FusedMaps maps, Geom g, Mult<float> m, Field
             ok = ok && mbar_wait(&bar[it % NS], (uint32_t)((it / NS) & 1));
         }
         ok = __all_sync(FULL, ok);   // keeps the shuffles below warp-uniform
+        // E^n(p-1) of the own cells: read once, used by the B taps and the E update
+        const Q4 E0x = ldq(Pm, e), E0y = ldq(Pm + ESLOT, e), E0z = ldq(Pm + 2 * ESLOT, e);
         // ---- B^{n+1/2}(p)
         // B^{n+1/2} ring slots: plane p (current), p-1, p-2
         const int r3m = r3 == 0 ? 2 : r3 - 1, r3mm = r3m == 0 ? 2 : r3m - 1;
@@ -268,7 +270,6 @@ step_kernel(const __grid_constant__ FusedMaps maps, Geom g, Mult<float> m, Field
             const float* Bzc = sB + (6 + (r2 ^ 1)) * BSLOT;
             const float* Bxp = sB + r3mm * BSLOT;
             const float* Byp = sB + (3 + r3mm) * BSLOT;
-            const Q4 E0x = ldq(Pm, e), E0y = ldq(Pm + ESLOT, e), E0z = ldq(Pm + 2 * ESLOT, e);
             const Q4 Bz4 = ldq(Bzc, bi), By4 = ldq(Byc, bi);
             const Q4 Bzy = ldq(Bzc, bi - BW), Byz = ldq(Byp, bi), Bx = ldq(Bxc, bi),
                      Bxz = ldq(Bxp, bi), Bxy = ldq(Bxc, bi - BW);
