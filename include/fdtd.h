@@ -169,9 +169,16 @@ int fdtd_step_adjoint(fdtd_handle* h, int32_t n, const fdtd_probe* probe, double
  *   FDTD_DIAG_PLANEWAVE: params = {component 0..5, k_x, k_y, k_z}; out_dev[0..1] = Re, Im of
  *                        sum_cells F exp(-i k . r) with r the component's staggered position
  *                        (App. A); its phase advance per step measures the scheme's omega(k)
- *                        of Eq. (dispersion_relation), Sec. 3.                          */
+ *                        of Eq. (dispersion_relation), Sec. 3.
+ *   FDTD_DIAG_MOMENTS:   params = {axis 0..2}; out_dev[0..2] = (W, C, S) = sum over the six
+ *                        components and all cells of (1/2) F^2 dV (1, cos th, sin th), with
+ *                        th = 2 pi (index_a + o) / n_a and o = 1/2 for components staggered
+ *                        along the axis (App. A).  atan2(S, C) n_a dx_a / (2 pi) is the
+ *                        periodic (circular-mean) energy centroid of a wave packet; its
+ *                        speed is the packet's group velocity (Sec. 5).               */
 #define FDTD_DIAG_ENERGY    0
 #define FDTD_DIAG_PLANEWAVE 1
+#define FDTD_DIAG_MOMENTS   2
 int fdtd_diagnostic(fdtd_handle* h, int32_t kind, const double* params, double* out_dev);
 
 /* Divergences of the current state, FP64, dense [nz][ny][nx] into out_dev (device):

@@ -382,6 +382,30 @@ def plane_wave_amplitude(F, kvec, dx, offset=(0.0, 0.0, 0.0)):
     return complex(np.sum(F * ph))
 
 
+def energy_moments(s: State, axis, dx):
+    """Energy moments along one axis, for the packet centroid (Sec. 5, group velocity):
+    (W, C, S) = sum over the six components and all cells of (1/2) F^2 dV (1, cos th, sin th),
+    th = 2 pi (index_axis + o) / n_axis, o = 1/2 where the component is staggered along the axis
+    (E_axis, and the two B components other than B_axis; App. A positions).
+    The periodic centroid is atan2(S, C) n_axis dx_axis / (2 pi)."""
+    fields = list(s.E) + list(s.B)
+    n = fields[0].shape[2 - axis]
+    dV = dx[0] * dx[1] * dx[2]
+    W = C = S = 0.0
+    for q, F in enumerate(fields):
+        comp = q % 3
+        staggered = (comp == axis) if q < 3 else (comp != axis)
+        o = 0.5 if staggered else 0.0
+        th = 2.0 * math.pi * (np.arange(n) + o) / n
+        e = 0.5 * F * F * dV
+        # sum over the two other axes, leaving a profile along `axis`
+        prof = e.sum(axis=tuple(a for a in range(3) if a != 2 - axis))
+        W += float(prof.sum())
+        C += float(np.sum(prof * np.cos(th)))
+        S += float(np.sum(prof * np.sin(th)))
+    return W, C, S
+
+
 def dt_of_courant(nu, dtmax):
     return nu * dtmax
 
@@ -391,5 +415,5 @@ def isclose_rel(a, b, tol):
 
 
 __all__ = ["Coeffs", "State", "Bunch", "step", "run", "adjoint_step", "grad_to_arrays",
-           "div_star_B", "div_yee_B", "div_E", "energy", "plane_wave_amplitude",
+           "div_star_B", "div_yee_B", "div_E", "energy", "plane_wave_amplitude", "energy_moments",
            "sponge_factor", "COEF_KEYS", "math"]

@@ -33,6 +33,7 @@ FDTD_W_CONE_X = 1
 FDTD_W_GAUSS_Y = 2
 FDTD_DIAG_ENERGY = 0
 FDTD_DIAG_PLANEWAVE = 1
+FDTD_DIAG_MOMENTS = 2
 FDTD_DIV_STAR_B = 0
 FDTD_DIV_YEE_B = 1
 FDTD_DIV_E = 2

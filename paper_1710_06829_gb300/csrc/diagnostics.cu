@@ -5,6 +5,10 @@
 //   plane-wave amplitude:  sum_cells F_c exp(-i k . r_c), r_c the component's staggered
 //                          position (App. A) -- the measured phase advance per step gives the
 //                          scheme's omega(k) (Sec. 3), its envelope the group velocity (Sec. 5);
+//   energy moments:        sum e (1, cos th, sin th) dV with e = (1/2) F^2 per component at its
+//                          staggered position and th = 2 pi x_a / L_a along one axis: the
+//                          circular mean atan2(S, C) L_a / 2 pi is the centroid of a wave
+//                          packet on the periodic grid, its speed the group velocity (Sec. 5);
 //   divergences:           D* . B (Eq. divstarb, extended stencil), Yee D . B and D . E
 //                          (Eq. divE) written per cell to a dense caller buffer.
 // Partials: one FP64 value (or pair) per block, summed in a fixed order by one block.
@@ -87,6 +91,47 @@ planewave_kernel(Geom g, const T* __restrict__ F, double kx, double ky, double k
         acc[1] -= v * sn;
     }
     block_reduce_store<2>(acc, part);
+}
+
+// sum over components and cells of (1/2) F^2 (1, cos th, sin th), th = 2 pi (idx_a + off) / n_a
+// with off = 1/2 for the components staggered along a (App. A positions)
+template <typename T>
+__global__ void __launch_bounds__(DG_THREADS)
+moments_kernel(Geom g, FieldSet<T> s, int axis, double* part) {
+    double acc[3] = {0.0, 0.0, 0.0};
+    const long long n = (long long)g.nx * g.ny * g.nz;
+    const int na = axis == 0 ? g.nx : axis == 1 ? g.ny : g.nz;
+    const double w = 2.0 * M_PI / na;
+    // staggered along `axis`: E_a, and the two B components other than B_a
+    bool half[6];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        half[c] = c == axis;
+        half[3 + c] = c != axis;
+    }
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(t % g.nx);
+        const long long r = t / g.nx;
+        const int j = (int)(r % g.ny);
+        const int k = (int)(r / g.ny);
+        const int ia = axis == 0 ? i : axis == 1 ? j : k;
+        double s0, c0, sh, ch;
+        sincos(w * ia, &s0, &c0);
+        sincos(w * (ia + 0.5), &sh, &ch);
+        const long long c = pidx(g, i, j, k);
+        double e0 = 0.0, eh = 0.0;
+#pragma unroll
+        for (int q = 0; q < 6; ++q) {
+            const double v = (double)s.c[q][c];
+            if (half[q]) eh += v * v;
+            else e0 += v * v;
+        }
+        acc[0] += e0 + eh;
+        acc[1] += e0 * c0 + eh * ch;
+        acc[2] += e0 * s0 + eh * sh;
+    }
+    block_reduce_store<3>(acc, part);
 }
 
 __global__ void final_sum_kernel(const double* __restrict__ part, int nblocks, int nv, double scale,
@@ -176,6 +221,14 @@ void launch_planewave(const Geom& g, const T* F, const double k[3], const double
 }
 
 template <typename T>
+void launch_moments(const Geom& g, FieldSet<T> s, int axis, double dV, double* part, double* out,
+                    cudaStream_t st) {
+    const int nb = diag_blocks(g);
+    moments_kernel<T><<<nb, DG_THREADS, 0, st>>>(g, s, axis, part);
+    final_sum_kernel<<<1, dim3(32, 3), 0, st>>>(part, nb, 3, 0.5 * dV, out);
+}
+
+template <typename T>
 void launch_divergence(const Geom& g, const Mult<double>& w, FieldSet<T> s, int which, double* out,
                        cudaStream_t st) {
     const long long n = (long long)g.nx * g.ny * g.nz;
@@ -190,6 +243,10 @@ template void launch_planewave<float>(const Geom&, const float*, const double[3]
                                       double*, double*, cudaStream_t);
 template void launch_planewave<double>(const Geom&, const double*, const double[3],
                                        const double[3], double*, double*, cudaStream_t);
+template void launch_moments<float>(const Geom&, FieldSet<float>, int, double, double*, double*,
+                                    cudaStream_t);
+template void launch_moments<double>(const Geom&, FieldSet<double>, int, double, double*, double*,
+                                     cudaStream_t);
 template void launch_divergence<float>(const Geom&, const Mult<double>&, FieldSet<float>, int,
                                        double*, cudaStream_t);
 template void launch_divergence<double>(const Geom&, const Mult<double>&, FieldSet<double>, int,

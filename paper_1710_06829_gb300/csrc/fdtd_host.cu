@@ -58,6 +58,9 @@ template <typename T>
 void launch_planewave(const Geom& g, const T* F, const double k[3], const double off[3],
                       double* part, double* out, cudaStream_t st);
 template <typename T>
+void launch_moments(const Geom& g, FieldSet<T> s, int axis, double dV, double* part, double* out,
+                    cudaStream_t st);
+template <typename T>
 void launch_divergence(const Geom& g, const Mult<double>& w, FieldSet<T> s, int which, double* out,
                        cudaStream_t st);
 
@@ -245,7 +248,7 @@ struct fdtd_handle {
     char* staging;      // one dense array
     long long step;
     int use_fused;
-    double* dpart;      // diagnostics partials (2 per block)
+    double* dpart;      // diagnostics partials (3 per block)
     std::vector<FusedMaps> hist_maps;   // TMA descriptors of each history snapshot (FP32 adjoint)
     FusedMaps lam_maps;                 // .e[c]: TMA descriptors of lambda_B component c (FP32)
     bool lam_staged = false;            // lam_maps valid: the staged FP32 adjoint E kernel runs
@@ -838,7 +841,7 @@ int fdtd_step_adjoint(fdtd_handle* h, int32_t n, const fdtd_probe* probe, double
 
 static int ensure_dpart(fdtd_handle* h) {
     if (h->dpart) return FDTD_OK;
-    CK(cudaMalloc(&h->dpart, (size_t)diag_blocks(h->g) * 2 * sizeof(double)));
+    CK(cudaMalloc(&h->dpart, (size_t)diag_blocks(h->g) * 3 * sizeof(double)));
     return FDTD_OK;
 }
 
@@ -867,6 +870,12 @@ int fdtd_diagnostic(fdtd_handle* h, int32_t kind, const double* params, double* 
         const double kd[3] = {params[1] * h->dx[0], params[2] * h->dx[1], params[3] * h->dx[2]};
         if (f32) launch_planewave<float>(g, (const float*)h->arr(h->cur, comp), kd, offs[comp], h->dpart, out_dev, h->stream);
         else launch_planewave<double>(g, (const double*)h->arr(h->cur, comp), kd, offs[comp], h->dpart, out_dev, h->stream);
+    } else if (kind == FDTD_DIAG_MOMENTS) {
+        const int axis = (int)params[0];
+        if (axis < 0 || axis > 2) { set_error("fdtd_diagnostic: axis must be 0..2"); return FDTD_EINVAL; }
+        const double dV = h->dx[0] * h->dx[1] * h->dx[2];
+        if (f32) launch_moments<float>(g, fieldset<float>(h, h->cur), axis, dV, h->dpart, out_dev, h->stream);
+        else launch_moments<double>(g, fieldset<double>(h, h->cur), axis, dV, h->dpart, out_dev, h->stream);
     } else {
         set_error("fdtd_diagnostic: unknown kind %d", kind);
         return FDTD_EINVAL;

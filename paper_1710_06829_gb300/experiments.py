@@ -57,6 +57,32 @@ def measure_omega(sm, comp, kvec, nsteps):
 
 # ---------------------------------------------------------------- plane waves (phase / group)
 
+def packet_velocity(beta, delta, dt, lam, nx=1024, sigma=32.0, nsteps=400, every=20):
+    """Energy-centroid speed of a Gaussian packet along x (FP32, nx x 8 x 8) and the
+    closed-form group velocity d omega / d k_x (central difference of libfdtd's omega(k))."""
+    dx = [1.0, 1.0, 1.0]
+    k0 = 2 * math.pi / lam
+    w0 = omega_closed((k0, 0, 0), beta, delta, dt, dx)
+    h = 1e-5
+    vg = (omega_closed((k0 + h, 0, 0), beta, delta, dt, dx) -
+          omega_closed((k0 - h, 0, 0), beta, delta, dt, dx)) / (2 * h)
+    shape = (nx, 8, 8)
+    sm = S.Simulation(shape, dx, dt, beta, delta, dims=3, dtype="f32")
+    fields = inputs.packet_x(shape, dx, nx / 4, sigma, lam, w0, dt)
+    sm.set_state([torch.from_numpy(f.astype(np.float32)) for f in fields])
+    mom = torch.empty((nsteps // every + 1, 3), dtype=torch.float64, device="cuda")
+    for i in range(nsteps // every + 1):
+        if i:
+            sm.step(every)
+        sm.energy_moments(0, out=mom[i])
+    sm.close()
+    m = mom.cpu().numpy()
+    xs = np.unwrap(np.arctan2(m[:, 2], m[:, 1])) * nx / (2 * math.pi)
+    ts = np.arange(len(xs)) * every * dt
+    v = float(np.polyfit(ts, xs, 1)[0])
+    return {"lambda": lam, "sigma": sigma, "vg_packet": v, "vg_closed": vg, "vg_rel_err": v / vg - 1}
+
+
 def dispersion(n=256, nsteps=400):
     dx = [1.0, 1.0, 1.0]
     sets = {"yee": (np.zeros((3, 3)), np.zeros(3))}
@@ -88,8 +114,18 @@ def dispersion(n=256, nsteps=400):
                     "vg_sim": (w1 - w0) / (kn1 - kn0), "vg_closed_fd": (wc1 - wc0) / (kn1 - kn0)})
         sm.close()
     worst = max(abs(r["omega_rel_err"]) for r in rows)
+    packets = []
+    for name, (beta, delta) in sets.items():
+        dtm, _, _ = S.dt_max(beta, delta, dx, 3)
+        for lam in (8, 16, 32):
+            r = packet_velocity(beta, delta, 0.95 * dtm, lam, sigma=4.0 * lam if lam < 16 else 2.0 * lam)
+            r["coeffs"] = name
+            packets.append(r)
     return {"experiment": "dispersion", "grid": [n, n, n], "dtype": "f32", "steps": nsteps,
-            "courant": "0.95 of dt_max", "worst_omega_rel_err": worst, "rows": rows}
+            "courant": "0.95 of dt_max", "worst_omega_rel_err": worst, "rows": rows,
+            "packets": {"grid": [1024, 8, 8], "steps": 400, "measure": "energy-centroid speed "
+                        "(FDTD_DIAG_MOMENTS) vs closed-form d omega / d k_x", "rows": packets,
+                        "worst_vg_rel_err": max(abs(r["vg_rel_err"]) for r in packets)}}
 
 
 # ---------------------------------------------------------------- rigid bunch (Cherenkov)

@@ -67,6 +67,23 @@ def plane_wave(shape_xyz, kvec, pol, dx, amplitude=1.0):
     return E + [zero, zero.copy(), zero.copy()]
 
 
+def packet_x(shape_xyz, dx, x_center, sigma, wavelength, omega0, dt):
+    """Plane packet moving along +x, uniform in y and z: E_z = g(x - xc) cos(k0 (x - xc)) at
+    t = 0 and B_y = -g(x - xc + v dt/2) cos(k0 (x - xc) + omega0 dt/2) at t = -dt/2 (the
+    leapfrog's B time), g a Gaussian of width sigma, k0 = 2 pi / wavelength and v = omega0 / k0.
+    omega0 is the caller's angular frequency for k0 (it only sets the initial phase of B)."""
+    nx, ny, nz = shape_xyz
+    k0 = 2 * math.pi / wavelength
+    v = omega0 / k0
+    zero = np.zeros((nz, ny, nx))
+    x, _, _ = positions(shape_xyz, 2, dx)
+    Ez = np.exp(-((x - x_center) ** 2) / (2 * sigma ** 2)) * np.cos(k0 * (x - x_center))
+    xb, _, _ = positions(shape_xyz, 4, dx)
+    u = xb - x_center + 0.5 * v * dt
+    By = -np.exp(-(u ** 2) / (2 * sigma ** 2)) * np.cos(k0 * (xb - x_center) + 0.5 * omega0 * dt)
+    return [zero, zero.copy(), Ez, zero.copy(), By, zero.copy()]
+
+
 def gaussian_pulse_2d(shape_xy, dx, center, waist, wavelength, seed=0, noise=1e-3):
     """2D TE pulse: stream function psi = exp(-r^2/waist^2) cos(2 pi x / wavelength) (+ seeded
     noise) sampled at the B_z positions; returned as psi (ny, nx).  Fields are derived from psi

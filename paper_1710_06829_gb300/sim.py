@@ -165,6 +165,14 @@ class Simulation:
         L.fdtd_diagnostic(self.h, L.FDTD_DIAG_PLANEWAVE, [component, *k], out.data_ptr())
         return out
 
+    def energy_moments(self, axis, out=None):
+        """(W, C, S) = sum (1/2) F^2 dV (1, cos th, sin th), th = 2 pi x_axis / L_axis, over the
+        six components at their staggered positions (FP64, device tensor of 3).  The periodic
+        energy centroid of a packet is atan2(S, C) L_axis / (2 pi)."""
+        out = out if out is not None else torch.empty(3, dtype=torch.float64, device="cuda")
+        L.fdtd_diagnostic(self.h, L.FDTD_DIAG_MOMENTS, [axis], out.data_ptr())
+        return out
+
     def divergence(self, which):
         """Dense FP64 divergence field (nz, ny, nx): L.FDTD_DIV_STAR_B / _YEE_B / _E."""
         out = torch.empty(self.shape, dtype=torch.float64, device="cuda")

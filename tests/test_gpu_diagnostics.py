@@ -118,3 +118,55 @@ def test_div_star_B_conserved_full_size_and_yee_div_B_is_not():
     ydrift = float((y1 - y0).abs().max() / y0.abs().max())
     assert drift < 1e-4          # FP32 round-off over 100 steps
     assert ydrift > 1e-2         # the random coefficients violate Eq. (beta)
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_energy_moments_match_oracle(dtype):
+    shape = (64, 16, 12)
+    sm, c, fields = make(shape, dtype=dtype)
+    sm.step(2)
+    st = [t.cpu().numpy().astype(np.float64) for t in sm.get_state()]
+    for axis in range(3):
+        ref = np.array(F.energy_moments(F.State(st[:3], st[3:]), axis, c.dx))
+        got = sm.energy_moments(axis).cpu().numpy()
+        assert np.max(np.abs(got - ref)) <= 1e-12 * ref[0], axis
+    sm.close()
+
+
+def test_packet_group_velocity_fp32_512():
+    """Sec. 5: the energy centroid of a Gaussian packet (sigma 32, lambda 16) along x moves at
+    the group velocity d omega / d k_x of Eq. (dispersion_relation); FP32, 512 x 8 x 8, 400
+    steps, a seeded extended coefficient set at Courant 0.95.  The finite-packet bias is
+    O((sigma k)^-2) times the curvature of v_g; the oracle run of the same packet measures
+    2.6e-5; the bound is 5e-4."""
+    nx = 512
+    shape = (nx, 8, 8)
+    dx = [1.0, 1.0, 1.0]
+    beta, delta = admissible_theta(1)
+    dt = 0.95 * D.dt_max(beta, delta, dx, 3)
+    lam, sigma, xc = 16.0, 32.0, 160.0
+    k0 = 2 * math.pi / lam
+    w0 = D.omega(k0, 0.0, 0.0, beta, delta, dt, dx, 3)
+    h = 1e-5
+    vg = (D.omega(k0 + h, 0.0, 0.0, beta, delta, dt, dx, 3) -
+          D.omega(k0 - h, 0.0, 0.0, beta, delta, dt, dx, 3)) / (2 * h)
+    fields = inputs.packet_x(shape, dx, xc, sigma, lam, w0, dt)
+    sm = S.Simulation(shape, dx, dt, beta, delta, dims=3, dtype="f32")
+    sm.set_state([torch.from_numpy(f.astype(np.float32)) for f in fields])
+    ts, xs = [], []
+    prev = None
+    for s in range(0, 401, 20):
+        if s:
+            sm.step(20)
+        W, C, Sn = (float(v) for v in sm.energy_moments(0).cpu())
+        x = math.atan2(Sn, C) * nx / (2 * math.pi)
+        if prev is not None:   # unwrap the periodic centroid
+            x += round((prev - x) / nx) * nx
+        prev = x
+        ts.append(s * dt)
+        xs.append(x)
+    sm.close()
+    v_meas = np.polyfit(ts, xs, 1)[0]
+    assert abs(v_meas / vg - 1) < 5e-4
+    W, C, Sn = F.energy_moments(F.State(fields[:3], fields[3:]), 0, dx)   # initial, oracle
+    assert abs(xs[0] - math.atan2(Sn, C) * nx / (2 * math.pi)) < 1e-3

@@ -209,3 +209,73 @@ def test_adjoint_gradient_vs_central_differences():
         dm[i] -= h
         fd = (loss(beta, dp) - loss(beta, dm)) / (2 * h)
         assert gd[i] == pytest.approx(fd, rel=1e-7, abs=1e-7)
+
+
+def _centroid(m, n):
+    W, C, S = m
+    return (math.atan2(S, C) * n / (2 * math.pi)) % n
+
+
+def test_energy_moments_pins():
+    """Packet centroid moments (Sec. 5 group velocity measurement): a single excited cell sits at
+    its component's staggered position (App. A), W is the field energy, and translating the
+    fields by m cells moves the centroid by exactly m (mod n)."""
+    nz, ny, nx = 3, 4, 40
+    dx = [1.0, 1.0, 1.0]
+    # E_y at i = 10 is not staggered along x; E_x and B_z are (offset 1/2); B_x is not
+    for comp, want in [(1, 10.0), (0, 10.5), (5, 10.5), (3, 10.0)]:
+        f = [np.zeros((nz, ny, nx)) for _ in range(6)]
+        f[comp][1, 2, 10] = 3.0
+        st = F.State(f[:3], f[3:])
+        m = F.energy_moments(st, 0, dx)
+        assert m[0] == pytest.approx(4.5)
+        assert _centroid(m, nx) == pytest.approx(want, abs=1e-12)
+    # along y: B_x is staggered along y, E_y too, E_x is not
+    f = [np.zeros((nz, ny, nx)) for _ in range(6)]
+    f[3][0, 1, 5] = 1.0
+    assert _centroid(F.energy_moments(F.State(f[:3], f[3:]), 1, dx), ny) == pytest.approx(1.5)
+    rng = np.random.default_rng(3)
+    f = [rng.standard_normal((nz, ny, nx)) for _ in range(6)]
+    st = F.State(f[:3], f[3:])
+    m0 = F.energy_moments(st, 0, [0.5, 2.0, 1.0])
+    assert m0[0] == pytest.approx(F.energy(st) * 1.0, rel=1e-12)
+    for shift in (1, 7, 39):
+        g = [np.roll(a, shift, axis=2) for a in f]
+        m = F.energy_moments(F.State(g[:3], g[3:]), 0, [0.5, 2.0, 1.0])
+        d = (_centroid(m, nx) - _centroid(m0, nx)) % nx
+        assert d == pytest.approx(shift, abs=1e-9)
+
+
+def test_packet_centroid_moves_at_group_velocity():
+    """Sec. 5: a Gaussian packet (sigma 32, lambda 16) on the oracle's leapfrog moves at the
+    closed-form group velocity d omega / d k_x of Eq. (dispersion_relation) (a seeded extended
+    coefficient set, whose v_g exceeds 1 by 1.3 %), measured by the energy centroid."""
+    import sys
+    import os
+    sys.path.insert(0, os.path.dirname(__file__))
+    from gpu_util import admissible_theta
+    from paper_1710_06829_gb300 import inputs
+    beta, delta = admissible_theta(1)
+    dx = [1.0, 1.0, 1.0]
+    dt = 0.95 * D.dt_max(beta, delta, dx, 3)
+    k0 = 2 * math.pi / 16
+    w0 = D.omega(k0, 0.0, 0.0, beta, delta, dt, dx, 3)
+    h = 1e-5
+    vg = (D.omega(k0 + h, 0, 0, beta, delta, dt, dx, 3) - D.omega(k0 - h, 0, 0, beta, delta, dt, dx, 3)) / (2 * h)
+    nx = 512
+    f = inputs.packet_x((nx, 2, 2), dx, 160.0, 32.0, 16.0, w0, dt)
+    st = F.State([a.copy() for a in f[:3]], [a.copy() for a in f[3:]])
+    c = F.Coeffs(beta, delta, dx, dt)
+    ts, xs, prev = [], [], None
+    for s in range(0, 201, 20):
+        if s:
+            F.run(st, c, 20)
+        x = _centroid(F.energy_moments(st, 0, dx), nx)
+        if prev is not None:
+            x += round((prev - x) / nx) * nx
+        prev = x
+        ts.append(s * dt)
+        xs.append(x)
+    v = np.polyfit(ts, xs, 1)[0]
+    assert vg > 1.005                      # the set is superluminal at lambda = 16 ...
+    assert abs(v / vg - 1) < 2e-4          # ... and the packet follows d omega / d k
