@@ -5,9 +5,9 @@
     python -m paper_1710_06829_gb300.experiments differentiable  # 128^3 checkpointed gradient
     python -m paper_1710_06829_gb300.experiments optimize        # coefficient minimisation
 
-Each prints one JSON object.  Every number comes from libfdtd's kernels; closed forms used
-for comparison (omega(k), its k-gradient) are evaluated here in FP64 from Eq. (dispersion_
-relation) only to report the deviation of the simulated values from them.
+Each prints one JSON object.  Every number comes from libfdtd's kernels, including the closed
+forms used for comparison (omega(k) of Eq. (dispersion_relation) and its k-gradient, from the
+omega(k) kernel in FP64).
 """
 from __future__ import annotations
 
@@ -207,14 +207,16 @@ def differentiable(n=128, nsteps=500, every=50, h=1e-4):
     for dtype in ("f32", "f64"):
         prob = ProbeLossProblem(shape, dx, dt, init, 2, xp, torch.from_numpy(tgt).cuda(), nsteps,
                                 every, dtype=dtype)
-        theta = theta0.clone().requires_grad_(True)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        beta, delta = tied_coefficients(theta)
-        loss = FdtdProbeLoss.apply(beta, delta, prob)
-        loss.backward()
-        torch.cuda.synchronize()
-        res[dtype] = (float(loss.detach()), theta.grad.numpy().copy(), time.perf_counter() - t0, prob)
+        # the first evaluation allocates the history, checkpoint and adjoint buffers; time the second
+        for rep in range(2):
+            theta = theta0.clone().requires_grad_(True)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            beta, delta = tied_coefficients(theta)
+            loss = FdtdProbeLoss.apply(beta, delta, prob)
+            loss.backward()
+            torch.cuda.synchronize()
+            res[dtype] = (float(loss.detach()), theta.grad.numpy().copy(), time.perf_counter() - t0, prob)
     # central differences of the FP64 GPU forward
     prob64 = res["f64"][3]
 
