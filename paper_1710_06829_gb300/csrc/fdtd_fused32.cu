@@ -24,12 +24,37 @@
 // the reference-form kernels (dstar_taps): the fields are bitwise equal.  Every mbarrier wait is
 // bounded (fdtd_tma.cuh); on expiry the CTA raises *err, drains its copies in flight (bounded)
 // and returns.
+#include <cstring>
+
 #include "fdtd_seg.cuh"
 
 namespace fdtd {
 namespace f32seg {
 
 using namespace seg;
+
+// the FP32 multipliers, each duplicated into a pair for the paired arithmetic
+struct Mult2 {
+    u64 cA[3], cD[3], cB[3][3], cE[3], ncE[3];   // ncE = -cE
+};
+
+inline Mult2 make_mult2(const Mult<float>& m) {
+    auto dup = [](float v) {
+        u64 r;
+        const float two[2] = {v, v};
+        memcpy(&r, two, sizeof r);
+        return r;
+    };
+    Mult2 p;
+    for (int a = 0; a < 3; ++a) {
+        p.cA[a] = dup(m.cA[a]);
+        p.cD[a] = dup(m.cD[a]);
+        p.cE[a] = dup(m.cE[a]);
+        p.ncE[a] = dup(-m.cE[a]);
+        for (int b = 0; b < 3; ++b) p.cB[a][b] = dup(m.cB[a][b]);
+    }
+    return p;
+}
 
 constexpr int W = 4;                                            // cells per thread (along x)
 constexpr int TX = 64, TY = 8, D = 1;   // z-chunk length: launch parameter (zchunk_len)
@@ -83,7 +108,7 @@ __device__ __forceinline__ void dstar_x(const float* Fm, const float* F0, const 
 }
 
 __global__ void __launch_bounds__(NT, 3)
-step_kernel(const __grid_constant__ FusedMaps maps, Geom g, Mult<float> m, FieldSet<float> in,
+step_kernel(const __grid_constant__ FusedMaps maps, Geom g, Mult<float> m, Mult2 m2, FieldSet<float> in,
             FieldSet<float> out, const float* __restrict__ spy, const float* __restrict__ spz,
             const float* __restrict__ jyz, const float* __restrict__ jx_row,
             float* __restrict__ h0, float* __restrict__ h1, float* __restrict__ h2, int tz,
@@ -225,30 +250,46 @@ step_kernel(const __grid_constant__ FusedMaps maps, Geom g, Mult<float> m, Field
                 for (int u = 0; u < W; ++u) bo[c][u] = bn[c][u];
             // issue the next plane's B^{n-1/2} loads first: they complete during this plane's work
             if (it + 1 < niter) load_bold(pw + 1 == g.nz ? 0 : pw + 1, bn);
-            float dz[W], dy[W], bxv[W], byv[W], bzv[W];
+            // cell pairs (0, 1) and (2, 3) in f32x2 arithmetic; D*_x stays scalar (its taps are
+            // shifted along x, which does not keep pairs aligned)
+            u64 dz2[2], dy2[2], b2[3][2];
+            float t[W];
             // B_x = B_x + (D*_z E_y - D*_y E_z)
-            dstar_z(Pm + ESLOT, P0 + ESLOT, P1 + ESLOT, P2 + ESLOT, e, lb, rb, m.cA[2], m.cD[2],
-                    m.cB[2][0], m.cB[2][1], dz);
-            dstar_y(Pm + 2 * ESLOT, P0 + 2 * ESLOT, P1 + 2 * ESLOT, e, lb, rb, m.cA[1], m.cD[1],
-                    m.cB[1][0], m.cB[1][2], dy);
+            dstar_z2<EW>(Pm + ESLOT, P0 + ESLOT, P1 + ESLOT, P2 + ESLOT, e, lb, rb, m2.cA[2], m2.cD[2],
+                         m2.cB[2][0], m2.cB[2][1], dz2);
+            dstar_y2<EW>(Pm + 2 * ESLOT, P0 + 2 * ESLOT, P1 + 2 * ESLOT, e, lb, rb, m2.cA[1], m2.cD[1],
+                         m2.cB[1][0], m2.cB[1][2], dy2);
 #pragma unroll
-            for (int u = 0; u < W; ++u) bxv[u] = bo[0][u] + (dz[u] - dy[u]);
+            for (int h = 0; h < 2; ++h)
+                b2[0][h] = add2(pk(bo[0][2 * h], bo[0][2 * h + 1]), sub2(dz2[h], dy2[h]));
             // B_y = B_y + (D*_x E_z - D*_z E_x)
             dstar_x(Pm + 2 * ESLOT, P0 + 2 * ESLOT, P1 + 2 * ESLOT, e, lb, rb, m.cA[0], m.cD[0],
-                    m.cB[0][1], m.cB[0][2], dy);
-            dstar_z(Pm, P0, P1, P2, e, lb, rb, m.cA[2], m.cD[2], m.cB[2][0], m.cB[2][1], dz);
+                    m.cB[0][1], m.cB[0][2], t);
+            dstar_z2<EW>(Pm, P0, P1, P2, e, lb, rb, m2.cA[2], m2.cD[2], m2.cB[2][0], m2.cB[2][1], dz2);
 #pragma unroll
-            for (int u = 0; u < W; ++u) byv[u] = bo[1][u] + (dy[u] - dz[u]);
+            for (int h = 0; h < 2; ++h)
+                b2[1][h] = add2(pk(bo[1][2 * h], bo[1][2 * h + 1]), sub2(pk(t[2 * h], t[2 * h + 1]), dz2[h]));
             // B_z = B_z + (D*_y E_x - D*_x E_y)
-            dstar_y(Pm, P0, P1, e, lb, rb, m.cA[1], m.cD[1], m.cB[1][0], m.cB[1][2], dy);
+            dstar_y2<EW>(Pm, P0, P1, e, lb, rb, m2.cA[1], m2.cD[1], m2.cB[1][0], m2.cB[1][2], dy2);
             dstar_x(Pm + ESLOT, P0 + ESLOT, P1 + ESLOT, e, lb, rb, m.cA[0], m.cD[0], m.cB[0][1],
-                    m.cB[0][2], dz);
+                    m.cB[0][2], t);
 #pragma unroll
-            for (int u = 0; u < W; ++u) bzv[u] = bo[2][u] + (dy[u] - dz[u]);
+            for (int h = 0; h < 2; ++h)
+                b2[2][h] = add2(pk(bo[2][2 * h], bo[2][2 * h + 1]), sub2(dy2[h], pk(t[2 * h], t[2 * h + 1])));
             if (spy != nullptr) {
                 const float f = spy[b_y] * spz[pw];
+                const u64 f2 = pk(f, f);
 #pragma unroll
-                for (int u = 0; u < W; ++u) { bxv[u] *= f; byv[u] *= f; bzv[u] *= f; }
+                for (int c = 0; c < 3; ++c)
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) b2[c][h] = mul2(b2[c][h], f2);
+            }
+            float bxv[W], byv[W], bzv[W];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                upk(b2[0][h], bxv[2 * h], bxv[2 * h + 1]);
+                upk(b2[1][h], byv[2 * h], byv[2 * h + 1]);
+                upk(b2[2][h], bzv[2 * h], bzv[2 * h + 1]);
             }
             if (b_store) {
                 stv(sB + r3 * BSLOT, bi, bxv);
@@ -285,12 +326,28 @@ step_kernel(const __grid_constant__ FusedMaps maps, Geom g, Mult<float> m, Field
                 Bz[0] = Bzc[bi - 1];
                 By[0] = Byc[bi - 1];
             }
+            // ampere_comp on cell pairs: e + fma(c1, p0 - pm, -(c2 (q0 - qm)))
             float ex[W], ey[W], ez[W];
+            auto amp2 = [](u64 e2, u64 dp, u64 dq, u64 c1, u64 nc2) {
+                return add2(e2, fma2(c1, dp, mul2(nc2, dq)));
+            };
 #pragma unroll
-            for (int u = 0; u < W; ++u) {
-                ex[u] = ampere_comp(E0x.v[u], Bz[1 + u], Bzy.v[u], By[1 + u], Byz.v[u], m.cE[1], m.cE[2]);
-                ey[u] = ampere_comp(E0y.v[u], Bx.v[u], Bxz.v[u], Bz[1 + u], Bz[u], m.cE[2], m.cE[0]);
-                ez[u] = ampere_comp(E0z.v[u], By[1 + u], By[u], Bx.v[u], Bxy.v[u], m.cE[0], m.cE[1]);
+            for (int h = 0; h < 2; ++h) {
+                const int u = 2 * h;
+                const u64 rx = amp2(pk(E0x.v[u], E0x.v[u + 1]),
+                                    sub2(pk(Bz[1 + u], Bz[2 + u]), pk(Bzy.v[u], Bzy.v[u + 1])),
+                                    sub2(pk(By[1 + u], By[2 + u]), pk(Byz.v[u], Byz.v[u + 1])),
+                                    m2.cE[1], m2.ncE[2]);
+                const u64 ry = amp2(pk(E0y.v[u], E0y.v[u + 1]),
+                                    sub2(pk(Bx.v[u], Bx.v[u + 1]), pk(Bxz.v[u], Bxz.v[u + 1])),
+                                    pk(Bz[1 + u] - Bz[u], Bz[2 + u] - Bz[1 + u]), m2.cE[2], m2.ncE[0]);
+                const u64 rz = amp2(pk(E0z.v[u], E0z.v[u + 1]),
+                                    pk(By[1 + u] - By[u], By[2 + u] - By[1 + u]),
+                                    sub2(pk(Bx.v[u], Bx.v[u + 1]), pk(Bxy.v[u], Bxy.v[u + 1])),
+                                    m2.cE[0], m2.ncE[1]);
+                upk(rx, ex[u], ex[u + 1]);
+                upk(ry, ey[u], ey[u + 1]);
+                upk(rz, ez[u], ez[u + 1]);
             }
             const int i0 = x0 + b_bx, j = y0 + b_by;
             if (jx_row != nullptr) {
@@ -400,7 +457,7 @@ void launch_fused32(const FusedMaps& maps, FieldSet<float> in, const Geom& g, co
     using namespace f32seg;
     const int tz = fused32_tz(g);
     const int nblk = (g.nx / TX) * (g.ny / TY) * ((g.nz + tz - 1) / tz);
-    step_kernel<<<nblk, NT, SMEM, st>>>(maps, g, m, in, out, spy, spz, jyz, jx_row, hist_E[0],
+    step_kernel<<<nblk, NT, SMEM, st>>>(maps, g, m, make_mult2(m), in, out, spy, spz, jyz, jx_row, hist_E[0],
                                         hist_E[1], hist_E[2], tz, err);
 }
 

@@ -159,3 +159,99 @@ __device__ __forceinline__ void taps_x(const float* Fm, const float* F0, const f
 
 }  // namespace seg
 }  // namespace fdtd
+
+namespace fdtd {
+namespace seg {
+
+// ---- paired FP32 arithmetic (f32x2: two lanes of data per instruction, IEEE round to nearest,
+// so every result equals the scalar operation's).  A pair holds two neighbouring cells.
+using u64 = unsigned long long;
+
+__device__ __forceinline__ u64 pk(float a, float b) {
+    u64 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void upk(u64 r, float& a, float& b) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
+}
+__device__ __forceinline__ u64 add2(u64 a, u64 b) {
+    u64 r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ u64 sub2(u64 a, u64 b) {
+    u64 r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ u64 mul2(u64 a, u64 b) {
+    u64 r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ u64 fma2(u64 a, u64 b, u64 c) {
+    u64 r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+__device__ __forceinline__ u64 lo2(const Q4& q) { return pk(q.v[0], q.v[1]); }
+__device__ __forceinline__ u64 hi2(const Q4& q) { return pk(q.v[2], q.v[3]); }
+
+// dstar_diff on a pair of cells, with the transverse sums already formed:
+//   cA d_a + cD (f_a2 - f_am1) + cBb sb + cBc sc, in the order of dstar_diff
+__device__ __forceinline__ u64 dstar_pair(u64 da, u64 a2, u64 am1, u64 sb, u64 sc, u64 cA, u64 cD,
+                                          u64 cBb, u64 cBc) {
+    u64 v = mul2(cA, da);
+    v = fma2(cD, sub2(a2, am1), v);
+    v = fma2(cBb, sb, v);
+    v = fma2(cBc, sc, v);
+    return v;
+}
+
+// D*_z (x then y transverse) on the four cells at e, as two cell pairs; as taps_z + dstar_diff
+template <int EW>
+__device__ __forceinline__ void dstar_z2(const float* Fm, const float* F0, const float* F1,
+                                         const float* F2, int e, bool lb, bool rb, u64 cA,
+                                         u64 cD, u64 cBx, u64 cBy, u64 out[2]) {
+    const Q4 c1 = ldq(F1, e), c0 = ldq(F0, e), c2 = ldq(F2, e), cm = ldq(Fm, e);
+    const Q4 p1 = ldq(F1, e + EW), p0 = ldq(F0, e + EW), m1 = ldq(F1, e - EW),
+             m0 = ldq(F0, e - EW);
+    const u64 dlo = sub2(lo2(c1), lo2(c0)), dhi = sub2(hi2(c1), hi2(c0));   // F1 - F0, x .. x+3
+    float d[6];
+    upk(dlo, d[1], d[2]);
+    upk(dhi, d[3], d[4]);
+    d[0] = from_left(d[4]);
+    d[5] = from_right(d[1]);
+    if (lb) d[0] = F1[e - 1] - F0[e - 1];
+    if (rb) d[5] = F1[e + 4] - F0[e + 4];
+    const u64 sylo = add2(sub2(lo2(p1), lo2(p0)), sub2(lo2(m1), lo2(m0)));
+    const u64 syhi = add2(sub2(hi2(p1), hi2(p0)), sub2(hi2(m1), hi2(m0)));
+    out[0] = dstar_pair(dlo, lo2(c2), lo2(cm), pk(d[2] + d[0], d[3] + d[1]), sylo, cA, cD, cBx, cBy);
+    out[1] = dstar_pair(dhi, hi2(c2), hi2(cm), pk(d[4] + d[2], d[5] + d[3]), syhi, cA, cD, cBx, cBy);
+}
+
+// D*_y (x then z transverse), as taps_y + dstar_diff
+template <int EW>
+__device__ __forceinline__ void dstar_y2(const float* Fm, const float* F0, const float* F1, int e,
+                                         bool lb, bool rb, u64 cA, u64 cD, u64 cBx, u64 cBz,
+                                         u64 out[2]) {
+    const Q4 a0 = ldq(F0, e), a1 = ldq(F0, e + EW), a2 = ldq(F0, e + 2 * EW),
+             am = ldq(F0, e - EW);
+    const Q4 b1 = ldq(F1, e), b1p = ldq(F1, e + EW), bm = ldq(Fm, e), bmp = ldq(Fm, e + EW);
+    const u64 dlo = sub2(lo2(a1), lo2(a0)), dhi = sub2(hi2(a1), hi2(a0));   // F0(y+1) - F0(y)
+    float d[6];
+    upk(dlo, d[1], d[2]);
+    upk(dhi, d[3], d[4]);
+    d[0] = from_left(d[4]);
+    d[5] = from_right(d[1]);
+    if (lb) d[0] = F0[e + EW - 1] - F0[e - 1];
+    if (rb) d[5] = F0[e + EW + 4] - F0[e + 4];
+    const u64 szlo = add2(sub2(lo2(b1p), lo2(b1)), sub2(lo2(bmp), lo2(bm)));
+    const u64 szhi = add2(sub2(hi2(b1p), hi2(b1)), sub2(hi2(bmp), hi2(bm)));
+    out[0] = dstar_pair(dlo, lo2(a2), lo2(am), pk(d[2] + d[0], d[3] + d[1]), szlo, cA, cD, cBx, cBz);
+    out[1] = dstar_pair(dhi, hi2(a2), hi2(am), pk(d[4] + d[2], d[5] + d[3]), szhi, cA, cD, cBx, cBz);
+}
+
+}  // namespace seg
+}  // namespace fdtd
