@@ -191,8 +191,17 @@ int fdtd_diagnostic(fdtd_handle* h, int32_t kind, const double* params, double* 
 #define FDTD_DIV_E      2
 int fdtd_divergence(fdtd_handle* h, int32_t which, double* out_dev);
 
+/* Failure-path self-test (no counterpart in the paper): launches, on the handle's stream, one
+ * thread that polls an mbarrier phase nothing will complete, with the same bounded-wait helper
+ * the TMA step kernels use, limited to `tries` polls (1 .. 2^20).  When the polls run out it
+ * raises the handle's error flag as an expired wait in a step kernel does, so the next
+ * fdtd_sync returns FDTD_ETIMEOUT (and clears the flag).  Nothing faults, traps or hangs; the
+ * handle stays usable.  Returns FDTD_EINVAL for tries outside the range. */
+int fdtd_selftest_wait_expiry(fdtd_handle* h, int32_t tries);
+
 /* Block until all work on the handle's stream has finished; reports any
- * asynchronous CUDA error. */
+ * asynchronous CUDA error, and FDTD_ETIMEOUT (clearing the flag) when a bounded
+ * wait inside a kernel expired since the last call. */
 int fdtd_sync(fdtd_handle* h);
 
 void fdtd_destroy(fdtd_handle* h);

@@ -45,7 +45,8 @@ STATUS_NAMES = {0: "FDTD_OK", -1: "FDTD_EINVAL", -2: "FDTD_EUNSTABLE", -3: "FDTD
 # every symbol include/fdtd.h declares
 EXPORTS = ["fdtd_create", "fdtd_set_coeffs", "fdtd_set_state", "fdtd_get_state", "fdtd_get_step",
            "fdtd_step", "fdtd_checkpoint", "fdtd_set_adjoint", "fdtd_get_adjoint",
-           "fdtd_step_adjoint", "fdtd_diagnostic", "fdtd_divergence", "fdtd_sync", "fdtd_destroy", "disp_norm_eval",
+           "fdtd_step_adjoint", "fdtd_diagnostic", "fdtd_divergence", "fdtd_selftest_wait_expiry",
+           "fdtd_sync", "fdtd_destroy", "disp_norm_eval",
            "disp_norm_eval_noalloc", "disp_omega_eval", "fdtd_coeff_update", "fdtd_dt_max", "fdtd_last_error"]
 
 
@@ -106,6 +107,7 @@ def load():
     lib.fdtd_diagnostic.argtypes = [P, I32, pd, P]
     lib.fdtd_divergence.argtypes = [P, I32, P]
     lib.fdtd_sync.argtypes = [P]
+    lib.fdtd_selftest_wait_expiry.argtypes = [P, C.c_int32]
     lib.fdtd_destroy.argtypes = [P]
     lib.fdtd_destroy.restype = None
     lib.disp_norm_eval.argtypes = [C.POINTER(fdtd_coeffs), D, pd, I32, C.POINTER(I32), I32, D,
@@ -210,6 +212,10 @@ def fdtd_divergence(h, which, out_dev):
 
 def fdtd_sync(h):
     check(load().fdtd_sync(h))
+
+
+def fdtd_selftest_wait_expiry(h, tries):
+    check(load().fdtd_selftest_wait_expiry(h, tries))
 
 
 def fdtd_destroy(h):

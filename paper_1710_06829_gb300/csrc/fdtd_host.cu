@@ -897,6 +897,29 @@ int fdtd_divergence(fdtd_handle* h, int32_t which, double* out_dev) {
     return FDTD_OK;
 }
 
+// One thread waits, with the kernels' bounded-wait helper, on an mbarrier phase that no
+// copy and no thread will ever complete; when its polls run out it raises the handle's error
+// flag exactly as an expired wait in a step kernel does, and returns.
+__global__ void wait_expiry_kernel(uint32_t tries, int* err) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        if (!mbar_wait_n(&bar, 0, tries)) atomicExch(err, 1);
+        asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(&bar)) : "memory");
+    }
+}
+
+int fdtd_selftest_wait_expiry(fdtd_handle* h, int32_t tries) {
+    if (!h || tries < 1 || tries > (1 << 20)) {
+        set_error("fdtd_selftest_wait_expiry: bad argument");
+        return FDTD_EINVAL;
+    }
+    wait_expiry_kernel<<<1, 32, 0, h->stream>>>((uint32_t)tries, h->err_dev);
+    CK(cudaGetLastError());
+    return FDTD_OK;
+}
+
 int fdtd_sync(fdtd_handle* h) {
     if (!h) { set_error("NULL handle"); return FDTD_EINVAL; }
     CK(cudaStreamSynchronize(h->stream));

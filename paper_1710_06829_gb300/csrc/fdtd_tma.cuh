@@ -47,11 +47,17 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     return ok != 0;
 }
 
-// bounded wait: about a second at most
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-    for (uint32_t it = 0; it < (1u << 20); ++it)
+// bounded wait: at most `tries` polls (each poll may suspend the thread for a short,
+// hardware-defined time); false when the phase did not complete
+__device__ __forceinline__ bool mbar_wait_n(uint64_t* bar, uint32_t parity, uint32_t tries) {
+    for (uint32_t it = 0; it < tries; ++it)
         if (mbar_try_wait(bar, parity)) return true;
     return false;
+}
+
+// the kernels' wait: about a second at most
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+    return mbar_wait_n(bar, parity, 1u << 20);
 }
 
 __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z,

@@ -13,6 +13,7 @@ pytestmark = pytest.mark.gpu
 
 from paper_1710_06829_gb300 import inputs  # noqa: E402
 from paper_1710_06829_gb300 import sim as S  # noqa: E402
+from paper_1710_06829_gb300 import _lib as L  # noqa: E402
 from paper_1710_06829_gb300._lib import FdtdError  # noqa: E402
 
 NP = {"f32": np.float32, "f64": np.float64}
@@ -253,3 +254,28 @@ def test_batched_2d_equals_independent_runs(dtype, shape):
         ref = run_oracle(c, f_k, 30, sponge=sp)
         err = rel_l2([g[k:k + 1] for g in got], ref)
         assert err <= (1e-12 if dtype == "f64" else 2e-6), (k, err)
+
+
+def test_expired_wait_reports_timeout_and_handle_stays_usable():
+    """Failure path without a fault: a bounded mbarrier wait that runs out raises the handle's
+    error flag; fdtd_sync reports FDTD_ETIMEOUT once, and the handle keeps stepping correctly."""
+    shape = (64, 16, 12)
+    beta, delta = admissible_theta(4)
+    dx = [1.0, 1.0, 1.0]
+    dt = 0.9 * D.dt_max(beta, delta, dx, 3)
+    fields = inputs.random_fields(shape, 7)
+    sm = S.Simulation(shape, dx, dt, beta, delta, dims=3, dtype="f64")
+    sm.set_state([torch.from_numpy(f) for f in fields])
+    with pytest.raises(L.FdtdError):
+        L.fdtd_selftest_wait_expiry(sm.h, 0)          # argument checked on the host
+    L.fdtd_selftest_wait_expiry(sm.h, 512)
+    with pytest.raises(L.FdtdError) as ei:
+        sm.sync()
+    assert ei.value.status == L.FDTD_ETIMEOUT
+    sm.sync()                                         # reported once, then cleared
+    sm.step(3)
+    got = [t.cpu().numpy() for t in sm.get_state()]
+    sm.close()
+    st = F.run(F.State(fields[:3], fields[3:]), F.Coeffs(beta, delta, dx, dt), 3)
+    for g, r in zip(got, st.E + st.B):
+        assert np.max(np.abs(g - r)) <= 1e-12 * max(1.0, np.max(np.abs(r)))
