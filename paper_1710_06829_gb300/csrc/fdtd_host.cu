@@ -245,7 +245,10 @@ struct fdtd_handle {
     int jx_cap;
     double* partials;   // adjoint gradient partials
     int npart;
-    char* staging;      // one dense array
+    char* staging[2];   // two dense arrays: host transfers of one component overlap the
+                        // (un)packing of the previous one
+    cudaStream_t xfer;  // copy stream of the host transfers
+    cudaEvent_t filled[2], freed[2];   // per staging buffer: data in place / buffer reusable
     long long step;
     int use_fused;
     double* dpart;      // diagnostics partials (3 per block)
@@ -448,47 +451,87 @@ int fdtd_set_coeffs(fdtd_handle* h, double dt, const fdtd_coeffs* coeffs) {
 }
 
 static int ensure_staging(fdtd_handle* h) {
-    if (h->staging) return FDTD_OK;
+    if (h->staging[0]) return FDTD_OK;
     const size_t n = (size_t)h->g.nx * h->g.ny * h->g.nz * h->esz;
-    CK(cudaMalloc(&h->staging, n));
+    CK(cudaStreamCreateWithFlags(&h->xfer, cudaStreamNonBlocking));
+    for (int b = 0; b < 2; ++b) {
+        CK(cudaEventCreateWithFlags(&h->filled[b], cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&h->freed[b], cudaEventDisableTiming));
+    }
+    for (int b = 0; b < 2; ++b) CK(cudaMalloc(&h->staging[b], n));
     return FDTD_OK;
 }
 
+// the copy stream starts after everything already queued on the handle's stream
+static int xfer_after_stream(fdtd_handle* h) {
+    CK(cudaEventRecord(h->filled[0], h->stream));
+    CK(cudaStreamWaitEvent(h->xfer, h->filled[0], 0));
+    return FDTD_OK;
+}
+
+// Host -> device: component c goes host -> staging[c % 2] on the copy stream, then is unpacked
+// (padded layout, periodic images) on the handle's stream; the copy of c + 1 overlaps the
+// unpacking of c.
 template <typename T>
 static int copy_in(fdtd_handle* h, void* const fields[6], int32_t mem, T* const dst[6]) {
     const size_t n = (size_t)h->g.nx * h->g.ny * h->g.nz;
+    if (mem == FDTD_MEM_HOST) {
+        int rc = ensure_staging(h);
+        if (rc) return rc;
+        rc = xfer_after_stream(h);
+        if (rc) return rc;
+    }
     for (int c = 0; c < 6; ++c) {
         const T* src = (const T*)(fields ? fields[c] : nullptr);
         if (src && mem == FDTD_MEM_HOST) {
-            int rc = ensure_staging(h);
-            if (rc) return rc;
-            CK(cudaMemcpyAsync(h->staging, src, n * sizeof(T), cudaMemcpyHostToDevice, h->stream));
-            src = (const T*)h->staging;
+            const int b = c & 1;
+            if (c >= 2) CK(cudaStreamWaitEvent(h->xfer, h->freed[b], 0));
+            CK(cudaMemcpyAsync(h->staging[b], src, n * sizeof(T), cudaMemcpyHostToDevice, h->xfer));
+            CK(cudaEventRecord(h->filled[b], h->xfer));
+            CK(cudaStreamWaitEvent(h->stream, h->filled[b], 0));
+            launch_unpack<T>(h->g, (const T*)h->staging[b], dst[c], h->stream);
+            CK(cudaGetLastError());
+            CK(cudaEventRecord(h->freed[b], h->stream));
+        } else {
+            launch_unpack<T>(h->g, src, dst[c], h->stream);
+            CK(cudaGetLastError());
         }
-        launch_unpack<T>(h->g, src, dst[c], h->stream);
-        CK(cudaGetLastError());
     }
     if (mem == FDTD_MEM_HOST) CK(cudaStreamSynchronize(h->stream));
     return FDTD_OK;
 }
 
+// Device -> host: component c is packed into staging[c % 2] on the handle's stream, then copied
+// to the host on the copy stream; the packing of c + 1 overlaps the copy of c.
 template <typename T>
 static int copy_out(fdtd_handle* h, void* const fields[6], int32_t mem, T* const srcs[6]) {
     const size_t n = (size_t)h->g.nx * h->g.ny * h->g.nz;
+    if (mem == FDTD_MEM_HOST) {
+        int rc = ensure_staging(h);
+        if (rc) return rc;
+    }
+    int used = 0;
     for (int c = 0; c < 6; ++c) {
         if (!fields[c]) continue;
         if (mem == FDTD_MEM_HOST) {
-            int rc = ensure_staging(h);
-            if (rc) return rc;
-            launch_pack<T>(h->g, srcs[c], (T*)h->staging, h->stream);
+            const int b = used & 1;
+            if (used >= 2) CK(cudaStreamWaitEvent(h->stream, h->freed[b], 0));
+            launch_pack<T>(h->g, srcs[c], (T*)h->staging[b], h->stream);
             CK(cudaGetLastError());
-            CK(cudaMemcpyAsync(fields[c], h->staging, n * sizeof(T), cudaMemcpyDeviceToHost, h->stream));
+            CK(cudaEventRecord(h->filled[b], h->stream));
+            CK(cudaStreamWaitEvent(h->xfer, h->filled[b], 0));
+            CK(cudaMemcpyAsync(fields[c], h->staging[b], n * sizeof(T), cudaMemcpyDeviceToHost, h->xfer));
+            CK(cudaEventRecord(h->freed[b], h->xfer));
+            ++used;
         } else {
             launch_pack<T>(h->g, srcs[c], (T*)fields[c], h->stream);
             CK(cudaGetLastError());
         }
     }
-    if (mem == FDTD_MEM_HOST) CK(cudaStreamSynchronize(h->stream));
+    if (mem == FDTD_MEM_HOST) {
+        CK(cudaStreamSynchronize(h->xfer));
+        CK(cudaStreamSynchronize(h->stream));
+    }
     return FDTD_OK;
 }
 
@@ -943,7 +986,15 @@ void fdtd_destroy(fdtd_handle* h) {
     if (h->aux) cudaFree(h->aux);
     if (h->jx) cudaFree(h->jx);
     if (h->partials) cudaFree(h->partials);
-    if (h->staging) cudaFree(h->staging);
+    if (h->staging[0]) {
+        cudaStreamSynchronize(h->xfer);
+        for (int b = 0; b < 2; ++b) {
+            cudaFree(h->staging[b]);
+            cudaEventDestroy(h->filled[b]);
+            cudaEventDestroy(h->freed[b]);
+        }
+        cudaStreamDestroy(h->xfer);
+    }
     if (h->err_dev) cudaFree(h->err_dev);
     if (h->dpart) cudaFree(h->dpart);
     if (h->plan) fused_plan_destroy(h->plan);
