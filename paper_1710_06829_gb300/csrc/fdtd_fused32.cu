@@ -156,7 +156,9 @@ step_kernel(const __grid_constant__ FusedMaps maps, Geom g, Mult<float> m, Mult2
                      : tid < NSEG * (TY + 1) ? -1 : min(tid - NSEG * (TY + 1) - 1, TY - 1);
     const bool b_store = tid < NBT;      // writes its B^{n+1/2} segment to the shared ring
     const bool b_own = tid < NSEG * TY;  // owned cells: stored to HBM, E phase
-    const bool lb = b_bx <= 0;           // no left neighbour lane in the row
+    // no left neighbour lane in the row (a halo-column segment skips its left side: x0-5 only
+    // reaches its first cell, x0-4, which is discarded)
+    const bool lb = b_bx == 0;
     const bool rb = b_bx < 0 || b_bx == TX - W;
     const int e = (b_by + 2) * EW + (b_bx + 4);   // in-plane index of the segment, E box
     const int bi = (b_by + 1) * BW + (b_bx + 4);  // in-plane index of the segment, B ring
