@@ -61,6 +61,10 @@ constexpr int TX = 64, TY = 8, D = 1;   // z-chunk length: launch parameter (zch
 constexpr int NSEG = TX / W;                                    // segments per row
 constexpr int NBT = NSEG * (TY + 1) + TY + 1;                   // B tasks: rows + halo column
 constexpr int NT = ((NBT + 31) / 32) * 32;
+// the thread that initialises the mbarriers, issues the TMA copies and waits for them: lane 0 of
+// the halo warp, which has no E update and reaches the block barrier first (with thread 0, the
+// copy waits and issues made the first owned-row warp the last to arrive every plane)
+constexpr int PRODUCER = NSEG * TY;
 // E box 76 x 12 (x0-4 .., y0-2 ..): the stencil needs x0-2 .. x0+65 (a 72-wide box); 76 floats
 // = 19 16-byte chunks per row put the halo-column lanes (one segment on each of nine rows) on
 // distinct bank groups, which removed most shared-memory bank conflicts.  In the last tile of a
@@ -169,14 +173,14 @@ step_kernel(const __grid_constant__ FusedMaps maps, Geom g, Mult<float> m, Mult2
     // owned-cell destinations of this thread's segment
     const SegOut dst = seg_out(g, x0 + (b_bx < 0 ? 0 : b_bx), y0 + (b_by < 0 ? 0 : b_by), edge);
 
-    if (tid == 0) {
+    if (tid == PRODUCER) {
         for (int s = 0; s <= NS; ++s) mbar_init(&bar[s], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
     __syncthreads();
     int issued = 0;
-    if (tid == 0) {
+    if (tid == PRODUCER) {
         mbar_expect_tx(&bar[NS], PRO_BYTES);
         for (int q = z0 - 2; q <= z0; ++q)
             for (int c = 0; c < 3; ++c) tma_load_3d(Ep(q, c), &maps.e[c], x0, y0, wrapz(q), &bar[NS]);
@@ -207,13 +211,13 @@ step_kernel(const __grid_constant__ FusedMaps maps, Geom g, Mult<float> m, Mult2
     // B^{n+1/2} ring: B_x, B_y keep planes p, p-1, p-2 (slot (p+6) mod 3); B_z keeps p, p-1.
     // Iteration it forms B^{n+1/2} on plane p = z0 - 1 + it (it < niter) and E^{n+1} on
     // plane p - 1 (when z0 <= p - 1 < zend).  One block barrier per iteration.
-    // Thread 0 waits for each plane's copies before the block barrier that precedes the
-    // plane's iteration; the other threads' own waits then return at once (no spinning).
+    // The producer thread waits for each plane's copies before the block barrier that precedes
+    // the plane's iteration; the other threads' own waits then return at once (no spinning).
     bool failed = false;
     int it = 0;
     {
         bool ok0 = true;
-        if (tid == 0) ok0 = mbar_wait(&bar[NS], 0) && mbar_wait(&bar[0], 0);
+        if (tid == PRODUCER) ok0 = mbar_wait(&bar[NS], 0) && mbar_wait(&bar[0], 0);
         failed = __syncthreads_or(!ok0);
     }
     // plane bookkeeping by counters (no integer division in the loop):
@@ -375,13 +379,13 @@ step_kernel(const __grid_constant__ FusedMaps maps, Geom g, Mult<float> m, Mult2
             }
         }
         bool ok_next = true;
-        if (tid == 0 && it + 1 < niter)
+        if (tid == PRODUCER && it + 1 < niter)
             ok_next = mbar_wait(&bar[(it + 1) % NS], (uint32_t)(((it + 1) / NS) & 1));
         if (__syncthreads_or(!ok || !ok_next)) {
             failed = true;
             break;
         }
-        if (tid == 0 && it + D + 1 < niter) {
+        if (tid == PRODUCER && it + D + 1 < niter) {
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             issue_unit(it + D + 1);
             issued = it + D + 2;
@@ -389,7 +393,7 @@ step_kernel(const __grid_constant__ FusedMaps maps, Geom g, Mult<float> m, Mult2
     }
     if (failed) {
         // the state written by this launch is not valid; drain this CTA's copies in flight
-        if (tid == 0) {
+        if (tid == PRODUCER) {
             atomicExch(err, 1);
             if (it == 0) mbar_wait(&bar[NS], 0);
             for (int u = it; u < issued; ++u) mbar_wait(&bar[u % NS], (uint32_t)((u / NS) & 1));
