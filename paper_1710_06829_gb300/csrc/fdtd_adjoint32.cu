@@ -215,9 +215,18 @@ adjB_kernel(const __grid_constant__ FusedMaps maps, Geom g, Mult<float> m, Field
             failed = true;
             break;
         }
-        if (tid == 0 && it + D + 1 < niter) {
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            issue_unit(it + D + 1);
+        // the next unit's three copies are issued by lane 0 of warps 1, 2, 3 (one component
+        // each; warp 1 also posts the expected bytes), so that no warp carries the whole issue
+        // on top of its share of the stencil; thread 0 keeps the waits
+        if (it + D + 1 < niter) {
+            const int c = tid / 32 - 1;
+            if ((tid & 31) == 0 && c >= 0 && c < 3) {
+                const int u = it + D + 1, qe = z0 + 2 + u;
+                uint64_t* b = &bar[u % NS];
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                if (c == 0) mbar_expect_tx(b, UNIT_BYTES);
+                tma_load_3d(Ep(qe, c), &maps.e[c], x0, y0, wrapz(qe), b);
+            }
             issued = it + D + 2;
         }
     }
