@@ -69,6 +69,7 @@ norm_kernel(NormParams p, const double* __restrict__ tab, double* __restrict__ p
     const double* s2z = kz + p.N[2];
     const double* cz = kz + 2 * p.N[2];
     const double dt = p.dt;
+    const double inv_dt = 1.0 / dt, two_over_dt = 2.0 * inv_dt;
     for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < p.npts;
          t += (long long)gridDim.x * blockDim.x) {
         const int mx = (int)(t % p.N[0]);
@@ -96,25 +97,28 @@ norm_kernel(NormParams p, const double* __restrict__ tab, double* __restrict__ p
             w = exp(-u * u);
         }
         if (w == 0.0) continue;
+        // one division per point: sqrt(S) / (dt sqrt(1 - dt^2 S)) = S dwdS / dt
         const double sq = sqrt(S);
-        const double om = 2.0 / dt * asin(dt * sq);
+        const double om = two_over_dt * asin(dt * sq);
         const double res = om - kn;
         const double root = sqrt(1.0 - dt * dt * S);
         const double dwdS = 1.0 / (sq * root);
         const double g = 2.0 * w * res;
         acc[0] += w * res * res;
-        const double gs = g * dwdS;
+        const double gs2 = 2.0 * g * dwdS;
+        const double tx = gs2 * s2[0], ty = gs2 * s2[1], tz = gs2 * s2[2];
+        const double cx1 = c[0] - 1.0, cy1 = c[1] - 1.0, cz1 = c[2] - 1.0;
         // beta: (x,y), (x,z), (y,x), (y,z), (z,x), (z,y)
-        acc[1] += gs * 2.0 * s2[0] * (c[1] - 1.0);
-        acc[2] += gs * 2.0 * s2[0] * (c[2] - 1.0);
-        acc[3] += gs * 2.0 * s2[1] * (c[0] - 1.0);
-        acc[4] += gs * 2.0 * s2[1] * (c[2] - 1.0);
-        acc[5] += gs * 2.0 * s2[2] * (c[0] - 1.0);
-        acc[6] += gs * 2.0 * s2[2] * (c[1] - 1.0);
-        acc[7] += gs * 2.0 * s2[0] * (c[0] - 1.0);
-        acc[8] += gs * 2.0 * s2[1] * (c[1] - 1.0);
-        acc[9] += gs * 2.0 * s2[2] * (c[2] - 1.0);
-        acc[10] += g * (-om / dt + 2.0 * sq / (dt * root));
+        acc[1] += tx * cy1;
+        acc[2] += tx * cz1;
+        acc[3] += ty * cx1;
+        acc[4] += ty * cz1;
+        acc[5] += tz * cx1;
+        acc[6] += tz * cy1;
+        acc[7] += tx * cx1;
+        acc[8] += ty * cy1;
+        acc[9] += tz * cz1;
+        acc[10] += g * inv_dt * (2.0 * S * dwdS - om);
     }
     __shared__ double red[NORM_THREADS / 32][NQ];
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
