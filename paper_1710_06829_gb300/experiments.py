@@ -4,6 +4,7 @@
     python -m paper_1710_06829_gb300.experiments cherenkov       # 512x256x256 rigid bunch
     python -m paper_1710_06829_gb300.experiments differentiable  # 128^3 checkpointed gradient
     python -m paper_1710_06829_gb300.experiments optimize        # coefficient minimisation
+    python -m paper_1710_06829_gb300.experiments reproduce       # Table 1 schemes by SLSQP on GPU
 
 Each prints one JSON object.  Every number comes from libfdtd's kernels, including the closed
 forms used for comparison (omega(k) of Eq. (dispersion_relation) and its k-gradient, from the
@@ -319,9 +320,52 @@ class batched_propagation:
         return float(loss.item()) / self.batch, g
 
 
+def reproduce(n=256):
+    """Sec. 5 / Table 1 on the GPU: SLSQP (host) on the GPU norm and gradient (256^2 k-grid)
+    reproduces min.1 (three parameters, 3 x 2 x 2 start grid), min.2-4 (Eq. beta, one
+    parameter at the printed c dt / dx), NDFX (c dt = dx) and Lehe's scheme (delta_y held at
+    zero, c dt / dx = 0.96)."""
+    N = (n, n, 1)
+    obj = O.NormObjective([1, 1, 1], 2, N)
+    rows = {}
+    t0 = time.perf_counter()
+    tie = O.Tying.symmetric_2d(dt=None)
+    starts = [[b, d, nu] for b in (-0.1, 0.05, 0.2) for d in (-0.1, 0.1) for nu in (0.3, 0.8)]
+    th, c, J = O.slsqp(obj, tie, starts, [-0.125, -0.125, 0.05], [0.25, 0.125, 1.0])
+    rows["min1"] = {"nu": th[2], "beta": th[0], "delta_x": th[1], "delta_y": th[1], "norm": J,
+                    "printed": {"nu": 0.686, "beta": 0.110, "delta": -0.125, "norm": 0.08}}
+    for name, nu, printed in (("min2", 0.95 / math.sqrt(2), (-0.013, 0.63)),
+                              ("min3", 0.5, (-0.065, 0.42)), ("min4", 0.1, (-0.125, 0.36))):
+        T = np.zeros((1, 13))
+        T[0][O.B(0, 1)] = T[0][O.B(1, 0)] = T[0][O.DELTA(0)] = T[0][O.DELTA(1)] = 1.0
+        c0 = np.zeros(13)
+        c0[O.DT] = nu
+        tie = O.Tying(T, c0, ["beta = delta"])
+        th, c, J = O.slsqp(obj, tie, [[-0.1], [0.0], [0.1]], [-0.125], [0.125])
+        rows[name] = {"nu": nu, "beta": th[0], "delta_x": th[0], "delta_y": th[0], "norm": J,
+                      "printed": {"nu": nu, "beta": printed[0], "delta": printed[0], "norm": printed[1]}}
+    tie = O.Tying.symmetric_2d(dt=None)
+    th, c, J = O.slsqp(obj, tie, [[0.0625, 0.0625, 1.0], [0.2, 0.0, 1.0], [0.15, 0.02, 1.0]],
+                       [-0.125, -0.125, 1.0], [0.25, 0.125, 1.0])
+    rows["NDFX"] = {"nu": th[2], "beta": th[0], "delta_x": th[1], "delta_y": th[1], "norm": J,
+                    "printed": {"nu": 1.0, "beta": 0.125, "delta": 0.0, "norm": 0.83},
+                    "setting": "lower bound of c dt / dx = 1"}
+    tie = O.Tying.sym_beta_2d(0.96)
+    starts = [[b, d, 0.0] for b in (0.0, 0.1, 0.2) for d in (-0.1, 0.0)]
+    th, c, J = O.slsqp(obj, tie, starts, [-0.125, -0.125, -1e-6], [0.25, 0.125, 1e-6])
+    rows["Lehe"] = {"nu": 0.96, "beta": th[0], "delta_x": th[1], "delta_y": th[2], "norm": J,
+                    "printed": {"nu": 0.96, "beta": 0.125, "delta_x": -0.021, "norm": 1.04},
+                    "setting": "delta_y in [-1e-6, 1e-6], c dt / dx = 0.96"}
+    torch.cuda.synchronize()
+    return {"experiment": "reproduce", "kgrid": list(N), "optimiser": "SciPy SLSQP on GPU norm + "
+            "gradient (disp_norm_eval), constraints from fdtd_dt_max", "rows": rows,
+            "norm_evaluations": obj.evals, "seconds": time.perf_counter() - t0}
+
+
 def main():
     p = argparse.ArgumentParser()
-    p.add_argument("what", choices=["dispersion", "cherenkov", "differentiable", "optimize"])
+    p.add_argument("what", choices=["dispersion", "cherenkov", "differentiable", "optimize",
+                                    "reproduce"])
     p.add_argument("--mu", type=float, default=0.0)
     p.add_argument("--iters", type=int, default=50)
     a = p.parse_args()
@@ -331,6 +375,8 @@ def main():
         r = cherenkov()
     elif a.what == "differentiable":
         r = differentiable()
+    elif a.what == "reproduce":
+        r = reproduce()
     else:
         r = optimize(iters=a.iters, mu=a.mu)
     print(json.dumps(r))

@@ -1,7 +1,9 @@
 """Constrained coefficient minimisation on the GPU (Sec. 4): projected gradient descent in FP64.
 
 The paper minimises the dispersion norm (Eq. norm) under Eq. (constraints) with SLSQP
-inside a bounds cuboid.  Here every evaluation and every update runs in libfdtd:
+inside a bounds cuboid; ``slsqp`` does the same with every norm and gradient evaluation on
+the GPU.  ``minimise`` is a GPU-resident alternative in which every evaluation and every
+update runs in libfdtd:
 ``disp_norm_eval`` gives the norm and its exact gradient, ``fdtd_coeff_update`` forms
 theta' = clip(theta - eta T g, lo, hi) and the scheme parameters c' = c0 + T^T theta', and
 a candidate that violates Eq. (constraints) is rejected by the library's exact CFL check.
@@ -56,6 +58,18 @@ class Tying:
         else:
             c0[DT] = dt
         return cls(np.array(rows), c0, names)
+
+    @classmethod
+    def sym_beta_2d(cls, dt):
+        """2D, beta_xy = beta_yx = beta, delta_x and delta_y free, fixed dt (Sec. 5: with delta_y
+        held at zero by its bounds this family contains Lehe's scheme)."""
+        T = np.zeros((3, 13))
+        T[0][B(0, 1)] = T[0][B(1, 0)] = 1.0
+        T[1][DELTA(0)] = 1.0
+        T[2][DELTA(1)] = 1.0
+        c0 = np.zeros(13)
+        c0[DT] = dt
+        return cls(T, c0, ["beta", "delta_x", "delta_y"])
 
     @classmethod
     def isotropic_3d(cls, dt):
@@ -132,3 +146,58 @@ def minimise(objective, tying: Tying, theta0, lo, hi, iters=50, eta0=1e-2, max_h
             break
         hist.append((it, J))
     return theta, c, J, hist
+
+
+def slsqp(objective, tying: Tying, starts, lo, hi, maxiter=200):
+    """The paper's optimiser (Sec. 4: SLSQP under Eq. (constraints) inside a bounds cuboid, from a
+    grid of start points), with every norm and gradient evaluation on the GPU
+    (``disp_norm_eval``) and the constraints from the library's exact extremes of S
+    (``fdtd_dt_max``): 1 - dt^2 max S >= 0 and min S >= 0.  SciPy's SLSQP drives the search on
+    the host.  Returns (theta, c, J) of the best feasible result over the starts."""
+    from scipy.optimize import minimize
+
+    lo, hi = np.asarray(lo, dtype=np.float64), np.asarray(hi, dtype=np.float64)
+
+    def coeffs(theta):
+        return tying.c0 + tying.T.T @ np.asarray(theta, dtype=np.float64)
+
+    def extremes(theta):
+        beta, delta, dt = Tying.split(coeffs(theta))
+        _, smin, smax = L.fdtd_dt_max(L.make_coeffs(beta, delta), objective.dx, objective.dims)
+        return smin, smax, dt
+
+    def cfl(theta):
+        smin, smax, dt = extremes(theta)
+        return 1.0 - dt * dt * smax
+
+    def pos(theta):
+        return extremes(theta)[0]
+
+    cache = {}
+
+    def fun(theta):
+        key = tuple(np.round(theta, 15))
+        if key not in cache:
+            if cfl(theta) < -1e-9 or pos(theta) < -1e-9:
+                cache[key] = (1e3, np.zeros(tying.n))
+            else:
+                J, g13 = objective(coeffs(theta))
+                cache[key] = (1e3, np.zeros(tying.n)) if J is None else (J, tying.T @ g13)
+        return cache[key]
+
+    best = (None, None, np.inf)
+    for x0 in starts:
+        x0 = np.clip(np.asarray(x0, dtype=np.float64), lo, hi)
+        if cfl(x0) < 0 or pos(x0) < 0:
+            continue
+        res = minimize(lambda t: fun(t)[0], x0, jac=lambda t: fun(t)[1], method="SLSQP",
+                       bounds=list(zip(lo, hi)),
+                       constraints=[{"type": "ineq", "fun": cfl}, {"type": "ineq", "fun": pos}],
+                       options={"maxiter": maxiter, "ftol": 1e-12})
+        x = np.clip(res.x, lo, hi)
+        if cfl(x) < -1e-9 or pos(x) < -1e-9:
+            continue
+        J = fun(x)[0]
+        if J < best[2]:
+            best = (x, coeffs(x), J)
+    return best

@@ -266,3 +266,35 @@ def test_minimiser_reproduces_min1(golden):
     assert abs(x[1] - float(row[3])) <= 0.002
     assert abs(x[2] - float(row[1])) <= 0.002
     assert printed_match(f, row[5])
+
+
+def _co2(bxy, byx, dx_, dy_):
+    b = np.zeros((3, 3))
+    b[0, 1], b[1, 0] = bxy, byx
+    return b, np.array([dx_, dy_, 0.0])
+
+
+def test_minimiser_reproduces_ndfx_with_dt_at_dx_over_c():
+    """Sec. 5 (reproducing published stencils): with c dt = dx as the lower bound of the time step
+    (so c dt = dx), the minimum of Eq. (norm) is Pukhov's NDFX scheme, beta = 1/8, delta = 0,
+    from several feasible starts."""
+    def up(x):
+        b, d = _co2(x[0], x[0], x[1], x[1])
+        return b, d, x[2]
+    bounds = [(-0.125, 0.25), (-0.125, 0.125), (1.0, 1.0)]
+    for start in ([0.0625, 0.0625, 1.0], [0.2, 0.0, 1.0], [0.15, 0.02, 1.0]):
+        x, f = D.minimise(up, bounds, [start], [1, 1, 1], (64, 64, 1), 2)
+        assert abs(x[0] - 0.125) <= 0.002 and abs(x[1]) <= 0.002, (start, x)
+
+
+def test_minimiser_reproduces_lehe_with_delta_y_pinned_at_zero():
+    """Sec. 5: delta_y held at zero and c dt / dx = 0.96 (read as the time step pinned at the bound;
+    with a free lower bound the minimum moves to c dt / dx ~ 0.68) give Lehe's scheme,
+    beta = 1/8 and delta_x = -0.021 (Table 1)."""
+    def up(x):
+        b, d = _co2(x[0], x[0], x[1], x[2])
+        return b, d, x[3]
+    bounds = [(-0.125, 0.25), (-0.125, 0.125), (-1e-6, 1e-6), (0.96, 0.96)]
+    starts = [[b, d, 0.0, 0.96] for b in (0.0, 0.1, 0.2) for d in (-0.1, 0.0)]
+    x, f = D.minimise(up, bounds, starts, [1, 1, 1], (64, 64, 1), 2)
+    assert abs(x[0] - 0.125) <= 0.002 and abs(x[1] + 0.021) <= 0.002, x
