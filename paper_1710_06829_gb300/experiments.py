@@ -356,6 +356,36 @@ def reproduce(n=256):
     rows["Lehe"] = {"nu": 0.96, "beta": th[0], "delta_x": th[1], "delta_y": th[2], "norm": J,
                     "printed": {"nu": 0.96, "beta": 0.125, "delta_x": -0.021, "norm": 1.04},
                     "setting": "delta_y in [-1e-6, 1e-6], c dt / dx = 0.96"}
+    # Table 2: the x-axis weight exp(-(k_y dy / 0.1)^2); the printed min.5 / min.6 coefficients
+    # are compared with the minimum by their weighted norms (the minimum is shallow)
+    objw = O.NormObjective([1, 1, 1], 2, N, L.FDTD_W_GAUSS_Y, 0.1)
+    for name, nu, printed in (("min5", 0.96, (0.133, -0.017, -0.019, 0.002)),
+                              ("min6", 0.999, (0.128, -0.0005, 0.0, 6.2e-7))):
+        tie = O.Tying.sym_beta_2d(nu)
+        starts = [[b, dx_, dy_] for b in (0.1, 0.13) for dx_ in (-0.02, 0.0) for dy_ in (-0.02, 0.0)]
+        th, c, J = O.slsqp(objw, tie, starts, [-0.125, -0.125, -0.125], [0.25, 0.125, 0.125])
+        Jp = objw(tie.c0 + tie.T.T @ np.array(printed[:3]))[0]
+        Jl = objw(O.Tying.sym_beta_2d(0.96).c0 + O.Tying.sym_beta_2d(0.96).T.T @
+                  np.array([0.125, -0.021, 0.0]))[0]
+        rows[name] = {"nu": nu, "beta": th[0], "delta_x": th[1], "delta_y": th[2],
+                      "weighted_norm": J, "weighted_norm_of_printed_coefficients": Jp,
+                      "weighted_norm_lehe_0.96": Jl,
+                      "printed": {"beta": printed[0], "delta_x": printed[1], "delta_y": printed[2],
+                                  "norm": printed[3]}}
+    # Fig. 3: dy = 10 dx (units where the larger step is 1): Yee at 0.95 of its limit vs the
+    # minimum over all five parameters
+    dxa = [0.1, 1.0, 1.0]
+    obja = O.NormObjective(dxa, 2, N)
+    yee_dt = 0.95 * L.fdtd_dt_max(L.make_coeffs(np.zeros((3, 3)), np.zeros(3)), dxa, 2)[0]
+    J_yee = obja(np.r_[np.zeros(12), yee_dt])[0]
+    tie = O.Tying.general_2d()
+    starts = [[bxy, byx, dxx, 0.0, f * yee_dt] for bxy in (0.0, 0.1) for byx in (0.0, 0.1)
+              for dxx in (-0.1, 0.0) for f in (0.5, 0.9)]
+    th, c, J = O.slsqp(obja, tie, starts, [-0.125, -0.125, -0.125, -0.125, 0.001],
+                       [0.25, 0.25, 0.125, 0.125, 0.2])
+    rows["fig3_aspect10"] = {"dx": dxa[:2], "yee_norm_at_0.95": J_yee, "printed_yee": 20.7,
+                             "minimum": {"beta_xy": th[0], "beta_yx": th[1], "delta_x": th[2],
+                                         "delta_y": th[3], "dt": th[4], "norm": J}}
     torch.cuda.synchronize()
     return {"experiment": "reproduce", "kgrid": list(N), "optimiser": "SciPy SLSQP on GPU norm + "
             "gradient (disp_norm_eval), constraints from fdtd_dt_max", "rows": rows,

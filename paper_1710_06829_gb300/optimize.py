@@ -72,6 +72,17 @@ class Tying:
         return cls(T, c0, ["beta", "delta_x", "delta_y"])
 
     @classmethod
+    def general_2d(cls):
+        """2D, theta = (beta_xy, beta_yx, delta_x, delta_y, dt), all free (unequal steps)."""
+        T = np.zeros((5, 13))
+        T[0][B(0, 1)] = 1.0
+        T[1][B(1, 0)] = 1.0
+        T[2][DELTA(0)] = 1.0
+        T[3][DELTA(1)] = 1.0
+        T[4][DT] = 1.0
+        return cls(T, np.zeros(13), ["beta_xy", "beta_yx", "delta_x", "delta_y", "dt"])
+
+    @classmethod
     def isotropic_3d(cls, dt):
         """3D theta = (delta_x, delta_perp, beta_x, beta_perp) at fixed dt."""
         T = np.zeros((4, 13))
