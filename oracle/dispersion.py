@@ -339,6 +339,100 @@ def group_velocity(kvec, beta, delta, dt, dx, dims=3, h=1e-6):
 
 
 # ----------------------------------------------------------------------------
+# group-velocity norm (a reading of the conclusions: "minimization of the numerical
+# group velocity error"); not printed in the paper, so its values are pinned by closed
+# forms, central differences and brute force only
+# ----------------------------------------------------------------------------
+
+
+def group_speed_terms(KX, KY, KZ, beta, delta, dt, dx, dims=3):
+    """Per point: S, grad_k S (3 arrays) and |v_g| = |d omega/dk| = omega'(S) |grad_k S|,
+    omega'(S) = 1 / (sqrt(S) sqrt(1 - dt^2 S)).  With alpha eliminated by Eq. (alpha),
+    A_i = 1 + 2 sum_{j != i} beta_ij (c_j - 1) + 2 delta_i (c_i - 1), S = sum_i s_i^2 A_i, and
+      dS/dk_m = sin(k_m dx_m) / (2 dx_m) A_m
+                - 2 dx_m sin(k_m dx_m) (delta_m s_m^2 + sum_{i != m} beta_im s_i^2)."""
+    b, d = clean_coeffs(beta, delta, dims)
+    dxa = np.asarray(dx, dtype=np.float64)
+    K = [KX, KY, KZ]
+    s2 = [s_sq(K[i], dxa[i]) for i in range(3)]
+    c = [np.cos(K[i] * dxa[i]) for i in range(3)]
+    sn = [np.sin(K[i] * dxa[i]) for i in range(3)]
+    A = []
+    for i in range(3):
+        a = 1.0 + 2.0 * d[i] * (c[i] - 1.0)
+        for j in range(3):
+            if j != i:
+                a = a + 2.0 * b[i, j] * (c[j] - 1.0)
+        A.append(a)
+    S = sum(s2[i] * A[i] for i in range(dims))
+    G = []
+    for m in range(3):
+        if m >= dims:
+            G.append(np.zeros_like(S))
+            continue
+        t = d[m] * s2[m]
+        for i in range(dims):
+            if i != m:
+                t = t + b[i, m] * s2[i]
+        G.append(sn[m] / (2.0 * dxa[m]) * A[m] - 2.0 * dxa[m] * sn[m] * t)
+    wS = 1.0 / (np.sqrt(S) * np.sqrt(1.0 - dt * dt * S))
+    Gn = np.sqrt(G[0] ** 2 + G[1] ** 2 + G[2] ** 2)
+    return dict(S=S, G=G, Gn=Gn, wS=wS, vg=wS * Gn, s2=s2, c=c, sn=sn, A=A)
+
+
+def group_norm_and_grad(beta, delta, dt, dx, N, dims=3, wkind=WEIGHT_UNIFORM, wparam=0.0):
+    """f_g = prod(dx) sum w (|v_g| - 1)^2 * cell volume on the midpoint grid of Eq. (norm), and
+    its gradient.  Chain rule: with r = |v_g| - 1,
+      d|v_g|/d theta = omega''(S) dS/dtheta |G| + omega'(S) (G . dG/dtheta) / |G|,
+      omega''(S) = -omega'(S)^3 (1 - 2 dt^2 S) / 2,   d omega'(S)/d dt = omega'(S)^3 dt S^2,
+      dS/d beta_ij = 2 s_i^2 (c_j - 1),  dS/d delta_i = 2 s_i^2 (c_i - 1),
+      dG_m/d beta_ij = [m = i] sin(k_i dx_i)(c_j - 1)/dx_i - [m = j] 2 dx_j sin(k_j dx_j) s_i^2,
+      dG_m/d delta_i = [m = i] (sin(k_i dx_i)(c_i - 1)/dx_i - 2 dx_i sin(k_i dx_i) s_i^2).
+    Returns (f, g_beta[3,3], g_delta[3], g_dt)."""
+    dxa = np.asarray(dx, dtype=np.float64)
+    KX, KY, KZ, vol = midpoint_grid(N, dxa, dims)
+    t = group_speed_terms(KX, KY, KZ, beta, delta, dt, dxa, dims)
+    S, G, Gn, wS, vg = t["S"], t["G"], t["Gn"], t["wS"], t["vg"]
+    s2, c, sn = t["s2"], t["c"], t["sn"]
+    wt = weight(KX, KY, KZ, wkind, wparam, dxa)
+    pref = float(np.prod(dxa[:dims]) * vol)
+    r = vg - 1.0
+    f = pref * float(np.sum(wt * r * r))
+    wSS = -0.5 * wS ** 3 * (1.0 - 2.0 * dt * dt * S)
+    common = 2.0 * wt * r
+    gb = np.zeros((3, 3))
+    gd = np.zeros(3)
+    for i in range(dims):
+        for j in range(dims):
+            if i == j:
+                continue
+            dS = 2.0 * s2[i] * (c[j] - 1.0)
+            GdG = G[i] * sn[i] * (c[j] - 1.0) / dxa[i] - G[j] * 2.0 * dxa[j] * sn[j] * s2[i]
+            dv = wSS * dS * Gn + wS * GdG / Gn
+            gb[i, j] = pref * float(np.sum(common * dv))
+        dS = 2.0 * s2[i] * (c[i] - 1.0)
+        GdG = G[i] * (sn[i] * (c[i] - 1.0) / dxa[i] - 2.0 * dxa[i] * sn[i] * s2[i])
+        dv = wSS * dS * Gn + wS * GdG / Gn
+        gd[i] = pref * float(np.sum(common * dv))
+    gdt = pref * float(np.sum(common * wS ** 3 * dt * S * S * Gn))
+    return f, gb, gd, gdt
+
+
+def group_norm_fd(beta, delta, dt, dx, N, dims=3, wkind=WEIGHT_UNIFORM, wparam=0.0, h=1e-6):
+    """The same sum with |v_g| from central differences of omega(k) (group_velocity), written
+    as explicit loops over the points (small N only)."""
+    dxa = np.asarray(dx, dtype=np.float64)
+    KX, KY, KZ, vol = midpoint_grid(N, dxa, dims)
+    wt = weight(KX, KY, KZ, wkind, wparam, dxa)
+    total = 0.0
+    for idx in np.ndindex(KX.shape):
+        k = np.array([KX[idx], KY[idx], KZ[idx]])
+        v = np.linalg.norm(group_velocity(k, beta, delta, dt, dxa, dims, h))
+        total += wt[idx] * (v - 1.0) ** 2
+    return float(np.prod(dxa[:dims]) * vol * total)
+
+
+# ----------------------------------------------------------------------------
 # constrained minimisation (Sec. 4): SLSQP, bounds cuboid, multistart grid
 # ----------------------------------------------------------------------------
 

@@ -298,3 +298,91 @@ def test_minimiser_reproduces_lehe_with_delta_y_pinned_at_zero():
     starts = [[b, d, 0.0, 0.96] for b in (0.0, 0.1, 0.2) for d in (-0.1, 0.0)]
     x, f = D.minimise(up, bounds, starts, [1, 1, 1], (64, 64, 1), 2)
     assert abs(x[0] - 0.125) <= 0.002 and abs(x[1] + 0.021) <= 0.002, x
+
+
+# ---------------------------------------------------------------- group-velocity norm
+
+def _rand_set(seed, dims=3):
+    rng = np.random.default_rng(seed)
+    b = np.zeros((3, 3))
+    for i in range(3):
+        for j in range(3):
+            if i != j:
+                b[i, j] = rng.uniform(-0.06, 0.06)
+    d = rng.uniform(-0.08, 0.0, 3)
+    return b, d
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_group_speed_matches_central_differences(seed):
+    """|d omega/dk| from the analytic grad_k S equals central differences of omega(k)."""
+    b, d = _rand_set(seed)
+    dx = [1.0, 1.1, 0.9]
+    dt = 0.8 * D.dt_max(b, d, dx, 3)
+    rng = np.random.default_rng(seed + 10)
+    for _ in range(5):
+        k = rng.uniform(0.05, 2.6, 3)
+        t = D.group_speed_terms(*(np.array(v) for v in k), b, d, dt, dx, 3)
+        assert float(t["vg"]) == pytest.approx(np.linalg.norm(D.group_velocity(k, b, d, dt, dx, 3)),
+                                               rel=1e-8)
+
+
+def test_group_norm_vanishes_for_1d_yee_at_courant_one():
+    """1D Yee with c dt = dx propagates every wavenumber at exactly c: v_g = 1, f_g = 0."""
+    b, d = np.zeros((3, 3)), np.zeros(3)
+    f, gb, gd, gdt = D.group_norm_and_grad(b, d, 1.0, [1.0, 1.0, 1.0], (256, 1, 1), 1)
+    assert f < 1e-24
+
+
+def test_group_norm_yee_2d_closed_form():
+    """Yee in 2D: |v_g|^2 = (sin^2(kx dx)/(4 dx^2) + sin^2(ky dy)/(4 dy^2)) / (S (1 - dt^2 S)),
+    S = sin^2(kx dx/2)/dx^2 + sin^2(ky dy/2)/dy^2, summed here independently."""
+    dx = [1.0, 0.7, 1.0]
+    dt = 0.9 / math.sqrt(1 / dx[0] ** 2 + 1 / dx[1] ** 2)
+    N = (40, 30, 1)
+    tot = 0.0
+    for my in range(N[1]):
+        for mx in range(N[0]):
+            kx = (mx + 0.5) * math.pi / (N[0] * dx[0])
+            ky = (my + 0.5) * math.pi / (N[1] * dx[1])
+            S = math.sin(kx * dx[0] / 2) ** 2 / dx[0] ** 2 + math.sin(ky * dx[1] / 2) ** 2 / dx[1] ** 2
+            g2 = math.sin(kx * dx[0]) ** 2 / (4 * dx[0] ** 2) + math.sin(ky * dx[1]) ** 2 / (4 * dx[1] ** 2)
+            tot += (math.sqrt(g2 / (S * (1 - dt * dt * S))) - 1.0) ** 2
+    ref = tot * (math.pi / N[0]) * (math.pi / N[1])
+    f, *_ = D.group_norm_and_grad(np.zeros((3, 3)), np.zeros(3), dt, dx, N, 2)
+    assert f == pytest.approx(ref, rel=1e-12)
+
+
+def test_group_norm_matches_difference_quotient_loops():
+    b, d = _rand_set(3)
+    dx = [1.0, 1.1, 0.9]
+    dt = 0.8 * D.dt_max(b, d, dx, 3)
+    f, *_ = D.group_norm_and_grad(b, d, dt, dx, (6, 5, 4), 3)
+    assert f == pytest.approx(D.group_norm_fd(b, d, dt, dx, (6, 5, 4), 3), rel=1e-7)
+
+
+@pytest.mark.parametrize("dims,wkind,wparam", [(3, D.WEIGHT_UNIFORM, 0.0), (2, D.WEIGHT_CONE_X, 0.6),
+                                               (2, D.WEIGHT_GAUSS_Y, 0.3)])
+def test_group_norm_gradient_vs_central_differences(dims, wkind, wparam):
+    b, d = _rand_set(4)
+    b, d = D.clean_coeffs(b, d, dims)
+    dx = [1.0, 1.1, 0.9]
+    dt = 0.8 * D.dt_max(b, d, dx, dims)
+    N = (12, 10, 8)
+    f, gb, gd, gdt = D.group_norm_and_grad(b, d, dt, dx, N, dims, wkind, wparam)
+    h = 1e-6
+
+    def F(bb, dd, tt):
+        return D.group_norm_and_grad(bb, dd, tt, dx, N, dims, wkind, wparam)[0]
+    for i in range(dims):
+        for j in range(dims):
+            if i != j:
+                bp, bm = b.copy(), b.copy()
+                bp[i, j] += h
+                bm[i, j] -= h
+                assert gb[i, j] == pytest.approx((F(bp, d, dt) - F(bm, d, dt)) / (2 * h), rel=1e-6, abs=1e-9)
+        dp, dm = d.copy(), d.copy()
+        dp[i] += h
+        dm[i] -= h
+        assert gd[i] == pytest.approx((F(b, dp, dt) - F(b, dm, dt)) / (2 * h), rel=1e-6, abs=1e-9)
+    assert gdt == pytest.approx((F(b, d, dt + h) - F(b, d, dt - h)) / (2 * h), rel=1e-6, abs=1e-9)
