@@ -218,6 +218,18 @@ int disp_norm_eval(const fdtd_coeffs* coeffs, double dt, const double dx[3], int
                    const int32_t N[3], int32_t weight, double weight_param, double* out,
                    void* stream);
 
+/* Group-velocity norm: the conclusions (Sec. 7) propose minimising the numerical group velocity
+ * error but give no formula; this library's reading uses the grid, weights and quadrature of
+ * Eq. (norm) with |d omega/dk| - c in place of omega - c|k|:
+ *     f_g = prod(dx) sum_points w (|grad_k omega| - 1)^2 prod(pi / (N_i dx_i)),
+ * grad_k omega = omega'(S) grad_k S from Eq. (dispersion_relation) (c = 1).
+ * Arguments, weights, limits, errors and synchronisation as disp_norm_eval; out (host, 14
+ * doubles) in the same layout: [0] f_g, [1..9] d/d beta, [10..12] d/d delta, [13] d/d dt.
+ * Allocates its scratch on `stream` (stream-ordered) and frees it before returning. */
+int disp_group_norm_eval(const fdtd_coeffs* coeffs, double dt, const double dx[3], int32_t dims,
+                         const int32_t N[3], int32_t weight, double weight_param, double* out,
+                         void* stream);
+
 /* omega(k) of Eq. (dispersion_relation), omega = (2/dt) asin(dt sqrt(sum_i s_i^2 A_i)), at n
  * wave vectors (k_dev: device, n x 3 doubles, row-major; axes beyond dims ignored) into
  * omega_dev (device, n doubles).  FP64.  Validates Eq. (constraints) like disp_norm_eval.

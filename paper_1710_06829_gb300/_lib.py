@@ -47,7 +47,7 @@ EXPORTS = ["fdtd_create", "fdtd_set_coeffs", "fdtd_set_state", "fdtd_get_state",
            "fdtd_step", "fdtd_checkpoint", "fdtd_set_adjoint", "fdtd_get_adjoint",
            "fdtd_step_adjoint", "fdtd_diagnostic", "fdtd_divergence", "fdtd_selftest_wait_expiry",
            "fdtd_sync", "fdtd_destroy", "disp_norm_eval",
-           "disp_norm_eval_noalloc", "disp_omega_eval", "fdtd_coeff_update", "fdtd_dt_max", "fdtd_last_error"]
+           "disp_norm_eval_noalloc", "disp_group_norm_eval", "disp_omega_eval", "fdtd_coeff_update", "fdtd_dt_max", "fdtd_last_error"]
 
 
 class FdtdError(RuntimeError):
@@ -113,6 +113,7 @@ def load():
     lib.disp_norm_eval.argtypes = [C.POINTER(fdtd_coeffs), D, pd, I32, C.POINTER(I32), I32, D,
                                    pd, P]
     lib.disp_norm_eval_noalloc.argtypes = lib.disp_norm_eval.argtypes
+    lib.disp_group_norm_eval.argtypes = lib.disp_norm_eval.argtypes
     lib.disp_omega_eval.argtypes = [C.POINTER(fdtd_coeffs), D, pd, I32, P, I32, P, P]
     lib.fdtd_coeff_update.argtypes = [I32, pd, pd, pd, pd, D, pd, pd, P, P]
     lib.fdtd_dt_max.argtypes = [C.POINTER(fdtd_coeffs), pd, I32, pd, pd, pd]
@@ -227,6 +228,14 @@ def disp_norm_eval(coeffs, dt, dx, dims, N, weight=FDTD_W_UNIFORM, weight_param=
     n3 = (C.c_int32 * 3)(*[int(v) for v in N])
     check(load().disp_norm_eval(C.byref(coeffs), float(dt), _d3(dx), int(dims), n3, int(weight),
                                 float(weight_param), out, C.c_void_p(stream)))
+    return list(out)
+
+
+def disp_group_norm_eval(coeffs, dt, dx, dims, N, weight=FDTD_W_UNIFORM, weight_param=0.0, stream=0):
+    out = (C.c_double * 14)()
+    n3 = (C.c_int32 * 3)(*[int(v) for v in N])
+    check(load().disp_group_norm_eval(C.byref(coeffs), float(dt), _d3(dx), int(dims), n3,
+                                      int(weight), float(weight_param), out, C.c_void_p(stream)))
     return list(out)
 
 

@@ -244,3 +244,182 @@ void launch_omega(const double alpha[3], const double beta[3][3], const double d
 }
 
 }  // namespace fdtd
+
+namespace fdtd {
+
+// ---- group-velocity norm (the conclusions' proposal; this library's reading) ----------------
+// f_g = prefactor * sum w (|d omega/dk| - 1)^2 on the same midpoint grid, with
+//   A_i = alpha_i + delta_i (1 + 2 c_i) + 2 sum_{j != i} beta_ij c_j       (as in norm_kernel)
+//   G_m = dS/dk_m = sin(k_m dx_m)/(2 dx_m) A_m - 2 dx_m sin(k_m dx_m) (delta_m s_m^2
+//                                                    + sum_{i != m} beta_im s_i^2)
+//   |v_g| = w_S |G|,  w_S = 1 / (sqrt(S) sqrt(1 - dt^2 S)),
+// and the gradient by the chain rule (w_SS = -w_S^3 (1 - 2 dt^2 S) / 2, d w_S/d dt = w_S^3 dt S^2):
+//   d|v_g| = w_SS dS |G| + w_S (G . dG) / |G|, with dS/d beta_ij = 2 s_i^2 (c_j - 1),
+//   dS/d delta_i = 2 s_i^2 (c_i - 1), dG_m/d beta_ij = [m=i] sin_i (c_j - 1)/dx_i
+//   - [m=j] 2 dx_j sin_j s_i^2, dG_m/d delta_i = [m=i] (sin_i (c_i - 1)/dx_i - 2 dx_i sin_i s_i^2).
+// FP64 throughout; per-block partials and the fixed-order final sum of norm_kernel.
+
+struct GroupParams {
+    NormParams n;
+    double dx[3];
+};
+
+__global__ void group_table_kernel(GroupParams p, double* __restrict__ tab) {
+    // tab layout: for axis a: [k], [s2], [c], [sin(k dx)] of N_a entries each
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    int off = 0;
+    for (int a = 0; a < 3; ++a) {
+        const int n = p.n.N[a];
+        if (t < n) {
+            double k = 0.0;
+            if (a < p.n.dims) k = (t + 0.5) * M_PI / (n * p.dx[a]);
+            const double sn = sin(0.5 * k * p.dx[a]) / p.dx[a];
+            tab[off + t] = k;
+            tab[off + n + t] = sn * sn;
+            tab[off + 2 * n + t] = cos(k * p.dx[a]);
+            tab[off + 3 * n + t] = sin(k * p.dx[a]);
+        }
+        off += 4 * n;
+    }
+}
+
+__global__ void __launch_bounds__(NORM_THREADS)
+group_norm_kernel(GroupParams gp, const double* __restrict__ tab, double* __restrict__ partials) {
+    const NormParams& p = gp.n;
+    double acc[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) acc[q] = 0.0;
+    const double* T[3];
+    {
+        int off = 0;
+        for (int a = 0; a < 3; ++a) {
+            T[a] = tab + off;
+            off += 4 * p.N[a];
+        }
+    }
+    const double dt = p.dt;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < p.npts;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int mi[3] = {(int)(t % p.N[0]), (int)((t / p.N[0]) % p.N[1]),
+                           (int)(t / ((long long)p.N[0] * p.N[1]))};
+        double k[3], s2[3], c[3], sn[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const int n = p.N[a];
+            k[a] = T[a][mi[a]];
+            s2[a] = T[a][n + mi[a]];
+            c[a] = T[a][2 * n + mi[a]];
+            sn[a] = T[a][3 * n + mi[a]];
+        }
+        double A[3], S = 0.0;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            double a = p.alpha[i] + p.delta[i] * (1.0 + 2.0 * c[i]);
+#pragma unroll
+            for (int j = 0; j < 3; ++j)
+                if (j != i) a += 2.0 * p.beta[i][j] * c[j];
+            A[i] = a;
+            S += s2[i] * a;
+        }
+        const double kn = sqrt(k[0] * k[0] + k[1] * k[1] + k[2] * k[2]);
+        double w = 1.0;
+        if (p.weight == FDTD_W_CONE_X) {
+            w = (k[0] >= kn * p.wparam) ? 1.0 : 0.0;
+        } else if (p.weight == FDTD_W_GAUSS_Y) {
+            const double u = k[1] * p.wparam;
+            w = exp(-u * u);
+        }
+        if (w == 0.0) continue;
+        double G[3];
+#pragma unroll
+        for (int m = 0; m < 3; ++m) {
+            double tm = p.delta[m] * s2[m];
+#pragma unroll
+            for (int i = 0; i < 3; ++i)
+                if (i != m) tm += p.beta[i][m] * s2[i];
+            G[m] = sn[m] / (2.0 * gp.dx[m]) * A[m] - 2.0 * gp.dx[m] * sn[m] * tm;
+        }
+        const double Gn = sqrt(G[0] * G[0] + G[1] * G[1] + G[2] * G[2]);
+        const double wS = 1.0 / (sqrt(S) * sqrt(1.0 - dt * dt * S));
+        const double vg = wS * Gn;
+        const double r = vg - 1.0;
+        acc[0] += w * r * r;
+        const double cm = 2.0 * w * r;
+        const double wS3 = wS * wS * wS;
+        const double wSS = -0.5 * wS3 * (1.0 - 2.0 * dt * dt * S);
+        const double a1 = cm * wSS * Gn;   // times dS/dtheta
+        const double a2 = cm * wS / Gn;    // times G . dG/dtheta
+        // beta: (x,y), (x,z), (y,x), (y,z), (z,x), (z,y)  (same slots as norm_kernel)
+        const int bi[6] = {0, 0, 1, 1, 2, 2}, bj[6] = {1, 2, 0, 2, 0, 1};
+#pragma unroll
+        for (int q = 0; q < 6; ++q) {
+            const int i = bi[q], j = bj[q];
+            const double dS = 2.0 * s2[i] * (c[j] - 1.0);
+            const double GdG = G[i] * sn[i] * (c[j] - 1.0) / gp.dx[i] -
+                               G[j] * 2.0 * gp.dx[j] * sn[j] * s2[i];
+            acc[1 + q] += a1 * dS + a2 * GdG;
+        }
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            const double dS = 2.0 * s2[i] * (c[i] - 1.0);
+            const double GdG = G[i] * (sn[i] * (c[i] - 1.0) / gp.dx[i] - 2.0 * gp.dx[i] * sn[i] * s2[i]);
+            acc[7 + i] += a1 * dS + a2 * GdG;
+        }
+        acc[10] += cm * wS3 * dt * S * S * Gn;
+    }
+    __shared__ double red[NORM_THREADS / 32][NQ];
+    const int wq = threadIdx.x >> 5, l = threadIdx.x & 31;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        double v = acc[q];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (l == 0) red[wq][q] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < NQ) {
+        double v = 0.0;
+        for (int ww = 0; ww < NORM_THREADS / 32; ++ww) v += red[ww][threadIdx.x];
+        partials[(long long)blockIdx.x * NQ + threadIdx.x] = v;
+    }
+}
+
+size_t group_scratch_doubles(const int N[3], long long npts) {
+    return (size_t)4 * (N[0] + N[1] + N[2]) + (size_t)norm_blocks(npts) * NQ + 14;
+}
+
+void launch_disp_group_norm(const double alpha[3], const double beta[3][3], const double delta[3],
+                            double dt, const double dx[3], int dims, const int N[3], int weight,
+                            double wparam, double* scratch, double** out_dev, cudaStream_t st) {
+    GroupParams gp;
+    NormParams& p = gp.n;
+    for (int i = 0; i < 3; ++i) {
+        p.alpha[i] = alpha[i];
+        p.delta[i] = delta[i];
+        for (int j = 0; j < 3; ++j) p.beta[i][j] = beta[i][j];
+        p.N[i] = i < dims ? N[i] : 1;
+        gp.dx[i] = dx[i];
+    }
+    p.dt = dt;
+    p.dims = dims;
+    p.weight = weight;
+    if (weight == FDTD_W_CONE_X) p.wparam = cos(wparam);
+    else if (weight == FDTD_W_GAUSS_Y) p.wparam = dx[1] / wparam;
+    else p.wparam = 0.0;
+    p.npts = (long long)p.N[0] * p.N[1] * p.N[2];
+    double pref = 1.0;
+    for (int i = 0; i < dims; ++i) pref *= dx[i] * (M_PI / (p.N[i] * dx[i]));
+    p.pref = pref;
+    double* tab = scratch;
+    const size_t ntab = (size_t)4 * (p.N[0] + p.N[1] + p.N[2]);
+    double* part = scratch + ntab;
+    const int nb = norm_blocks(p.npts);
+    double* out = part + (size_t)nb * NQ;
+    int nmax = p.N[0] > p.N[1] ? p.N[0] : p.N[1];
+    if (p.N[2] > nmax) nmax = p.N[2];
+    group_table_kernel<<<(nmax + 255) / 256, 256, 0, st>>>(gp, tab);
+    group_norm_kernel<<<nb, NORM_THREADS, 0, st>>>(gp, tab, part);
+    norm_final_kernel<<<1, dim3(32, NQ), 0, st>>>(part, nb, pref, out);
+    *out_dev = out;
+}
+
+}  // namespace fdtd

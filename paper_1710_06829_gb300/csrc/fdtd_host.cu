@@ -34,6 +34,10 @@ void launch_bunch_table(int nx, int n, double x0, double vdt, double inv_sig, do
 void launch_disp_norm(const double alpha[3], const double beta[3][3], const double delta[3],
                       double dt, const double dx[3], int dims, const int N[3], int weight,
                       double wparam, double* scratch, double** out_dev, cudaStream_t st);
+size_t group_scratch_doubles(const int N[3], long long npts);
+void launch_disp_group_norm(const double alpha[3], const double beta[3][3], const double delta[3],
+                            double dt, const double dx[3], int dims, const int N[3], int weight,
+                            double wparam, double* scratch, double** out_dev, cudaStream_t st);
 size_t norm_scratch_doubles(const int N[3], long long npts);
 int diag_blocks(const Geom& g);
 void launch_omega(const double alpha[3], const double beta[3][3], const double delta[3], double dt,
@@ -1044,6 +1048,47 @@ int disp_norm_eval(const fdtd_coeffs* coeffs, double dt, const double dx[3], int
     return FDTD_OK;
 }
 
+
+int disp_group_norm_eval(const fdtd_coeffs* coeffs, double dt, const double dx[3], int32_t dims,
+                         const int32_t N[3], int32_t weight, double weight_param, double* out,
+                         void* stream) {
+    if (!coeffs || !dx || !N || !out || dims < 1 || dims > 3) {
+        set_error("disp_group_norm_eval: bad argument");
+        return FDTD_EINVAL;
+    }
+    for (int i = 0; i < dims; ++i)
+        if (N[i] < 1 || !(dx[i] > 0)) { set_error("disp_group_norm_eval: bad grid"); return FDTD_EINVAL; }
+    if (weight != FDTD_W_UNIFORM && weight != FDTD_W_CONE_X && weight != FDTD_W_GAUSS_Y) {
+        set_error("unknown weight %d", weight);
+        return FDTD_EINVAL;
+    }
+    if (weight == FDTD_W_GAUSS_Y && !(weight_param > 0)) { set_error("gauss width must be > 0"); return FDTD_EINVAL; }
+    Clean cc = clean_coeffs(coeffs, dims);
+    int rc = validate(cc, dx, dims, dt);
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    int Nd[3];
+    long long npts = 1;
+    for (int i = 0; i < 3; ++i) {
+        Nd[i] = i < dims ? N[i] : 1;
+        npts *= Nd[i];
+    }
+    const size_t nscr = group_scratch_doubles(Nd, npts);
+    double* scratch = nullptr;
+    CK(cudaMallocAsync((void**)&scratch, nscr * sizeof(double), st));
+    double* res = nullptr;
+    launch_disp_group_norm(cc.alpha, cc.beta, cc.delta, dt, dx, dims, Nd, weight, weight_param,
+                           scratch, &res, st);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, res, 14 * sizeof(double), cudaMemcpyDeviceToHost, st);
+    cudaFreeAsync(scratch, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        set_error("disp_group_norm_eval: %s", cudaGetErrorString(e));
+        return FDTD_ECUDA;
+    }
+    return FDTD_OK;
+}
 
 int disp_omega_eval(const fdtd_coeffs* coeffs, double dt, const double dx[3], int32_t dims,
                     const double* k_dev, int32_t n, double* omega_dev, void* stream) {

@@ -195,6 +195,17 @@ def disp_norm(beta, delta, dt, dx, dims, N, weight=L.FDTD_W_UNIFORM, weight_para
     return out[0], gb, out[10:13], out[13]
 
 
+def group_norm(beta, delta, dt, dx, dims, N, weight=L.FDTD_W_UNIFORM, weight_param=0.0,
+               stream=None):
+    """Group-velocity norm (|d omega/dk| - c)^2 on the norm's grid, and its gradient, on the GPU.
+
+    Returns (f_g, g_beta 3x3 (list of lists), g_delta (3), g_dt)."""
+    out = L.disp_group_norm_eval(coeffs_struct(beta, delta), dt, dx, dims, N, weight, weight_param,
+                                 _stream_ptr(stream))
+    gb = [out[1:4], out[4:7], out[7:10]]
+    return out[0], gb, out[10:13], out[13]
+
+
 def omega(beta, delta, dt, dx, dims, k, stream=None):
     """omega(k) of the scheme (Eq. dispersion_relation) on the GPU for an (n, 3) array of k."""
     kt = torch.as_tensor(np.asarray(k, dtype=np.float64).reshape(-1, 3)).cuda().contiguous()

@@ -86,3 +86,41 @@ def test_omega_eval_matches_oracle_and_table3(golden):
         w = S.omega(be, de, float(nu), [1, 1, 1], 2, K)
         v = w / np.linalg.norm(K, axis=1)
         assert abs(v.min() - float(vmin)) <= 0.015 and abs(v.max() - float(vmax)) <= 0.015, name
+
+
+@pytest.mark.parametrize("dims,N", [(2, (64, 48, 1)), (3, (24, 20, 17)), (1, (100, 1, 1))])
+@pytest.mark.parametrize("w", ["uniform", "cone", "gauss"])
+def test_group_norm_and_gradient_match_oracle(dims, N, w):
+    okind, gkind, par = WK[w]
+    beta, delta = inputs.random_theta(9, dims)
+    smin, _ = D.S_extremes(beta, delta, [1, 1, 1], dims)
+    if smin < 0:
+        beta, delta = beta * 0.3, delta * 0.3
+    dx = [1.0, 1.2, 0.9]
+    dt = 0.9 * D.dt_max(beta, delta, dx, dims)
+    f, gb, gd, gdt = S.group_norm(beta, delta, dt, dx, dims, N, gkind, par)
+    rf, rgb, rgd, rgdt = D.group_norm_and_grad(beta, delta, dt, dx, N, dims, okind, par)
+    assert f == pytest.approx(rf, rel=1e-11, abs=1e-300)
+    scale = max(1.0, abs(rf))
+    assert np.allclose(np.array(gb), rgb, rtol=1e-10, atol=1e-12 * scale)
+    assert np.allclose(gd, rgd, rtol=1e-10, atol=1e-12 * scale)
+    assert gdt == pytest.approx(rgdt, rel=1e-10, abs=1e-12 * scale)
+
+
+def test_group_norm_full_size_256_cubed():
+    """256^3 group norm: value and gradient against the oracle's own full-size evaluation."""
+    beta, delta = inputs.isotropic_theta(-0.05, -0.04, 0.02, 0.01)
+    dt = 0.9 * D.dt_max(beta, delta, [1, 1, 1], 3)
+    f, gb, gd, gdt = S.group_norm(beta, delta, dt, [1, 1, 1], 3, (256, 256, 256))
+    rf, rgb, rgd, rgdt = D.group_norm_and_grad(beta, delta, dt, [1, 1, 1], (256, 256, 256), 3)
+    assert f == pytest.approx(rf, rel=1e-10)
+    assert np.allclose(gd, rgd, rtol=1e-9)
+    assert np.allclose(np.array(gb), rgb, rtol=1e-9, atol=1e-11)
+    assert gdt == pytest.approx(rgdt, rel=1e-9)
+
+
+def test_group_norm_1d_yee_courant_one_is_zero():
+    """1D Yee at c dt = dx: v_g = 1 exactly, so f_g is round-off only (near k dx = pi both the
+    numerator and sqrt(1 - dt^2 S) of |v_g| vanish, which amplifies it)."""
+    f, *_ = S.group_norm(np.zeros((3, 3)), np.zeros(3), 1.0, [1, 1, 1], 1, (4096, 1, 1))
+    assert f < 1e-18
