@@ -5,6 +5,7 @@
     python -m paper_1710_06829_gb300.experiments differentiable  # 128^3 checkpointed gradient
     python -m paper_1710_06829_gb300.experiments optimize        # coefficient minimisation
     python -m paper_1710_06829_gb300.experiments reproduce       # Table 1 schemes by SLSQP on GPU
+    python -m paper_1710_06829_gb300.experiments group           # group-velocity minimisation
 
 Each prints one JSON object.  Every number comes from libfdtd's kernels, including the closed
 forms used for comparison (omega(k) of Eq. (dispersion_relation) and its k-gradient, from the
@@ -392,10 +393,40 @@ def reproduce(n=256):
             "norm_evaluations": obj.evals, "seconds": time.perf_counter() - t0}
 
 
+def group(n=256):
+    """The conclusions' proposal: minimise the group-velocity error, or phase and group error
+    together (2D, dx = dy, beta_xy = beta_yx, delta_x = delta_y, c dt / dx free; SLSQP over the
+    GPU norms, 3 x 2 x 2 start grid).  Each optimum is reported with both norms, beside Yee at
+    0.95 of its limit and the printed min.1."""
+    N = (n, n, 1)
+    tie = O.Tying.symmetric_2d(dt=None)
+    starts = [[b, d, nu] for b in (-0.1, 0.05, 0.2) for d in (-0.1, 0.1) for nu in (0.3, 0.8)]
+    lo, hi = [-0.125, -0.125, 0.05], [0.25, 0.125, 1.0]
+    ph = O.NormObjective([1, 1, 1], 2, N)
+    gr = O.NormObjective([1, 1, 1], 2, N, phase=0.0, group=1.0)
+
+    def both(theta):
+        c = tie.c0 + tie.T.T @ np.asarray(theta, dtype=np.float64)
+        return {"phase_norm": ph(c)[0], "group_norm": gr(c)[0]}
+    out = {"experiment": "group", "kgrid": list(N), "rows": {}}
+    out["rows"]["yee_0.95"] = {"theta": [0.0, 0.0, 0.95 / math.sqrt(2)],
+                               **both([0.0, 0.0, 0.95 / math.sqrt(2)])}
+    out["rows"]["min1_printed"] = {"theta": [0.110, -0.125, 0.686], **both([0.110, -0.125, 0.686])}
+    t0 = time.perf_counter()
+    for name, obj in (("min_phase", ph), ("min_group", gr),
+                      ("min_phase_plus_group", O.NormObjective([1, 1, 1], 2, N, phase=1.0, group=1.0))):
+        th, c, J = O.slsqp(obj, tie, starts, lo, hi)
+        out["rows"][name] = {"theta": [float(v) for v in th], "objective": J, **both(th)}
+    torch.cuda.synchronize()
+    out["seconds"] = time.perf_counter() - t0
+    out["theta"] = "(beta, delta, c dt / dx)"
+    return out
+
+
 def main():
     p = argparse.ArgumentParser()
     p.add_argument("what", choices=["dispersion", "cherenkov", "differentiable", "optimize",
-                                    "reproduce"])
+                                    "reproduce", "group"])
     p.add_argument("--mu", type=float, default=0.0)
     p.add_argument("--iters", type=int, default=50)
     a = p.parse_args()
@@ -407,6 +438,8 @@ def main():
         r = differentiable()
     elif a.what == "reproduce":
         r = reproduce()
+    elif a.what == "group":
+        r = group()
     else:
         r = optimize(iters=a.iters, mu=a.mu)
     print(json.dumps(r))

@@ -98,27 +98,34 @@ class Tying:
 
 
 class NormObjective:
-    """Eq. (norm) on a midpoint k-grid (GPU) plus an optional mu * propagation loss."""
+    """phase * Eq. (norm) + group * (group-velocity norm) on a midpoint k-grid (GPU), plus an
+    optional mu * propagation loss."""
 
-    def __init__(self, dx, dims, N, weight=L.FDTD_W_UNIFORM, weight_param=0.0, prop=None, mu=0.0):
+    def __init__(self, dx, dims, N, weight=L.FDTD_W_UNIFORM, weight_param=0.0, prop=None, mu=0.0,
+                 phase=1.0, group=0.0):
         self.dx, self.dims, self.N = list(dx), dims, tuple(N)
         self.weight, self.wparam = weight, weight_param
         self.prop, self.mu = prop, mu
+        self.phase, self.group = phase, group
         self.evals = 0
 
     def __call__(self, c):
         """Returns (J, grad13) or (None, None) when c violates Eq. (constraints)."""
         beta, delta, dt = Tying.split(c)
+        st = torch.cuda.current_stream().cuda_stream
+        J, g = 0.0, np.zeros(13)
         try:
-            out = L.disp_norm_eval(L.make_coeffs(beta, delta), dt, self.dx, self.dims, self.N,
-                                   self.weight, self.wparam, torch.cuda.current_stream().cuda_stream)
+            for wgt, fn in ((self.phase, L.disp_norm_eval), (self.group, L.disp_group_norm_eval)):
+                if wgt != 0.0:
+                    out = fn(L.make_coeffs(beta, delta), dt, self.dx, self.dims, self.N,
+                             self.weight, self.wparam, st)
+                    J += wgt * out[0]
+                    g += wgt * np.array(out[1:14])
         except L.FdtdError as e:
             if e.status == L.FDTD_EUNSTABLE:
                 return None, None
             raise
         self.evals += 1
-        J = out[0]
-        g = np.array(out[1:14])
         if self.prop is not None and self.mu != 0.0:
             Lp, gp = self.prop(beta, delta, dt)
             J = J + self.mu * Lp
