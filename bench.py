@@ -17,6 +17,7 @@ import math
 import os
 import statistics
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -113,7 +114,7 @@ class Clocks:
 
     def __init__(self, index=0):
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        self.path = os.path.join(tempfile.gettempdir(), f"fdtd_bench_clocks_{os.getpid()}.csv")
         self.index = index
         self.t0 = self.t1 = None
 

@@ -13,7 +13,7 @@ Conventions
   and their coefficients are ignored (treated as zero).
 * Units: c = 1.
 
-Readings of the paper taken here (each is listed in the design doc):
+Readings of the paper taken here:
 * App. B, final line: the paper prints ``+4 sum dx_j^2 beta_ij s_i^2 s_j^2``.
   The line before it has ``beta_ij/dx_i^2 (-1 + c_i + c_j - c_i c_j)``, which
   equals ``-4 dx_j^2 beta_ij s_i^2 s_j^2``; the minus sign is the one
