@@ -34,7 +34,7 @@ BYTES_FWD32 = 48.0    # E, B read once and written once per cell-update (FP32)
 BYTES_FWD64 = 96.0
 BYTES_ADJ32 = 60.0    # lambda (6) read+write, E^n (3) read
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of the FP32 step
-# kernel at 256^3, from one ncu capture (profiles/step_kernel_fp32_256cubed.md); reported only
+# kernel at 256^3, from one ncu capture of that kernel version; reported only
 # while the kernel sources still hash to the captured version.
 STEP_TRAFFIC = {"sources_sha256_16": "bb21314f498fdbad", "bytes_per_launch": 834147584}
 STEP_SOURCES = ["fdtd_fused32.cu", "fdtd_seg.cuh", "fdtd_tma.cuh", "fdtd_internal.cuh"]
