@@ -350,7 +350,7 @@ def run_ours(args):
             print(json.dumps({"part": "adj32", "gcells_per_s": adj, "ms_per_step": t_adj / seg * 1e3}))
         return
 
-    # --- end to end through the C ABI with host buffers: upload, 100 steps, download
+    # --- end to end through the C ABI with host buffers: upload, 20 steps, download
     n_inner = 20
     pinned_in = [f.pin_memory() for f in fields]
     pinned_out = [torch.empty_like(f).pin_memory() for f in fields]
@@ -360,7 +360,7 @@ def run_ours(args):
         sm.step(n_inner)
         sm.get_state_host(pinned_out)
     e2e_step()
-    e2e_reps = 3
+    e2e_reps = 10
     t0 = time.perf_counter()
     for _ in range(e2e_reps):
         e2e_step()
@@ -368,6 +368,18 @@ def run_ours(args):
     t_e2e = barrier_max(time.perf_counter() - t0, world)
     e2e = world * cells * n_inner * e2e_reps / t_e2e / 1e9
     sm.close()
+    # the host link alone: plain copies of the same pinned buffers; with the step time this gives
+    # the rate an upload + steps + download cannot exceed on this link
+    dev_bufs = [torch.empty_like(f, device="cuda") for f in fields]
+    for d, h in zip(dev_bufs, pinned_in):
+        d.copy_(h, non_blocking=True)
+    t_h2d = time_events(lambda: [d.copy_(h, non_blocking=True) for d, h in zip(dev_bufs, pinned_in)],
+                        3, stream) / 3
+    t_d2h = time_events(lambda: [h.copy_(d, non_blocking=True) for d, h in zip(dev_bufs, pinned_out)],
+                        3, stream) / 3
+    del dev_bufs
+    link_bytes = 6 * 4 * cells
+    e2e_ceiling = world * cells * n_inner / (t_h2d + n_inner * t_fwd / args.steps + t_d2h) / 1e9
 
     # --- FP64 forward for comparison
     sm64 = S.Simulation(shape, [1, 1, 1], dt, beta, delta, dims=3, dtype="f64", stream=stream)
@@ -406,7 +418,9 @@ def run_ours(args):
                      "kernel": "forward step (48 B/cell-update algorithmic)"},
         "e2e": {"value": e2e, "unit": "Gcell-updates/s",
                 "h2d_bytes_per_step": int(6 * 4 * cells), "d2h_bytes_per_step": int(6 * 4 * cells),
-                "step": f"host upload + {n_inner} leapfrog steps + host download"},
+                "step": f"host upload + {n_inner} leapfrog steps + host download",
+                "link_h2d_gbs": link_bytes / t_h2d / 1e9, "link_d2h_gbs": link_bytes / t_d2h / 1e9,
+                "ceiling": e2e_ceiling, "frac_of_ceiling": e2e / e2e_ceiling},
         "gpu_launches": args.steps * (1 if (n % 64 == 0 and n % 8 == 0) else 2),
         "clocks": clk.summary(),
     }

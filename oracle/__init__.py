@@ -16,6 +16,9 @@ Modules
                 gradient, the divergence diagnostics (Sec. 2.1/2.2) and the
                 rigid-bunch current that satisfies the discrete continuity
                 equation (App. A).
+``pic``         macro-particles coupled to the solver: first-order shape, staggered
+                field gather, Boris push and Esirkepov's charge-conserving current
+                (App. A, numerical continuity equation), one leapfrog PIC cycle.
 
 Units throughout: c = 1, mu0 = eps0 = 1.
 """
