@@ -191,6 +191,55 @@ int fdtd_diagnostic(fdtd_handle* h, int32_t kind, const double* params, double* 
 #define FDTD_DIV_E      2
 int fdtd_divergence(fdtd_handle* h, int32_t which, double* out_dev);
 
+/* ---- macro-particles (PIC coupling) -------------------------------------
+ *
+ * The paper keeps Yee's stencil in Ampere's law so that a charge-conserving current
+ * weighting makes the discrete continuity equation D_t rho + D . J = 0 hold (App. A,
+ * numerical continuity equation, after Esirkepov); Gauss's law D . E = rho (Eq. divE)
+ * is then kept from step to step.  Its particle runs (Sec. 6) use relativistic electron
+ * bunches.  The library's particle coupling (the shape and the pusher are readings; the
+ * paper names neither):
+ *   shape     first order: node i of axis a carries max(0, 1 - |x_a / dx_a - i|);
+ *   rho       at the nodes (i, j, k), sum_p q S_i S_j S_k / (dx dy dz);
+ *   gather    every field component from its own staggered positions (table above)
+ *             with the same shape; B^n = (B^{n-1/2} + B^{n+1/2}) / 2;
+ *   push      Boris's relativistic scheme in u = gamma v (c = 1);
+ *   current   Esirkepov's decomposition of the shape change, J_a at the E_a positions.
+ *
+ * A species: n macro-particles of charge q and charge-to-mass ratio q_over_m.  x[a] and
+ * u[a] (a = x, y, z) are device arrays of n values in the handle's dtype (float for
+ * FDTD_F32, double for FDTD_F64), structure of arrays, borrowed for the call and updated
+ * in place: positions in the units of dx (any finite value; they are wrapped into
+ * [0, n_a dx_a) by the step), u = gamma v.  A particle whose position or momentum is not
+ * finite, or whose position lies beyond 2^30 cells, is left unchanged, deposits nothing,
+ * and makes the next fdtd_sync return FDTD_ENONFINITE. */
+typedef struct {
+    void* x[3];
+    void* u[3];
+    int64_t n;
+    double q;
+    double q_over_m;
+} fdtd_species;
+
+/* Advance n >= 0 PIC cycles of the current state and the nspecies species:
+ *   B^{n+1/2} = B^{n-1/2} - dt D* x E^n                        (extended stencil, Eq. D*)
+ *   per particle: gather E^n, B^n at x^n; Boris u^{n-1/2} -> u^{n+1/2};
+ *                 x^{n+1} = x^n + dt u^{n+1/2} / gamma^{n+1/2}; Esirkepov J^{n+1/2}
+ *   E^{n+1}   = E^n + dt (D x B^{n+1/2} - J^{n+1/2})           (Yee stencil)
+ * The grid must be 3D (dims = 3) and not batched: FDTD_EINVAL otherwise.  With an absorbing
+ * layer the sponge factor multiplies B after the Faraday half and E after the Ampere half,
+ * as in fdtd_step (Gauss's law then holds outside the layer only); particles inside it are
+ * pushed as anywhere else.  The current is accumulated with floating-point global
+ * reductions, so the summation order (and the last bits of J) may differ between runs.
+ * The recorded history of fdtd_step is dropped (a PIC cycle has no adjoint here). */
+int fdtd_pic_step(fdtd_handle* h, int32_t n, const fdtd_species* species, int32_t nspecies);
+
+/* Add the charge density of the species at the nodes (first-order shape) to rho_dev:
+ * dense [nz][ny][nx] device array of the handle's dtype (the caller zeroes it).  With
+ * fdtd_divergence(FDTD_DIV_E) this checks Gauss's law D . E = rho (Eq. divE). */
+int fdtd_deposit_rho(fdtd_handle* h, const fdtd_species* species, int32_t nspecies,
+                     void* rho_dev);
+
 /* Failure-path self-test (no counterpart in the paper): launches, on the handle's stream, one
  * thread that polls an mbarrier phase nothing will complete, with the same bounded-wait helper
  * the TMA step kernels use, limited to `tries` polls (1 .. 2^20).  When the polls run out it

@@ -179,11 +179,15 @@ def push(p: Particles, E, Bn, dx, dt):
     return u1, x1
 
 
-def pic_step(s: F.State, species, c: F.Coeffs):
-    """One PIC cycle on state s (E^n, B^{n-1/2}) and the species list (x^n, u^{n-1/2})."""
+def pic_step(s: F.State, species, c: F.Coeffs, sponge=None):
+    """One PIC cycle on state s (E^n, B^{n-1/2}) and the species list (x^n, u^{n-1/2}).
+    ``sponge`` (the factor array of ``oracle.fdtd.sponge_factor``) multiplies B^{n+1/2}
+    and E^{n+1} after their updates, as in ``oracle.fdtd.step``."""
     shape = s.E[0].shape
     f = F.faraday_rhs(s.E, c)
     B_half = [s.B[a] + c.dt * f[a] for a in range(3)]
+    if sponge is not None:
+        B_half = [b * sponge for b in B_half]
     Bn = [0.5 * (s.B[a] + B_half[a]) for a in range(3)]
     J = [np.zeros(shape) for _ in range(3)]
     for p in species:
@@ -196,4 +200,6 @@ def pic_step(s: F.State, species, c: F.Coeffs):
     s.B = B_half
     g = F.ampere_curl(s.B, c)
     s.E = [s.E[a] + c.dt * (g[a] - J[a]) for a in range(3)]
+    if sponge is not None:
+        s.E = [e * sponge for e in s.E]
     return s

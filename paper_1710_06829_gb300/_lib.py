@@ -45,7 +45,8 @@ STATUS_NAMES = {0: "FDTD_OK", -1: "FDTD_EINVAL", -2: "FDTD_EUNSTABLE", -3: "FDTD
 # every symbol include/fdtd.h declares
 EXPORTS = ["fdtd_create", "fdtd_set_coeffs", "fdtd_set_state", "fdtd_get_state", "fdtd_get_step",
            "fdtd_step", "fdtd_checkpoint", "fdtd_set_adjoint", "fdtd_get_adjoint",
-           "fdtd_step_adjoint", "fdtd_diagnostic", "fdtd_divergence", "fdtd_selftest_wait_expiry",
+           "fdtd_step_adjoint", "fdtd_diagnostic", "fdtd_divergence", "fdtd_pic_step",
+           "fdtd_deposit_rho", "fdtd_selftest_wait_expiry",
            "fdtd_sync", "fdtd_destroy", "disp_norm_eval",
            "disp_norm_eval_noalloc", "disp_group_norm_eval", "disp_omega_eval", "fdtd_coeff_update", "fdtd_dt_max", "fdtd_last_error"]
 
@@ -75,6 +76,11 @@ class fdtd_source(C.Structure):
 class fdtd_probe(C.Structure):
     _fields_ = [("component", C.c_int32), ("x_index", C.c_int32), ("target", C.c_void_p),
                 ("target_steps", C.c_int64)]
+
+
+class fdtd_species(C.Structure):
+    _fields_ = [("x", C.c_void_p * 3), ("u", C.c_void_p * 3), ("n", C.c_int64), ("q", C.c_double),
+                ("q_over_m", C.c_double)]
 
 
 _lib = None
@@ -209,6 +215,16 @@ def fdtd_diagnostic(h, kind, params, out_dev):
 
 def fdtd_divergence(h, which, out_dev):
     check(load().fdtd_divergence(h, int(which), C.c_void_p(out_dev)))
+
+
+def fdtd_pic_step(h, n, species):
+    arr = (fdtd_species * max(1, len(species)))(*species)
+    check(load().fdtd_pic_step(h, int(n), arr, len(species)))
+
+
+def fdtd_deposit_rho(h, species, rho_dev):
+    arr = (fdtd_species * max(1, len(species)))(*species)
+    check(load().fdtd_deposit_rho(h, arr, len(species), C.c_void_p(rho_dev)))
 
 
 def fdtd_sync(h):

@@ -16,6 +16,7 @@
 #include <vector>
 
 #include "fdtd_tma.cuh"
+#include "pic.cuh"
 
 namespace fdtd {
 
@@ -260,7 +261,9 @@ struct fdtd_handle {
     FusedMaps lam_maps;                 // .e[c]: TMA descriptors of lambda_B component c (FP32)
     bool lam_staged = false;            // lam_maps valid: the staged FP32 adjoint E kernel runs
     FusedPlan* plan;    // TMA descriptors of both state sets (nullptr: reference-form kernels)
-    int* err_dev;       // raised by a kernel whose bounded wait expired
+    int* err_dev;       // bit 1: a bounded wait inside a kernel expired; bit 2: a particle
+                        // with a non-finite (or out-of-range) position or momentum
+    char* jpic;         // PIC current J^{n+1/2}: 3 padded arrays
 
     void* arr(int set, int c) { return state + ((size_t)set * 6 + c) * g.total * esz; }
     void* lam_arr(int c) { return lam + (size_t)c * g.total * esz; }
@@ -975,10 +978,127 @@ int fdtd_sync(fdtd_handle* h) {
     CK(cudaMemcpy(&flag, h->err_dev, sizeof(int), cudaMemcpyDeviceToHost));
     if (flag) {
         cudaMemset(h->err_dev, 0, sizeof(int));
-        set_error("a bounded wait inside a step kernel expired; the state is not valid");
-        return FDTD_ETIMEOUT;
+        if (flag & 1) {
+            set_error("a bounded wait inside a step kernel expired; the state is not valid");
+            return FDTD_ETIMEOUT;
+        }
+        set_error("a particle position or momentum was not finite (or beyond 2^30 cells); "
+                  "such particles were left unchanged and deposited nothing");
+        return FDTD_ENONFINITE;
     }
     return FDTD_OK;
+}
+
+// ---- macro-particles (PIC cycle) --------------------------------------------------------
+
+static int check_species(const fdtd_handle* h, const fdtd_species* sp, int32_t nsp,
+                         const char* who) {
+    if (nsp < 0 || (nsp > 0 && !sp)) {
+        set_error("%s: bad species list", who);
+        return FDTD_EINVAL;
+    }
+    if (h->grid.dims != 3 || h->grid.batched) {
+        set_error("%s: particles need a 3D grid (dims = 3, not batched)", who);
+        return FDTD_EINVAL;
+    }
+    for (int s = 0; s < nsp; ++s) {
+        if (sp[s].n < 0) { set_error("%s: species %d has a negative count", who, s); return FDTD_EINVAL; }
+        if (sp[s].n == 0) continue;
+        for (int a = 0; a < 3; ++a)
+            if (!sp[s].x[a] || !sp[s].u[a]) {
+                set_error("%s: species %d has a NULL array", who, s);
+                return FDTD_EINVAL;
+            }
+        if (!std::isfinite(sp[s].q) || !std::isfinite(sp[s].q_over_m)) {
+            set_error("%s: species %d has a non-finite charge or charge-to-mass ratio", who, s);
+            return FDTD_EINVAL;
+        }
+    }
+    return FDTD_OK;
+}
+
+template <typename T>
+static int pic_impl(fdtd_handle* h, int n, const fdtd_species* sp, int nsp) {
+    const Geom& g = h->g;
+    const Mult<T> m = make_mult<T>(h->cc, h->dx, h->dt, true);
+    const size_t arr = (size_t)g.total * sizeof(T);
+    if (!h->jpic) CK(cudaMalloc(&h->jpic, 3 * arr));
+    const T* spy = nullptr;
+    const T* spz = nullptr;
+    if (h->grid.absorb_cells > 0) {
+        spy = (const T*)h->aux;
+        spz = spy + g.ny;
+    }
+    T* J[3] = {(T*)h->jpic, (T*)(h->jpic + arr), (T*)(h->jpic + 2 * arr)};
+    const T* Jc[3] = {J[0], J[1], J[2]};
+    h->hist_len = 0;   // a PIC cycle has no recorded adjoint
+    for (int s = 0; s < n; ++s) {
+        FieldSet<T> cur = fieldset<T>(h, h->cur), nxt = fieldset<T>(h, 1 - h->cur);
+        CK(cudaMemsetAsync(h->jpic, 0, 3 * arr, h->stream));
+        launch_faraday_oop<T>(g, m, cur, nxt, spy, spz, h->stream);
+        CK(cudaGetLastError());
+        for (int q = 0; q < nsp; ++q) {
+            if (sp[q].n == 0) continue;
+            PushArgs<T> a;
+            a.g = g;
+            for (int c = 0; c < 3; ++c) {
+                const int b = c == 0 ? 1 : 0, d = c == 2 ? 1 : 2;
+                a.E[c] = cur.c[c];
+                a.B0[c] = cur.c[3 + c];
+                a.B1[c] = nxt.c[3 + c];
+                a.J[c] = J[c];
+                a.x[c] = (T*)sp[q].x[c];
+                a.u[c] = (T*)sp[q].u[c];
+                a.inv_dx[c] = (T)(1.0 / h->dx[c]);
+                a.jscale[c] = (T)(-sp[q].q / (h->dt * h->dx[b] * h->dx[d]));
+            }
+            a.L[0] = (T)(g.nx * h->dx[0]);
+            a.L[1] = (T)(g.ny * h->dx[1]);
+            a.L[2] = (T)(g.nz * h->dx[2]);
+            a.n = sp[q].n;
+            a.h = (T)(0.5 * sp[q].q_over_m * h->dt);
+            a.dt = (T)h->dt;
+            a.err = h->err_dev;
+            launch_pic_push<T>(a, h->stream);
+            CK(cudaGetLastError());
+        }
+        launch_ampere_current<T>(g, m, cur, nxt, Jc, nxt, spy, spz, h->stream);
+        CK(cudaGetLastError());
+        h->cur = 1 - h->cur;
+        h->step += 1;
+    }
+    return FDTD_OK;
+}
+
+int fdtd_pic_step(fdtd_handle* h, int32_t n, const fdtd_species* species, int32_t nspecies) {
+    if (!h || n < 0) { set_error("fdtd_pic_step: bad argument"); return FDTD_EINVAL; }
+    int rc = check_species(h, species, nspecies, "fdtd_pic_step");
+    if (rc) return rc;
+    if (h->grid.dtype == FDTD_F32) return pic_impl<float>(h, n, species, nspecies);
+    return pic_impl<double>(h, n, species, nspecies);
+}
+
+template <typename T>
+static int rho_impl(fdtd_handle* h, const fdtd_species* sp, int nsp, T* rho) {
+    const T inv_dx[3] = {(T)(1.0 / h->dx[0]), (T)(1.0 / h->dx[1]), (T)(1.0 / h->dx[2])};
+    const double vol = h->dx[0] * h->dx[1] * h->dx[2];
+    for (int q = 0; q < nsp; ++q) {
+        if (sp[q].n == 0) continue;
+        const T* x[3] = {(const T*)sp[q].x[0], (const T*)sp[q].x[1], (const T*)sp[q].x[2]};
+        launch_deposit_rho<T>(h->g, x, sp[q].n, inv_dx, (T)(sp[q].q / vol), rho, h->err_dev,
+                              h->stream);
+        CK(cudaGetLastError());
+    }
+    return FDTD_OK;
+}
+
+int fdtd_deposit_rho(fdtd_handle* h, const fdtd_species* species, int32_t nspecies,
+                     void* rho_dev) {
+    if (!h || !rho_dev) { set_error("fdtd_deposit_rho: bad argument"); return FDTD_EINVAL; }
+    int rc = check_species(h, species, nspecies, "fdtd_deposit_rho");
+    if (rc) return rc;
+    if (h->grid.dtype == FDTD_F32) return rho_impl<float>(h, species, nspecies, (float*)rho_dev);
+    return rho_impl<double>(h, species, nspecies, (double*)rho_dev);
 }
 
 void fdtd_destroy(fdtd_handle* h) {
@@ -1000,6 +1120,7 @@ void fdtd_destroy(fdtd_handle* h) {
         cudaStreamDestroy(h->xfer);
     }
     if (h->err_dev) cudaFree(h->err_dev);
+    if (h->jpic) cudaFree(h->jpic);
     if (h->dpart) cudaFree(h->dpart);
     if (h->plan) fused_plan_destroy(h->plan);
     for (char* p : h->ckpt)

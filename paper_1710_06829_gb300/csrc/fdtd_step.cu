@@ -14,6 +14,7 @@
 #include <cmath>
 
 #include "fdtd_internal.cuh"
+#include "pic.cuh"
 
 namespace fdtd {
 
@@ -127,6 +128,102 @@ void launch_ampere_v0(const Geom& g, const Mult<T>& m, FieldSet<T> s, const T* s
     dim3 blk(128), grd((g.nx + 127) / 128, g.ny, g.nz);
     ampere_v0_kernel<T><<<grd, blk, 0, st>>>(g, m, s, sponge_y, sponge_z, jyz, jx_row);
 }
+
+// ---------------------------------------------------------------------------
+// PIC cycle field halves (one thread per cell, out of place so that the particle push sees
+// both B^{n-1/2} and B^{n+1/2}; the current J^{n+1/2} is three padded arrays at the E
+// positions, App. A numerical continuity equation)
+// ---------------------------------------------------------------------------
+
+template <typename T>
+__global__ void faraday_oop_kernel(Geom g, Mult<T> m, FieldSet<T> in, FieldSet<T> out,
+                                   const T* __restrict__ spy, const T* __restrict__ spz) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y, k = blockIdx.z;
+    if (i >= g.nx) return;
+    const long long c = pidx(g, i, j, k);
+    const long long Y = g.nxp;
+    const long long zp1 = zoff(g, k, 1), zm1 = zoff(g, k, -1), zp2 = zoff(g, k, 2);
+    const T* Ex = in.c[0];
+    const T* Ey = in.c[1];
+    const T* Ez = in.c[2];
+#define DSX(F) dstar_at(F, c, 1, 2, -1, Y, -Y, zp1, zm1, m.cA[0], m.cD[0], m.cB[0][1], m.cB[0][2])
+#define DSY(F) dstar_at(F, c, Y, 2 * Y, -Y, 1, -1, zp1, zm1, m.cA[1], m.cD[1], m.cB[1][0], m.cB[1][2])
+#define DSZ(F) dstar_at(F, c, zp1, zp2, zm1, 1, -1, Y, -Y, m.cA[2], m.cD[2], m.cB[2][0], m.cB[2][1])
+    T bx = in.c[3][c] + (DSZ(Ey) - DSY(Ez));
+    T by = in.c[4][c] + (DSX(Ez) - DSZ(Ex));
+    T bz = in.c[5][c] + (DSY(Ex) - DSX(Ey));
+#undef DSX
+#undef DSY
+#undef DSZ
+    if (spy != nullptr) {
+        const T f = spy[j] * spz[k];
+        bx *= f; by *= f; bz *= f;
+    }
+    store_images(g, out.c[3], i, j, k, bx);
+    store_images(g, out.c[4], i, j, k, by);
+    store_images(g, out.c[5], i, j, k, bz);
+}
+
+template <typename T>
+__global__ void ampere_current_kernel(Geom g, Mult<T> m, FieldSet<T> in, FieldSet<T> bset,
+                                      const T* __restrict__ Jx, const T* __restrict__ Jy,
+                                      const T* __restrict__ Jz, FieldSet<T> out,
+                                      const T* __restrict__ spy, const T* __restrict__ spz) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y, k = blockIdx.z;
+    if (i >= g.nx) return;
+    const long long c = pidx(g, i, j, k);
+    const long long Y = g.nxp;
+    const long long zm1 = zoff(g, k, -1);
+    const T* Bx = bset.c[3];
+    const T* By = bset.c[4];
+    const T* Bz = bset.c[5];
+    T ex = ampere_comp(in.c[0][c], Bz[c], Bz[c - Y], By[c], By[c + zm1], m.cE[1], m.cE[2]);
+    T ey = ampere_comp(in.c[1][c], Bx[c], Bx[c + zm1], Bz[c], Bz[c - 1], m.cE[2], m.cE[0]);
+    T ez = ampere_comp(in.c[2][c], By[c], By[c - 1], Bx[c], Bx[c - Y], m.cE[0], m.cE[1]);
+    ex = fma(-m.dt, Jx[c], ex);
+    ey = fma(-m.dt, Jy[c], ey);
+    ez = fma(-m.dt, Jz[c], ez);
+    if (spy != nullptr) {
+        const T f = spy[j] * spz[k];
+        ex *= f; ey *= f; ez *= f;
+    }
+    store_images(g, out.c[0], i, j, k, ex);
+    store_images(g, out.c[1], i, j, k, ey);
+    store_images(g, out.c[2], i, j, k, ez);
+}
+
+template <typename T>
+void launch_faraday_oop(const Geom& g, const Mult<T>& m, FieldSet<T> in, FieldSet<T> out,
+                        const T* sponge_y, const T* sponge_z, cudaStream_t st) {
+    dim3 blk(128), grd((g.nx + 127) / 128, g.ny, g.nz);
+    faraday_oop_kernel<T><<<grd, blk, 0, st>>>(g, m, in, out, sponge_y, sponge_z);
+}
+
+template <typename T>
+void launch_ampere_current(const Geom& g, const Mult<T>& m, FieldSet<T> in, FieldSet<T> bset,
+                           const T* const J[3], FieldSet<T> out, const T* sponge_y,
+                           const T* sponge_z, cudaStream_t st) {
+    dim3 blk(128), grd((g.nx + 127) / 128, g.ny, g.nz);
+    ampere_current_kernel<T><<<grd, blk, 0, st>>>(g, m, in, bset, J[0], J[1], J[2], out, sponge_y,
+                                                  sponge_z);
+}
+
+template void launch_faraday_oop<float>(const Geom&, const Mult<float>&, FieldSet<float>,
+                                        FieldSet<float>, const float*, const float*,
+                                        cudaStream_t);
+template void launch_faraday_oop<double>(const Geom&, const Mult<double>&, FieldSet<double>,
+                                         FieldSet<double>, const double*, const double*,
+                                         cudaStream_t);
+template void launch_ampere_current<float>(const Geom&, const Mult<float>&, FieldSet<float>,
+                                           FieldSet<float>, const float* const[3],
+                                           FieldSet<float>, const float*, const float*,
+                                           cudaStream_t);
+template void launch_ampere_current<double>(const Geom&, const Mult<double>&, FieldSet<double>,
+                                            FieldSet<double>, const double* const[3],
+                                            FieldSet<double>, const double*, const double*,
+                                            cudaStream_t);
 
 template void launch_faraday_v0<float>(const Geom&, const Mult<float>&, FieldSet<float>,
                                        const float*, const float*, cudaStream_t);

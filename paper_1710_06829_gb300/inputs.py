@@ -195,3 +195,50 @@ def vacuum_target_2d(F0, dx, dt, nsteps, x_index):
         col = (F * np.cos(kn * s * dt)) @ phase_x     # [ny] in k_y
         out[s - 1] = np.fft.ifft(col).real
     return out
+
+
+def particles(shape_xyz, dx, n, seed, u_scale=1.0):
+    """n macro-particles: positions uniform over the periodic box, momenta u = gamma v with
+    standard-normal components times u_scale.  Arrays (3, n), float64."""
+    rng = np.random.default_rng(seed)
+    L = np.array([shape_xyz[a] * dx[a] for a in range(3)])[:, None]
+    x = rng.uniform(0.0, 1.0, (3, n)) * L
+    u = u_scale * rng.standard_normal((3, n))
+    return x, u
+
+
+def uniform_plasma(shape_xyz, dx, ppc, seed, u_th):
+    """ppc particles in every cell, ordered cell by cell (x fastest), each uniformly placed
+    inside its cell; thermal momenta u_th * N(0, 1) per component.  Arrays (3, n), float64."""
+    rng = np.random.default_rng(seed)
+    nx, ny, nz = shape_xyz
+    k, j, i = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    cells = np.stack([i.ravel(), j.ravel(), k.ravel()]).astype(np.float64)
+    base = np.repeat(cells, ppc, axis=1)
+    x = (base + rng.uniform(0.0, 1.0, base.shape)) * np.asarray(dx, dtype=np.float64)[:, None]
+    u = u_th * rng.standard_normal(base.shape)
+    return x, u
+
+
+def gaussian_bunch(n, center, sigma, direction, gamma, seed, dx=(1.0, 1.0, 1.0)):
+    """n macro-particles of a relativistic bunch: positions Gaussian about `center` with
+    widths sigma = (sigma_parallel, sigma_perp) (in cells, parallel = along `direction`),
+    all with momentum u = sqrt(gamma^2 - 1) along the unit vector `direction`.  The draw is
+    sorted by cell (x fastest after z, y) so that neighbouring particles share cells.
+    Arrays (3, n), float64, positions in the units of dx."""
+    rng = np.random.default_rng(seed)
+    d = np.asarray(direction, dtype=np.float64)
+    d = d / np.linalg.norm(d)
+    # an orthonormal pair perpendicular to d
+    a = np.array([0.0, 0.0, 1.0]) if abs(d[2]) < 0.9 else np.array([1.0, 0.0, 0.0])
+    e1 = np.cross(d, a)
+    e1 /= np.linalg.norm(e1)
+    e2 = np.cross(d, e1)
+    s_par, s_perp = sigma
+    r = rng.standard_normal((3, n))
+    cells = (np.asarray(center, dtype=np.float64)[:, None] + s_par * r[0] * d[:, None]
+             + s_perp * r[1] * e1[:, None] + s_perp * r[2] * e2[:, None])
+    order = np.lexsort((np.floor(cells[0]), np.floor(cells[1]), np.floor(cells[2])))
+    x = cells[:, order] * np.asarray(dx, dtype=np.float64)[:, None]
+    u = np.repeat((math.sqrt(gamma * gamma - 1.0) * d)[:, None], n, axis=1)
+    return x, u

@@ -45,6 +45,25 @@ class Probe:
         self.s = L.fdtd_probe(int(component), int(x_index), target.data_ptr(), target.shape[0])
 
 
+class Species:
+    """Macro-particles of one species on the device (see fdtd_species in include/fdtd.h):
+    x, u are (3, n) tensors (positions, u = gamma v) of the simulation's dtype, updated in
+    place by Simulation.pic_step; q is the macro-particle charge, qm the charge-to-mass ratio."""
+
+    def __init__(self, x: torch.Tensor, u: torch.Tensor, q, qm):
+        assert x.is_cuda and u.is_cuda and x.shape == u.shape and x.shape[0] == 3
+        assert x.dtype == u.dtype
+        self.x = x.contiguous()
+        self.u = u.contiguous()
+        self.q, self.qm = float(q), float(qm)
+
+    def struct(self):
+        n = self.x.shape[1]
+        return L.fdtd_species((L.C.c_void_p * 3)(*[self.x[a].data_ptr() for a in range(3)]),
+                              (L.C.c_void_p * 3)(*[self.u[a].data_ptr() for a in range(3)]),
+                              n, self.q, self.qm)
+
+
 class Simulation:
     """One FDTD state (E, B) on a periodic nx x ny x nz grid, owned by libfdtd."""
 
@@ -151,6 +170,26 @@ class Simulation:
         if probe is not None and probe.target.dtype != self.tdtype:
             raise TypeError("probe target dtype does not match the simulation dtype")
         L.fdtd_step_adjoint(self.h, n, probe.s if probe is not None else None, grad.data_ptr())
+
+    # -- macro-particles (PIC cycle) -----------------------------------------
+    def _check_species(self, species):
+        for sp in species:
+            if sp.x.dtype != self.tdtype:
+                raise TypeError("species dtype does not match the simulation dtype")
+
+    def pic_step(self, n, species):
+        """n PIC cycles: extended Faraday, gather + Boris push + Esirkepov current for every
+        species, Yee Ampere with the current (fdtd_pic_step)."""
+        self._check_species(species)
+        L.fdtd_pic_step(self.h, n, [sp.struct() for sp in species])
+
+    def deposit_rho(self, species, out=None):
+        """Charge density at the nodes (first-order shape), dense (nz, ny, nx) of the dtype."""
+        self._check_species(species)
+        if out is None:
+            out = torch.zeros(self.shape, dtype=self.tdtype, device="cuda")
+        L.fdtd_deposit_rho(self.h, [sp.struct() for sp in species], out.data_ptr())
+        return out
 
     # -- diagnostics -----------------------------------------------------------
     def energy(self, x_lo, x_len, margin=0, out=None):
