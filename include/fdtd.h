@@ -211,8 +211,8 @@ int fdtd_divergence(fdtd_handle* h, int32_t which, double* out_dev);
  * FDTD_F32, double for FDTD_F64), structure of arrays, borrowed for the call and updated
  * in place: positions in the units of dx (any finite value; they are wrapped into
  * [0, n_a dx_a) by the step), u = gamma v.  A particle whose position or momentum is not
- * finite, or whose position lies beyond 2^30 cells, is left unchanged, deposits nothing,
- * and makes the next fdtd_sync return FDTD_ENONFINITE. */
+ * finite is left unchanged, deposits nothing, and makes the next fdtd_sync return
+ * FDTD_ENONFINITE. */
 typedef struct {
     void* x[3];
     void* u[3];
@@ -229,8 +229,10 @@ typedef struct {
  * The grid must be 3D (dims = 3) and not batched: FDTD_EINVAL otherwise.  With an absorbing
  * layer the sponge factor multiplies B after the Faraday half and E after the Ampere half,
  * as in fdtd_step (Gauss's law then holds outside the layer only); particles inside it are
- * pushed as anywhere else.  The current is accumulated with floating-point global
- * reductions, so the summation order (and the last bits of J) may differ between runs.
+ * pushed as anywhere else.  Ampere's law is linear in J: the step forms E^{n+1} without the
+ * current and the particles add -dt J^{n+1/2} into it with floating-point reductions (summed
+ * over a warp first when its 32 particles share their cells), so the summation order, and
+ * the last bits of E, may differ between runs.
  * The recorded history of fdtd_step is dropped (a PIC cycle has no adjoint here). */
 int fdtd_pic_step(fdtd_handle* h, int32_t n, const fdtd_species* species, int32_t nspecies);
 

@@ -263,7 +263,6 @@ struct fdtd_handle {
     FusedPlan* plan;    // TMA descriptors of both state sets (nullptr: reference-form kernels)
     int* err_dev;       // bit 1: a bounded wait inside a kernel expired; bit 2: a particle
                         // with a non-finite (or out-of-range) position or momentum
-    char* jpic;         // PIC current J^{n+1/2}: 3 padded arrays
 
     void* arr(int set, int c) { return state + ((size_t)set * 6 + c) * g.total * esz; }
     void* lam_arr(int c) { return lam + (size_t)c * g.total * esz; }
@@ -982,8 +981,8 @@ int fdtd_sync(fdtd_handle* h) {
             set_error("a bounded wait inside a step kernel expired; the state is not valid");
             return FDTD_ETIMEOUT;
         }
-        set_error("a particle position or momentum was not finite (or beyond 2^30 cells); "
-                  "such particles were left unchanged and deposited nothing");
+        set_error("a particle position or momentum was not finite; such particles were left "
+                  "unchanged and deposited nothing");
         return FDTD_ENONFINITE;
     }
     return FDTD_OK;
@@ -1021,21 +1020,26 @@ template <typename T>
 static int pic_impl(fdtd_handle* h, int n, const fdtd_species* sp, int nsp) {
     const Geom& g = h->g;
     const Mult<T> m = make_mult<T>(h->cc, h->dx, h->dt, true);
-    const size_t arr = (size_t)g.total * sizeof(T);
-    if (!h->jpic) CK(cudaMalloc(&h->jpic, 3 * arr));
     const T* spy = nullptr;
     const T* spz = nullptr;
     if (h->grid.absorb_cells > 0) {
         spy = (const T*)h->aux;
         spz = spy + g.ny;
     }
-    T* J[3] = {(T*)h->jpic, (T*)(h->jpic + arr), (T*)(h->jpic + 2 * arr)};
-    const T* Jc[3] = {J[0], J[1], J[2]};
     h->hist_len = 0;   // a PIC cycle has no recorded adjoint
     for (int s = 0; s < n; ++s) {
         FieldSet<T> cur = fieldset<T>(h, h->cur), nxt = fieldset<T>(h, 1 - h->cur);
-        CK(cudaMemsetAsync(h->jpic, 0, 3 * arr, h->stream));
-        launch_faraday_oop<T>(g, m, cur, nxt, spy, spz, h->stream);
+        // (E^{n+1} without the current, B^{n+1/2}) into the other set: Ampere's law is linear
+        // in J, so the particles add -dt J^{n+1/2} to E^{n+1} afterwards
+        if (h->plan) {
+            T* hE[3] = {nullptr, nullptr, nullptr};
+            launch_step_fused<T>(h->plan, h->cur, g, m, cur, nxt, spy, spz, nullptr, nullptr, hE,
+                                 h->err_dev, h->stream);
+        } else {
+            launch_faraday_oop<T>(g, m, cur, nxt, spy, spz, h->stream);
+            CK(cudaGetLastError());
+            launch_ampere_current<T>(g, m, cur, nxt, nullptr, nxt, spy, spz, h->stream);
+        }
         CK(cudaGetLastError());
         for (int q = 0; q < nsp; ++q) {
             if (sp[q].n == 0) continue;
@@ -1046,12 +1050,14 @@ static int pic_impl(fdtd_handle* h, int n, const fdtd_species* sp, int nsp) {
                 a.E[c] = cur.c[c];
                 a.B0[c] = cur.c[3 + c];
                 a.B1[c] = nxt.c[3 + c];
-                a.J[c] = J[c];
+                a.Eout[c] = nxt.c[c];
                 a.x[c] = (T*)sp[q].x[c];
                 a.u[c] = (T*)sp[q].u[c];
                 a.inv_dx[c] = (T)(1.0 / h->dx[c]);
-                a.jscale[c] = (T)(-sp[q].q / (h->dt * h->dx[b] * h->dx[d]));
+                a.escale[c] = (T)(sp[q].q / (h->dx[b] * h->dx[d]));
             }
+            a.spy = spy;
+            a.spz = spz;
             a.L[0] = (T)(g.nx * h->dx[0]);
             a.L[1] = (T)(g.ny * h->dx[1]);
             a.L[2] = (T)(g.nz * h->dx[2]);
@@ -1062,7 +1068,7 @@ static int pic_impl(fdtd_handle* h, int n, const fdtd_species* sp, int nsp) {
             launch_pic_push<T>(a, h->stream);
             CK(cudaGetLastError());
         }
-        launch_ampere_current<T>(g, m, cur, nxt, Jc, nxt, spy, spz, h->stream);
+        launch_refresh_images<T>(g, nxt.c[0], nxt.c[1], nxt.c[2], h->stream);
         CK(cudaGetLastError());
         h->cur = 1 - h->cur;
         h->step += 1;
@@ -1081,11 +1087,12 @@ int fdtd_pic_step(fdtd_handle* h, int32_t n, const fdtd_species* species, int32_
 template <typename T>
 static int rho_impl(fdtd_handle* h, const fdtd_species* sp, int nsp, T* rho) {
     const T inv_dx[3] = {(T)(1.0 / h->dx[0]), (T)(1.0 / h->dx[1]), (T)(1.0 / h->dx[2])};
+    const T L[3] = {(T)(h->g.nx * h->dx[0]), (T)(h->g.ny * h->dx[1]), (T)(h->g.nz * h->dx[2])};
     const double vol = h->dx[0] * h->dx[1] * h->dx[2];
     for (int q = 0; q < nsp; ++q) {
         if (sp[q].n == 0) continue;
         const T* x[3] = {(const T*)sp[q].x[0], (const T*)sp[q].x[1], (const T*)sp[q].x[2]};
-        launch_deposit_rho<T>(h->g, x, sp[q].n, inv_dx, (T)(sp[q].q / vol), rho, h->err_dev,
+        launch_deposit_rho<T>(h->g, x, sp[q].n, inv_dx, L, (T)(sp[q].q / vol), rho, h->err_dev,
                               h->stream);
         CK(cudaGetLastError());
     }
@@ -1120,7 +1127,6 @@ void fdtd_destroy(fdtd_handle* h) {
         cudaStreamDestroy(h->xfer);
     }
     if (h->err_dev) cudaFree(h->err_dev);
-    if (h->jpic) cudaFree(h->jpic);
     if (h->dpart) cudaFree(h->dpart);
     if (h->plan) fused_plan_destroy(h->plan);
     for (char* p : h->ckpt)

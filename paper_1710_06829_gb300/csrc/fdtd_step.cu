@@ -182,9 +182,11 @@ __global__ void ampere_current_kernel(Geom g, Mult<T> m, FieldSet<T> in, FieldSe
     T ex = ampere_comp(in.c[0][c], Bz[c], Bz[c - Y], By[c], By[c + zm1], m.cE[1], m.cE[2]);
     T ey = ampere_comp(in.c[1][c], Bx[c], Bx[c + zm1], Bz[c], Bz[c - 1], m.cE[2], m.cE[0]);
     T ez = ampere_comp(in.c[2][c], By[c], By[c - 1], Bx[c], Bx[c - Y], m.cE[0], m.cE[1]);
-    ex = fma(-m.dt, Jx[c], ex);
-    ey = fma(-m.dt, Jy[c], ey);
-    ez = fma(-m.dt, Jz[c], ez);
+    if (Jx != nullptr) {
+        ex = fma(-m.dt, Jx[c], ex);
+        ey = fma(-m.dt, Jy[c], ey);
+        ez = fma(-m.dt, Jz[c], ez);
+    }
     if (spy != nullptr) {
         const T f = spy[j] * spz[k];
         ex *= f; ey *= f; ez *= f;
@@ -206,7 +208,10 @@ void launch_ampere_current(const Geom& g, const Mult<T>& m, FieldSet<T> in, Fiel
                            const T* const J[3], FieldSet<T> out, const T* sponge_y,
                            const T* sponge_z, cudaStream_t st) {
     dim3 blk(128), grd((g.nx + 127) / 128, g.ny, g.nz);
-    ampere_current_kernel<T><<<grd, blk, 0, st>>>(g, m, in, bset, J[0], J[1], J[2], out, sponge_y,
+    const T* Jx = J ? J[0] : nullptr;
+    const T* Jy = J ? J[1] : nullptr;
+    const T* Jz = J ? J[2] : nullptr;
+    ampere_current_kernel<T><<<grd, blk, 0, st>>>(g, m, in, bset, Jx, Jy, Jz, out, sponge_y,
                                                   sponge_z);
 }
 

@@ -14,11 +14,16 @@
 // so that (rho^{n+1} - rho^n)/dt + D.J^{n+1/2} = 0 holds to rounding (App. A numerical
 // continuity equation) and Gauss's law D.E = rho (Eq. divE) is kept.  A particle moves less
 // than a cell per step (|v| < c, c dt < dx on any stable grid), so per axis its old and new
-// supports fit a 3-node window starting at floor(g0) + min(0, floor(g1) - floor(g0)); each
-// particle adds at most 2 x 3 x 3 face values per component with global reductions.
+// supports fit the 4-node window floor(g0) - 1 .. floor(g0) + 2.
 //
-// One thread per particle, grid-stride; the J arrays use the padded field layout (owned cells
-// only, no images: the Ampere kernel reads owned cells).
+// Ampere's law is linear in J, so the cycle first forms E^{n+1} without the current (the
+// vacuum step kernel) and the push adds -dt J^{n+1/2} into its owned cells: no current
+// array, no extra pass over the grid; a small kernel then copies the owned cells near the x
+// and y ends to their periodic images (the ghosts the next step reads).  Warps move through the particle array together; when all 32
+// lanes of a warp share the same deposit windows (a dense bunch whose particles share a
+// cell), each face value is summed over the warp by shuffles and added once, which removes
+// most same-address global reductions; otherwise every lane adds its own values.
+#include <climits>
 #include <cmath>
 
 #include "pic.cuh"
@@ -27,6 +32,7 @@ namespace fdtd {
 namespace picd {
 
 constexpr int THREADS = 256;
+constexpr unsigned FULL = 0xffffffffu;
 
 __device__ __forceinline__ int wrapi(int i, int n) {
     int r = i % n;
@@ -86,28 +92,42 @@ __device__ __forceinline__ T gather_mean(const T* __restrict__ F0, const T* __re
     return out;
 }
 
-// old-shape weights, shape change and absolute first node of the 3-node window of one axis
+// old-shape weights and shape change on the 4-node window f0 - 1 .. f0 + 2 of one axis
+// (f0 = floor(g0)): it holds the old support (f0, f0 + 1) and, for a move of less than one
+// cell, the new one; it depends on the old position only, so particles of one cell share it
 template <typename T>
 struct Win {
-    int start;
-    T S0[3], dS[3];
+    int idx[4];   // the four nodes, wrapped into [0, n)
+    T s1, s2;     // old-shape weights of nodes f0, f0 + 1 (those of f0 - 1 and f0 + 2 are 0)
+    T dS[4];      // shape change S1 - S0 on the four nodes
+    __device__ __forceinline__ T S0(int m) const { return m == 1 ? s1 : (m == 2 ? s2 : T(0)); }
 };
 
 template <typename T>
-__device__ __forceinline__ Win<T> window(T g0, T g1) {
-    const T f0 = floor(g0), f1 = floor(g1);
-    const int s = (int)(f1 - f0);   // -1, 0 or 1 for a move of less than one cell
+__device__ __forceinline__ Win<T> window(T g0, T g1, int n) {
+    const T f0 = floor(g0);
     Win<T> w;
-    w.start = (int)f0 + (s < 0 ? s : 0);
+    w.idx[0] = wrapi((int)f0 - 1, n);
 #pragma unroll
-    for (int m = 0; m < 3; ++m) {
-        const T node = (T)(w.start + m);
+    for (int m = 1; m < 4; ++m) w.idx[m] = w.idx[m - 1] + 1 == n ? 0 : w.idx[m - 1] + 1;
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        const T node = f0 + (T)(m - 1);
         const T s0 = fmax(T(0), T(1) - fabs(g0 - node));
         const T s1 = fmax(T(0), T(1) - fabs(g1 - node));
-        w.S0[m] = s0;
+        if (m == 1) w.s1 = s0;
+        if (m == 2) w.s2 = s0;
         w.dS[m] = s1 - s0;
     }
     return w;
+}
+
+// a finite coordinate moved into [0, L] (unchanged when already inside)
+template <typename T>
+__device__ __forceinline__ T into_box(T x, T L) {
+    if (x >= T(0) && x < L) return x;
+    const T r = x - L * floor(x / L);
+    return r < T(0) ? T(0) : (r > L ? L : r);
 }
 
 template <typename T>
@@ -115,109 +135,232 @@ __device__ __forceinline__ bool finite3(T a, T b, T c) {
     return isfinite(a) && isfinite(b) && isfinite(c);
 }
 
-// J_a face values of one particle: axis a carries the cumulative sum, b and c the weights
+// where -dt J goes: the owned cells of E^{n+1}, times the absorbing-layer factor if any
 template <typename T>
-__device__ __forceinline__ void deposit_axis(T* __restrict__ J, const Geom& g, const Win<T>& wa,
-                                             const Win<T>& wb, const Win<T>& wc, int na, int nb,
-                                             int nc, int axis, T scale) {
-    const T third = T(1) / T(3);
+struct Sink {
+    T* E[3];
+    const T* spy;
+    const T* spz;
+    Geom g;
+
+    // owned cell (wrapped node indices); the ghosts are refreshed after the push
+    __device__ __forceinline__ void add(int axis, int i, int j, int k, T v) const {
+        if (spy != nullptr) v *= spy[j] * spz[k];
+        T* Ea = axis == 0 ? E[0] : (axis == 1 ? E[1] : E[2]);   // no local-memory indexing
+        atomicAdd(Ea + pidx(g, i, j, k), v);
+    }
+};
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll
-    for (int mb = 0; mb < 3; ++mb)
-#pragma unroll
-        for (int mc = 0; mc < 3; ++mc) {
-            const T f = wb.S0[mb] * wc.S0[mc] + T(0.5) * wb.dS[mb] * wc.S0[mc] +
-                        T(0.5) * wb.S0[mb] * wc.dS[mc] + third * wb.dS[mb] * wc.dS[mc];
-            if (f == T(0)) continue;
-            const T c0 = wa.dS[0] * f;
-            const T c1 = c0 + wa.dS[1] * f;
-            const int ib = wrapi(wb.start + mb, nb), ic = wrapi(wc.start + mc, nc);
-#pragma unroll
-            for (int ma = 0; ma < 2; ++ma) {
-                const T v = ma == 0 ? c0 : c1;
-                if (v == T(0)) continue;
-                const int ia = wrapi(wa.start + ma, na);
-                int i, j, k;
-                if (axis == 0) { i = ia; j = ib; k = ic; }
-                else if (axis == 1) { i = ib; j = ia; k = ic; }
-                else { i = ib; j = ic; k = ia; }
-                atomicAdd(J + pidx(g, i, j, k), scale * v);
-            }
-        }
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+    return v;
 }
 
 template <typename T>
-__global__ void __launch_bounds__(THREADS) push_kernel(PushArgs<T> a) {
+__device__ __forceinline__ T pick4(int m, T a, T b, T c, T d) {
+    return m == 0 ? a : (m == 1 ? b : (m == 2 ? c : d));
+}
+
+template <typename T>
+__device__ __forceinline__ Win<T> pick_win(int m, const Win<T>& a, const Win<T>& b,
+                                           const Win<T>& c) {
+    Win<T> w;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        w.idx[q] = m == 0 ? a.idx[q] : (m == 1 ? b.idx[q] : c.idx[q]);
+        w.dS[q] = m == 0 ? a.dS[q] : (m == 1 ? b.dS[q] : c.dS[q]);
+    }
+    w.s1 = m == 0 ? a.s1 : (m == 1 ? b.s1 : c.s1);
+    w.s2 = m == 0 ? a.s2 : (m == 1 ? b.s2 : c.s2);
+    return w;
+}
+
+// -dt J^{n+1/2} of one particle into E^{n+1}.  For component a the axis a carries the
+// cumulative sum of W_a over its window (faces f0 - 1/2 .. f0 + 3/2; the sum over the whole
+// window vanishes) and the other two axes b < c the weights; escale[a] = q / (dx_b dx_c)
+// turns the cumulative sum into -dt J_a.  `uni` (warp-uniform): every lane of the warp is
+// live with the same windows, so each face value is summed over the warp by shuffles and
+// lane 0 adds it once; otherwise every lane adds its own values.  The axis and b loops stay
+// rolled (operands picked by selects) to keep the kernel's code small: fully unrolled, the
+// reduction sites overflowed the instruction cache.
+template <typename T>
+__device__ __forceinline__ void deposit(const Sink<T>& sink, const Win<T>& wx, const Win<T>& wy,
+                                        const Win<T>& wz, const T escale[3], bool uni) {
+    const T third = T(1) / T(3);
+    const bool lane0 = (threadIdx.x & 31) == 0;
+#pragma unroll 1
+    for (int axis = 0; axis < 3; ++axis) {
+        const Win<T> wa = pick_win(axis, wx, wy, wz);
+        const Win<T> wb = axis == 0 ? wy : wx;
+        const Win<T> wc = axis == 2 ? wy : wz;
+        const T scale = axis == 0 ? escale[0] : (axis == 1 ? escale[1] : escale[2]);
+        const bool moved = wa.dS[0] != T(0) || wa.dS[1] != T(0) || wa.dS[2] != T(0);
+        if (uni ? !__any_sync(FULL, moved) : !moved) continue;
+#pragma unroll 1
+        for (int mb = 0; mb < 4; ++mb) {
+            const T s0b = wb.S0(mb);
+            const T dsb = pick4(mb, wb.dS[0], wb.dS[1], wb.dS[2], wb.dS[3]);
+            const int ib = pick4(mb, wb.idx[0], wb.idx[1], wb.idx[2], wb.idx[3]);
+#pragma unroll
+            for (int mc = 0; mc < 4; ++mc) {
+                const T s0c = wc.S0(mc);
+                const T f = s0b * s0c + T(0.5) * dsb * s0c + T(0.5) * s0b * wc.dS[mc] +
+                            third * dsb * wc.dS[mc];
+                if (uni ? !__any_sync(FULL, f != T(0)) : f == T(0)) continue;
+                const int ic = wc.idx[mc];
+                T cum = T(0);
+#pragma unroll
+                for (int ma = 0; ma < 3; ++ma) {
+                    cum += wa.dS[ma] * f;
+                    T v = scale * cum;
+                    if (uni) {
+                        v = warp_sum(v);
+                        if (!lane0) continue;
+                    }
+                    if (v == T(0)) continue;
+                    const int ia = wa.idx[ma];
+                    // (i, j, k) of the face: axis a gets ia, the others ib (lower) and ic
+                    const int i = axis == 0 ? ia : ib;
+                    const int j = axis == 0 ? ib : (axis == 1 ? ia : ic);
+                    const int k = axis == 2 ? ia : ic;
+                    sink.add(axis, i, j, k, v);
+                }
+            }
+        }
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(THREADS, 2) push_kernel(PushArgs<T> a) {
     const Geom& g = a.g;
-    const T lim = T(1073741824);   // 2^30 cells
-    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < a.n;
-         p += (long long)gridDim.x * blockDim.x) {
-        const T x = a.x[0][p], y = a.x[1][p], z = a.x[2][p];
-        const T ux = a.u[0][p], uy = a.u[1][p], uz = a.u[2][p];
-        if (!finite3(x, y, z) || !finite3(ux, uy, uz)) {
-            atomicOr(a.err, 2);
-            continue;
+    Sink<T> sink;
+    sink.g = g;
+    for (int c = 0; c < 3; ++c) sink.E[c] = a.Eout[c];
+    sink.spy = a.spy;
+    sink.spz = a.spz;
+    // the loop bound is warp-uniform, so every lane of a warp runs every iteration
+    for (long long base = (long long)blockIdx.x * blockDim.x; base < a.n;
+         base += (long long)gridDim.x * blockDim.x) {
+        const long long p = base + threadIdx.x;
+        bool live = p < a.n;
+        T x = 0, y = 0, z = 0, ux = 0, uy = 0, uz = 0;
+        if (live) {
+            x = a.x[0][p]; y = a.x[1][p]; z = a.x[2][p];
+            ux = a.u[0][p]; uy = a.u[1][p]; uz = a.u[2][p];
+            if (!finite3(x, y, z) || !finite3(ux, uy, uz)) {
+                atomicOr(a.err, 2);
+                live = false;
+            } else {
+                x = into_box(x, a.L[0]); y = into_box(y, a.L[1]); z = into_box(z, a.L[2]);
+            }
         }
-        const T gx = x * a.inv_dx[0], gy = y * a.inv_dx[1], gz = z * a.inv_dx[2];
-        if (fabs(gx) > lim || fabs(gy) > lim || fabs(gz) > lim) {
-            atomicOr(a.err, 2);
-            continue;
+        Win<T> wx, wy, wz;
+        if (live) {
+            const T gx = x * a.inv_dx[0], gy = y * a.inv_dx[1], gz = z * a.inv_dx[2];
+            // ---- gather at x^n
+            const Lin<T> nx_ = lin(gx, g.nx), ny_ = lin(gy, g.ny), nz_ = lin(gz, g.nz);
+            const Lin<T> sx = lin(gx - T(0.5), g.nx), sy = lin(gy - T(0.5), g.ny),
+                         sz = lin(gz - T(0.5), g.nz);
+            const T Ex = gather(a.E[0], g, sx, ny_, nz_);
+            const T Ey = gather(a.E[1], g, nx_, sy, nz_);
+            const T Ez = gather(a.E[2], g, nx_, ny_, sz);
+            const T Bx = gather_mean(a.B0[0], a.B1[0], g, nx_, sy, sz);
+            const T By = gather_mean(a.B0[1], a.B1[1], g, sx, ny_, sz);
+            const T Bz = gather_mean(a.B0[2], a.B1[2], g, sx, sy, nz_);
+            // ---- Boris push u^{n-1/2} -> u^{n+1/2}
+            const T h = a.h;
+            const T umx = ux + h * Ex, umy = uy + h * Ey, umz = uz + h * Ez;
+            const T gm = sqrt(T(1) + umx * umx + umy * umy + umz * umz);
+            const T tx = h * Bx / gm, ty = h * By / gm, tz = h * Bz / gm;
+            const T t2 = tx * tx + ty * ty + tz * tz;
+            const T den = T(1) + t2;
+            const T sxv = T(2) * tx / den, syv = T(2) * ty / den, szv = T(2) * tz / den;
+            const T upx = umx + (umy * tz - umz * ty);
+            const T upy = umy + (umz * tx - umx * tz);
+            const T upz = umz + (umx * ty - umy * tx);
+            const T u1x = umx + (upy * szv - upz * syv) + h * Ex;
+            const T u1y = umy + (upz * sxv - upx * szv) + h * Ey;
+            const T u1z = umz + (upx * syv - upy * sxv) + h * Ez;
+            const T g1 = sqrt(T(1) + u1x * u1x + u1y * u1y + u1z * u1z);
+            const T x1 = x + a.dt * u1x / g1, y1 = y + a.dt * u1y / g1, z1 = z + a.dt * u1z / g1;
+            wx = window(gx, x1 * a.inv_dx[0], g.nx);
+            wy = window(gy, y1 * a.inv_dx[1], g.ny);
+            wz = window(gz, z1 * a.inv_dx[2], g.nz);
+            // ---- new state, positions wrapped into [0, L)
+            T xw = x1, yw = y1, zw = z1;
+            if (xw < T(0)) xw += a.L[0]; else if (xw >= a.L[0]) xw -= a.L[0];
+            if (yw < T(0)) yw += a.L[1]; else if (yw >= a.L[1]) yw -= a.L[1];
+            if (zw < T(0)) zw += a.L[2]; else if (zw >= a.L[2]) zw -= a.L[2];
+            a.x[0][p] = xw; a.x[1][p] = yw; a.x[2][p] = zw;
+            a.u[0][p] = u1x; a.u[1][p] = u1y; a.u[2][p] = u1z;
+        } else {
+#pragma unroll
+            for (int m = 0; m < 4; ++m) {
+                wx.idx[m] = wy.idx[m] = wz.idx[m] = 0;
+                wx.dS[m] = wy.dS[m] = wz.dS[m] = T(0);
+            }
+            wx.s1 = wx.s2 = wy.s1 = wy.s2 = wz.s1 = wz.s2 = T(0);
         }
-        // ---- gather at x^n
-        const Lin<T> nx_ = lin(gx, g.nx), ny_ = lin(gy, g.ny), nz_ = lin(gz, g.nz);
-        const Lin<T> sx = lin(gx - T(0.5), g.nx), sy = lin(gy - T(0.5), g.ny),
-                     sz = lin(gz - T(0.5), g.nz);
-        const T Ex = gather(a.E[0], g, sx, ny_, nz_);
-        const T Ey = gather(a.E[1], g, nx_, sy, nz_);
-        const T Ez = gather(a.E[2], g, nx_, ny_, sz);
-        const T Bx = gather_mean(a.B0[0], a.B1[0], g, nx_, sy, sz);
-        const T By = gather_mean(a.B0[1], a.B1[1], g, sx, ny_, sz);
-        const T Bz = gather_mean(a.B0[2], a.B1[2], g, sx, sy, nz_);
-        // ---- Boris push u^{n-1/2} -> u^{n+1/2}
-        const T h = a.h;
-        const T umx = ux + h * Ex, umy = uy + h * Ey, umz = uz + h * Ez;
-        const T gm = sqrt(T(1) + umx * umx + umy * umy + umz * umz);
-        const T tx = h * Bx / gm, ty = h * By / gm, tz = h * Bz / gm;
-        const T t2 = tx * tx + ty * ty + tz * tz;
-        const T den = T(1) + t2;
-        const T sxv = T(2) * tx / den, syv = T(2) * ty / den, szv = T(2) * tz / den;
-        const T upx = umx + (umy * tz - umz * ty);
-        const T upy = umy + (umz * tx - umx * tz);
-        const T upz = umz + (umx * ty - umy * tx);
-        const T u1x = umx + (upy * szv - upz * syv) + h * Ex;
-        const T u1y = umy + (upz * sxv - upx * szv) + h * Ey;
-        const T u1z = umz + (upx * syv - upy * sxv) + h * Ez;
-        const T g1 = sqrt(T(1) + u1x * u1x + u1y * u1y + u1z * u1z);
-        const T x1 = x + a.dt * u1x / g1, y1 = y + a.dt * u1y / g1, z1 = z + a.dt * u1z / g1;
-        // ---- Esirkepov current J^{n+1/2} from x^n -> x^{n+1}
-        const Win<T> wx = window(gx, x1 * a.inv_dx[0]);
-        const Win<T> wy = window(gy, y1 * a.inv_dx[1]);
-        const Win<T> wz = window(gz, z1 * a.inv_dx[2]);
-        deposit_axis(a.J[0], g, wx, wy, wz, g.nx, g.ny, g.nz, 0, a.jscale[0]);
-        deposit_axis(a.J[1], g, wy, wx, wz, g.ny, g.nx, g.nz, 1, a.jscale[1]);
-        deposit_axis(a.J[2], g, wz, wx, wy, g.nz, g.nx, g.ny, 2, a.jscale[2]);
-        // ---- new state, positions wrapped into [0, L)
-        T xw = x1, yw = y1, zw = z1;
-        if (xw < T(0)) xw += a.L[0]; else if (xw >= a.L[0]) xw -= a.L[0];
-        if (yw < T(0)) yw += a.L[1]; else if (yw >= a.L[1]) yw -= a.L[1];
-        if (zw < T(0)) zw += a.L[2]; else if (zw >= a.L[2]) zw -= a.L[2];
-        a.x[0][p] = xw; a.x[1][p] = yw; a.x[2][p] = zw;
-        a.u[0][p] = u1x; a.u[1][p] = u1y; a.u[2][p] = u1z;
+        // ---- Esirkepov current: -dt J^{n+1/2} into E^{n+1}.  Every lane reaches these
+        // shuffles (no short-circuit evaluation around them): the warp is converged here.
+        const int s0x = __shfl_sync(FULL, wx.idx[0], 0);
+        const int s0y = __shfl_sync(FULL, wy.idx[0], 0);
+        const int s0z = __shfl_sync(FULL, wz.idx[0], 0);
+        const bool same = live && wx.idx[0] == s0x && wy.idx[0] == s0y && wz.idx[0] == s0z;
+        const bool uni = __all_sync(FULL, same);
+        if (uni || live) deposit(sink, wx, wy, wz, a.escale, uni);   // uni: the whole warp
+    }
+}
+
+// ghost cells of the padded layout (periodic images of owned cells), per plane: the PY rows
+// below and above the owned rows (whole padded rows) and the PX columns left and right of
+// every owned row.  Each thread copies one ghost cell of each of the three arrays from its
+// owned image.
+template <typename T>
+__global__ void __launch_bounds__(THREADS)
+refresh_kernel(Geom g, T* __restrict__ F0, T* __restrict__ F1, T* __restrict__ F2) {
+    const long long rows_cells = 2LL * PY * g.nxp;        // ghost rows of one plane
+    const long long per_plane = rows_cells + 2LL * PX * g.ny;
+    const long long total = per_plane * g.nz;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int k = (int)(t / per_plane);
+        const long long r = t - (long long)k * per_plane;
+        int ip, jp;
+        if (r < rows_cells) {
+            const int row = (int)(r / g.nxp);
+            ip = (int)(r - (long long)row * g.nxp);
+            jp = row < PY ? row : g.ny + row;   // rows 0 .. PY-1 and ny+PY .. ny+2PY-1
+        } else {
+            const int q = (int)(r - rows_cells);
+            const int row = q / (2 * PX), col = q - row * (2 * PX);
+            jp = PY + row;
+            ip = col < PX ? col : g.nx + col;   // columns 0 .. PX-1 and nx+PX .. nx+2PX-1
+        }
+        const int i = wrapi(ip - PX, g.nx), j = wrapi(jp - PY, g.ny);
+        const long long dst = ((long long)k * g.nyp + jp) * g.nxp + ip;
+        const long long src = pidx(g, i, j, k);
+        F0[dst] = F0[src];
+        F1[dst] = F1[src];
+        F2[dst] = F2[src];
     }
 }
 
 template <typename T>
 __global__ void __launch_bounds__(THREADS)
 rho_kernel(Geom g, const T* __restrict__ x0, const T* __restrict__ x1, const T* __restrict__ x2,
-           long long n, T ix, T iy, T iz, T scale, T* __restrict__ rho, int* err) {
-    const T lim = T(1073741824);
+           long long n, T ix, T iy, T iz, T Lx, T Ly, T Lz, T scale, T* __restrict__ rho, int* err) {
     for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n;
          p += (long long)gridDim.x * blockDim.x) {
-        const T gx = x0[p] * ix, gy = x1[p] * iy, gz = x2[p] * iz;
-        if (!finite3(gx, gy, gz) || fabs(gx) > lim || fabs(gy) > lim || fabs(gz) > lim) {
+        T x = x0[p], y = x1[p], z = x2[p];
+        if (!finite3(x, y, z)) {
             atomicOr(err, 2);
             continue;
         }
-        const Lin<T> a = lin(gx, g.nx), b = lin(gy, g.ny), c = lin(gz, g.nz);
+        x = into_box(x, Lx); y = into_box(y, Ly); z = into_box(z, Lz);
+        const Lin<T> a = lin(x * ix, g.nx), b = lin(y * iy, g.ny), c = lin(z * iz, g.nz);
 #pragma unroll
         for (int ia = 0; ia < 2; ++ia)
 #pragma unroll
@@ -248,18 +391,28 @@ void launch_pic_push(const PushArgs<T>& a, cudaStream_t st) {
 }
 
 template <typename T>
+void launch_refresh_images(const Geom& g, T* F0, T* F1, T* F2, cudaStream_t st) {
+    const long long total = (2LL * PY * g.nxp + 2LL * PX * g.ny) * g.nz;
+    picd::refresh_kernel<T><<<picd::blocks_for(total), picd::THREADS, 0, st>>>(g, F0, F1, F2);
+}
+
+template <typename T>
 void launch_deposit_rho(const Geom& g, const T* const x[3], long long n, const T inv_dx[3],
-                        T scale, T* rho, int* err, cudaStream_t st) {
+                        const T L[3], T scale, T* rho, int* err, cudaStream_t st) {
     if (n <= 0) return;
     picd::rho_kernel<T><<<picd::blocks_for(n), picd::THREADS, 0, st>>>(
-        g, x[0], x[1], x[2], n, inv_dx[0], inv_dx[1], inv_dx[2], scale, rho, err);
+        g, x[0], x[1], x[2], n, inv_dx[0], inv_dx[1], inv_dx[2], L[0], L[1], L[2], scale, rho, err);
 }
 
 template void launch_pic_push<float>(const PushArgs<float>&, cudaStream_t);
 template void launch_pic_push<double>(const PushArgs<double>&, cudaStream_t);
+template void launch_refresh_images<float>(const Geom&, float*, float*, float*, cudaStream_t);
+template void launch_refresh_images<double>(const Geom&, double*, double*, double*, cudaStream_t);
 template void launch_deposit_rho<float>(const Geom&, const float* const[3], long long,
-                                        const float[3], float, float*, int*, cudaStream_t);
+                                        const float[3], const float[3], float, float*, int*,
+                                        cudaStream_t);
 template void launch_deposit_rho<double>(const Geom&, const double* const[3], long long,
-                                         const double[3], double, double*, int*, cudaStream_t);
+                                         const double[3], const double[3], double, double*, int*,
+                                         cudaStream_t);
 
 }  // namespace fdtd

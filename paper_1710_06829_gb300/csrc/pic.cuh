@@ -13,23 +13,28 @@ void launch_faraday_oop(const Geom& g, const Mult<T>& m, FieldSet<T> in, FieldSe
                         const T* sponge_y, const T* sponge_z, cudaStream_t st);
 
 // Ampere step with a current on the grid: out.E = in.E + dt (D x Bh - J) (Yee stencil), with
-// Bh = the B arrays of `bset` and J three padded arrays at the E positions; images included;
-// sponge as for the Faraday half.
+// Bh = the B arrays of `bset` and J three padded arrays at the E positions (J NULL: no
+// current); images included; sponge as for the Faraday half.
 template <typename T>
 void launch_ampere_current(const Geom& g, const Mult<T>& m, FieldSet<T> in, FieldSet<T> bset,
                            const T* const J[3], FieldSet<T> out, const T* sponge_y,
                            const T* sponge_z, cudaStream_t st);
 
-// Per-particle gather (E^n, B^n = (B0 + B1) / 2), Boris push, move and Esirkepov current
-// added into J (padded, three arrays).  Particles whose position or momentum is not finite
-// (or whose position is beyond 2^30 cells) are left unchanged and raise bit 2 of *err.
+// Per-particle gather (E^n, B^n = (B0 + B1) / 2), Boris push, move, and Esirkepov's current as
+// -dt J^{n+1/2} added into the owned cells of Eout (E^{n+1} without the current, padded; times
+// the absorbing-layer factor when spy is non-NULL); launch_refresh_images then brings its
+// ghosts up to date.  Positions outside the box are wrapped first.
+// Particles whose position or momentum is not finite are left unchanged and raise bit 2 of
+// *err.
 template <typename T>
 struct PushArgs {
     Geom g;
     const T* E[3];
     const T* B0[3];
     const T* B1[3];
-    T* J[3];
+    T* Eout[3];
+    const T* spy;
+    const T* spz;
     T* x[3];
     T* u[3];
     long long n;
@@ -37,15 +42,21 @@ struct PushArgs {
     T L[3];
     T h;           // (q/m) dt / 2
     T dt;
-    T jscale[3];   // -q / (dt dx_b dx_c) for J_a
+    T escale[3];   // q / (dx_b dx_c): the cumulative shape change of axis a times this is -dt J_a
     int* err;
 };
 template <typename T>
 void launch_pic_push(const PushArgs<T>& a, cudaStream_t st);
 
-// rho at the nodes (first-order shape) added into a dense [nz][ny][nx] array.
+// Copy every owned cell that has periodic images (the ghosts of the padded layout) to them,
+// for three padded arrays.
+template <typename T>
+void launch_refresh_images(const Geom& g, T* F0, T* F1, T* F2, cudaStream_t st);
+
+// rho at the nodes (first-order shape) added into a dense [nz][ny][nx] array; positions outside
+// the box [0, L) are wrapped first, non-finite ones raise bit 2 of *err and add nothing.
 template <typename T>
 void launch_deposit_rho(const Geom& g, const T* const x[3], long long n, const T inv_dx[3],
-                        T scale, T* rho, int* err, cudaStream_t st);
+                        const T L[3], T scale, T* rho, int* err, cudaStream_t st);
 
 }  // namespace fdtd
