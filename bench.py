@@ -36,6 +36,13 @@ BYTES_ADJ32 = 60.0    # lambda (6) read+write, E^n (3) read
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of the FP32 step
 # kernel at 256^3, from one ncu capture of that kernel version; reported only
 # while the kernel sources still hash to the captured version.
+# PIC cycle workload (the paper's Sec. 6 setting): 512 x 256 x 256 FP32, 16-cell absorbing
+# layers on +-y, +-z, a gamma = 10 electron bunch of 2^22 macro-particles along +x
+PIC_SHAPE = (512, 256, 256)
+PIC_N = 1 << 22
+PIC_WORKLOAD = ("PIC cycle 512x256x256 FP32, 16-cell absorbing layers on y and z, extended "
+                "stencil (seeded coefficient set 0), Courant 0.95; gamma=10 electron bunch, "
+                "2^22 macro-particles, sigma_par=4, sigma_perp=8 cells, along +x")
 STEP_TRAFFIC = {"sources_sha256_16": "bb21314f498fdbad", "bytes_per_launch": 834147584}
 STEP_SOURCES = ["fdtd_fused32.cu", "fdtd_seg.cuh", "fdtd_tma.cuh", "fdtd_internal.cuh"]
 
@@ -65,7 +72,7 @@ def parse():
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--n", type=int, default=N_CELLS)
-    p.add_argument("--part", default="all", choices=["all", "fwd32", "adj32"],
+    p.add_argument("--part", default="all", choices=["all", "fwd32", "adj32", "pic"],
                    help="fwd32: run only the FP32 forward steps (profiling driver); prints a "
                         "short line that is not a bench result")
     return p.parse_args()
@@ -294,6 +301,39 @@ def time_events(fn, steps, stream):
     return start.elapsed_time(stop) / 1e3
 
 
+def pic_leg(S, inputs, beta, delta, dt, stream, world, args):
+    """PIC cycles (fdtd_pic_step) of the bunch workload: whole cycles timed with CUDA events,
+    and the same cycles without particles (the field part) for the split."""
+    import numpy as np
+    import torch
+    nx, ny, nz = PIC_SHAPE
+    sm = S.Simulation(PIC_SHAPE, [1, 1, 1], dt, beta, delta, dims=3, dtype="f32",
+                      absorb_cells=16, absorb_sigma=0.5, stream=stream)
+    sm.set_state([None] * 6)
+    x, u = inputs.gaussian_bunch(PIC_N, (64.0, ny / 2, nz / 2), (4.0, 8.0), (1.0, 0.0, 0.0), 10.0,
+                                 seed=21)
+    sp = S.Species(torch.from_numpy(x.astype(np.float32)).cuda(),
+                   torch.from_numpy(u.astype(np.float32)).cuda(), -1.0 / PIC_N, -1.0)
+    empty = S.Species(torch.empty((3, 0), device="cuda"), torch.empty((3, 0), device="cuda"), 0.0,
+                      1.0)
+    for _ in range(max(3, args.warmup)):
+        sm.pic_step(1, [sp])
+    k = max(5, min(args.steps, 50))
+    t_cyc = barrier_max(time_events(lambda: sm.pic_step(1, [sp]), k, stream), world)
+    t_fld = barrier_max(time_events(lambda: sm.pic_step(1, [empty]), k, stream), world)
+    sm.sync()
+    sm.close()
+    cells = float(nx * ny * nz)
+    return {"value": world * PIC_N * k / t_cyc / 1e9, "unit": "Gparticle-pushes/s",
+            "workload": PIC_WORKLOAD, "particles": PIC_N, "cycles": k,
+            "ms_per_cycle": t_cyc / k * 1e3, "field_ms_per_cycle": t_fld / k * 1e3,
+            "push_ms_per_cycle": (t_cyc - t_fld) / k * 1e3,
+            "push_rate": {"value": PIC_N * k / max(t_cyc - t_fld, 1e-12) / 1e9,
+                          "unit": "Gparticle-pushes/s", "note": "gather + Boris + Esirkepov "
+                          "deposit alone (cycle minus the particle-free cycle)"},
+            "cycle_cell_rate": {"value": world * cells * k / t_cyc / 1e9, "unit": "Gcell-updates/s"}}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -348,6 +388,14 @@ def run_ours(args):
         sm.close()
         if rank == 0:
             print(json.dumps({"part": "adj32", "gcells_per_s": adj, "ms_per_step": t_adj / seg * 1e3}))
+        return
+
+    # --- PIC cycle: bunch of macro-particles on the 512 x 256 x 256 absorbing-layer grid
+    pic = pic_leg(S, inputs, beta, delta, dt, stream, world, args)
+    if args.part == "pic":
+        sm.close()
+        if rank == 0:
+            print(json.dumps({"part": "pic", **pic}))
         return
 
     # --- end to end through the C ABI with host buffers: upload, 20 steps, download
@@ -416,6 +464,7 @@ def run_ours(args):
                      "frac": achieved / peak, "traffic": step_traffic(n),
                      "traffic_unit": "DRAM bytes per launch (ncu)", "peak_kind": peak_kind,
                      "kernel": "forward step (48 B/cell-update algorithmic)"},
+        "pic": pic,
         "e2e": {"value": e2e, "unit": "Gcell-updates/s",
                 "h2d_bytes_per_step": int(6 * 4 * cells), "d2h_bytes_per_step": int(6 * 4 * cells),
                 "step": f"host upload + {n_inner} leapfrog steps + host download",

@@ -232,6 +232,43 @@ __device__ __forceinline__ void deposit(const Sink<T>& sink, const Win<T>& wx, c
     }
 }
 
+// first-order weights of one axis relative to the node f0 - 1 of a warp whose particles all
+// have old node f0: l0 (0 or 1) is the local index of the lower of the two nodes used
+template <typename T>
+struct Loc {
+    int l0;
+    T w0, w1;
+};
+
+template <typename T>
+__device__ __forceinline__ Loc<T> loc(T gc, int f0) {
+    const T f = floor(gc);
+    Loc<T> l;
+    l.w1 = gc - f;
+    l.w0 = T(1) - l.w1;
+    l.l0 = (int)f - (f0 - 1);
+    return l;
+}
+
+// interpolation from the 3 x 3 x 3 node block of the warp (lane a + 3 b + 9 c holds node
+// (f0x - 1 + a, f0y - 1 + b, f0z - 1 + c) of the component in `val`); the same weights and
+// summation order as gather()
+template <typename T>
+__device__ __forceinline__ T interp27(T val, const Loc<T>& a, const Loc<T>& b, const Loc<T>& c) {
+    T out = T(0);
+#pragma unroll
+    for (int ia = 0; ia < 2; ++ia)
+#pragma unroll
+        for (int ib = 0; ib < 2; ++ib)
+#pragma unroll
+            for (int ic = 0; ic < 2; ++ic) {
+                const T w = (ia ? a.w1 : a.w0) * (ib ? b.w1 : b.w0) * (ic ? c.w1 : c.w0);
+                const int lane = (a.l0 + ia) + 3 * (b.l0 + ib) + 9 * (c.l0 + ic);
+                out += w * __shfl_sync(FULL, val, lane);
+            }
+    return out;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(THREADS, 2) push_kernel(PushArgs<T> a) {
     const Geom& g = a.g;
@@ -256,19 +293,54 @@ __global__ void __launch_bounds__(THREADS, 2) push_kernel(PushArgs<T> a) {
                 x = into_box(x, a.L[0]); y = into_box(y, a.L[1]); z = into_box(z, a.L[2]);
             }
         }
-        Win<T> wx, wy, wz;
-        if (live) {
-            const T gx = x * a.inv_dx[0], gy = y * a.inv_dx[1], gz = z * a.inv_dx[2];
-            // ---- gather at x^n
+        const T gx = x * a.inv_dx[0], gy = y * a.inv_dx[1], gz = z * a.inv_dx[2];
+        const int fx = live ? (int)floor(gx) : 0, fy = live ? (int)floor(gy) : 0,
+                  fz = live ? (int)floor(gz) : 0;
+        // warp-uniform: all 32 particles live in one cell (same old node on every axis).  Every
+        // lane reaches these shuffles (no short-circuit evaluation around them).
+        const int f0x = __shfl_sync(FULL, fx, 0);
+        const int f0y = __shfl_sync(FULL, fy, 0);
+        const int f0z = __shfl_sync(FULL, fz, 0);
+        const bool same = live && fx == f0x && fy == f0y && fz == f0z;
+        const bool uni = __all_sync(FULL, same);
+        // ---- gather at x^n
+        T Ex = 0, Ey = 0, Ez = 0, Bx = 0, By = 0, Bz = 0;
+        if (uni) {
+            // the warp loads the 3 x 3 x 3 node block once (27 lanes, one value per array) and
+            // every particle interpolates from it by shuffles
+            const int l = threadIdx.x & 31;
+            T v0 = 0, v1 = 0, v2 = 0, v3 = 0, v4 = 0, v5 = 0;
+            if (l < 27) {
+                const long long o = pidx(g, wrapi(f0x - 1 + l % 3, g.nx),
+                                         wrapi(f0y - 1 + (l / 3) % 3, g.ny),
+                                         wrapi(f0z - 1 + l / 9, g.nz));
+                v0 = a.E[0][o]; v1 = a.E[1][o]; v2 = a.E[2][o];
+                v3 = T(0.5) * (a.B0[0][o] + a.B1[0][o]);
+                v4 = T(0.5) * (a.B0[1][o] + a.B1[1][o]);
+                v5 = T(0.5) * (a.B0[2][o] + a.B1[2][o]);
+            }
+            const Loc<T> nxl = loc(gx, f0x), nyl = loc(gy, f0y), nzl = loc(gz, f0z);
+            const Loc<T> sxl = loc(gx - T(0.5), f0x), syl = loc(gy - T(0.5), f0y),
+                         szl = loc(gz - T(0.5), f0z);
+            Ex = interp27(v0, sxl, nyl, nzl);
+            Ey = interp27(v1, nxl, syl, nzl);
+            Ez = interp27(v2, nxl, nyl, szl);
+            Bx = interp27(v3, nxl, syl, szl);
+            By = interp27(v4, sxl, nyl, szl);
+            Bz = interp27(v5, sxl, syl, nzl);
+        } else if (live) {
             const Lin<T> nx_ = lin(gx, g.nx), ny_ = lin(gy, g.ny), nz_ = lin(gz, g.nz);
             const Lin<T> sx = lin(gx - T(0.5), g.nx), sy = lin(gy - T(0.5), g.ny),
                          sz = lin(gz - T(0.5), g.nz);
-            const T Ex = gather(a.E[0], g, sx, ny_, nz_);
-            const T Ey = gather(a.E[1], g, nx_, sy, nz_);
-            const T Ez = gather(a.E[2], g, nx_, ny_, sz);
-            const T Bx = gather_mean(a.B0[0], a.B1[0], g, nx_, sy, sz);
-            const T By = gather_mean(a.B0[1], a.B1[1], g, sx, ny_, sz);
-            const T Bz = gather_mean(a.B0[2], a.B1[2], g, sx, sy, nz_);
+            Ex = gather(a.E[0], g, sx, ny_, nz_);
+            Ey = gather(a.E[1], g, nx_, sy, nz_);
+            Ez = gather(a.E[2], g, nx_, ny_, sz);
+            Bx = gather_mean(a.B0[0], a.B1[0], g, nx_, sy, sz);
+            By = gather_mean(a.B0[1], a.B1[1], g, sx, ny_, sz);
+            Bz = gather_mean(a.B0[2], a.B1[2], g, sx, sy, nz_);
+        }
+        Win<T> wx, wy, wz;
+        if (live) {
             // ---- Boris push u^{n-1/2} -> u^{n+1/2}
             const T h = a.h;
             const T umx = ux + h * Ex, umy = uy + h * Ey, umz = uz + h * Ez;
@@ -303,13 +375,8 @@ __global__ void __launch_bounds__(THREADS, 2) push_kernel(PushArgs<T> a) {
             }
             wx.s1 = wx.s2 = wy.s1 = wy.s2 = wz.s1 = wz.s2 = T(0);
         }
-        // ---- Esirkepov current: -dt J^{n+1/2} into E^{n+1}.  Every lane reaches these
-        // shuffles (no short-circuit evaluation around them): the warp is converged here.
-        const int s0x = __shfl_sync(FULL, wx.idx[0], 0);
-        const int s0y = __shfl_sync(FULL, wy.idx[0], 0);
-        const int s0z = __shfl_sync(FULL, wz.idx[0], 0);
-        const bool same = live && wx.idx[0] == s0x && wy.idx[0] == s0y && wz.idx[0] == s0z;
-        const bool uni = __all_sync(FULL, same);
+        // ---- Esirkepov current: -dt J^{n+1/2} into E^{n+1} (the windows start at the old
+        // node - 1, so a uniform warp shares them)
         if (uni || live) deposit(sink, wx, wy, wz, a.escale, uni);   // uni: the whole warp
     }
 }

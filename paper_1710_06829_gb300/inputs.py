@@ -224,8 +224,9 @@ def gaussian_bunch(n, center, sigma, direction, gamma, seed, dx=(1.0, 1.0, 1.0))
     """n macro-particles of a relativistic bunch: positions Gaussian about `center` with
     widths sigma = (sigma_parallel, sigma_perp) (in cells, parallel = along `direction`),
     all with momentum u = sqrt(gamma^2 - 1) along the unit vector `direction`.  The draw is
-    sorted by cell (x fastest after z, y) so that neighbouring particles share cells.
-    Arrays (3, n), float64, positions in the units of dx."""
+    ordered by z cell, then y cell, then x position, so that neighbouring particles share
+    cells, and still do after the bunch has drifted along x.  Arrays (3, n), float64,
+    positions in the units of dx."""
     rng = np.random.default_rng(seed)
     d = np.asarray(direction, dtype=np.float64)
     d = d / np.linalg.norm(d)
@@ -238,7 +239,7 @@ def gaussian_bunch(n, center, sigma, direction, gamma, seed, dx=(1.0, 1.0, 1.0))
     r = rng.standard_normal((3, n))
     cells = (np.asarray(center, dtype=np.float64)[:, None] + s_par * r[0] * d[:, None]
              + s_perp * r[1] * e1[:, None] + s_perp * r[2] * e2[:, None])
-    order = np.lexsort((np.floor(cells[0]), np.floor(cells[1]), np.floor(cells[2])))
+    order = np.lexsort((cells[0], np.floor(cells[1]), np.floor(cells[2])))
     x = cells[:, order] * np.asarray(dx, dtype=np.float64)[:, None]
     u = np.repeat((math.sqrt(gamma * gamma - 1.0) * d)[:, None], n, axis=1)
     return x, u

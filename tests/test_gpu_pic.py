@@ -2,7 +2,9 @@
 
 * Several cycles with extended coefficients, random fields and two mobile species: fields
   and particles element by element against ``oracle.pic`` (FP64 and FP32, with and without
-  the absorbing layer), on grids that are not multiples of any tile.
+  the absorbing layer), on grids that are not multiples of any tile; scattered particles
+  (every lane on its own) and particles in blocks of 32 sharing a cell (the warp-shared
+  gather and deposit), with a ragged last warp.
 * Gauss's law D.E - rho (Eq. divE with App. A's continuity equation) stays at its initial
   value on the GPU, FP64 and FP32.
 * Closed forms on the GPU path: the Boris rotation angle in a uniform B; a cold plasma
@@ -52,10 +54,28 @@ def _case(shape_xyz, seed, dx=(1.0, 1.1, 0.9), frac=0.8):
     return beta, delta, list(dx), dt, fields, species
 
 
-@pytest.mark.parametrize("dtype,absorb", [("f64", 0), ("f32", 0), ("f64", 3)])
-def test_pic_cycles_match_oracle(dtype, absorb):
+def _clustered(shape_xyz, dx, seed, ncell=37, per=32, extra=13):
+    """Particles in blocks of `per` sharing one cell (the warp-uniform path of the push), in
+    cell order, plus a ragged block of `extra`; momenta small enough to stay near the cell."""
+    rng = np.random.default_rng(seed)
+    cells = np.stack([rng.integers(0, shape_xyz[a], ncell) for a in range(3)])
+    base = np.repeat(cells, per, axis=1)
+    x = (base + rng.uniform(0.02, 0.98, base.shape)) * np.asarray(dx)[:, None]
+    xe, _ = inputs.particles(shape_xyz, dx, extra, seed=seed + 1)
+    x = np.concatenate([x, xe], axis=1)
+    u = 0.3 * rng.standard_normal(x.shape)
+    return x, u
+
+
+@pytest.mark.parametrize("dtype,absorb,clustered", [("f64", 0, False), ("f32", 0, False),
+                                                    ("f64", 3, False), ("f64", 0, True),
+                                                    ("f32", 2, True)])
+def test_pic_cycles_match_oracle(dtype, absorb, clustered):
     shape = (20, 13, 11)
     beta, delta, dx, dt, fields, species = _case(shape, seed=11)
+    if clustered:
+        xc, uc = _clustered(shape, dx, seed=12)
+        species = [(xc, uc, -0.02, -1.0)] + species[1:]
     npd = TD[dtype][1]
     # the oracle starts from the values the device holds
     fields = [f.astype(npd).astype(np.float64) for f in fields]
