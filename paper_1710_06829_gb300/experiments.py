@@ -2,6 +2,7 @@
 
     python -m paper_1710_06829_gb300.experiments dispersion      # 256^3 plane waves
     python -m paper_1710_06829_gb300.experiments cherenkov       # 512x256x256 rigid bunch
+    python -m paper_1710_06829_gb300.experiments cherenkov_pic   # macro-particle bunch, 0/45 deg
     python -m paper_1710_06829_gb300.experiments differentiable  # 128^3 checkpointed gradient
     python -m paper_1710_06829_gb300.experiments optimize        # coefficient minimisation
     python -m paper_1710_06829_gb300.experiments reproduce       # Table 1 schemes by SLSQP on GPU
@@ -185,6 +186,81 @@ def cherenkov(nsteps=2000, every=50, shape=(512, 256, 256)):
     ys, ms = out["series"].get("yee"), out["series"].get("min1_lift")
     if ys and ms and ys["mean_energy_second_half"] and ms["mean_energy_second_half"] is not None:
         out["ratio_min1_over_yee"] = ms["mean_energy_second_half"] / ys["mean_energy_second_half"]
+    return out
+
+
+# ---------------------------------------------------------------- Cherenkov with macro-particles
+
+def cherenkov_pic(travel=320.0, sample=16.0, n=1 << 21, sigma=(1.0, 2.0)):
+    """Sec. 6 with macro-particles (fdtd_pic_step): a short gamma = 10 electron bunch (sigma_par,
+    sigma_perp = `sigma` cells, unit total charge: short enough to have spectral content at the
+    grid-scale wavenumbers where a scheme's phase velocity drops below the bunch's) launched
+    along theta = 0 and 45 degrees from x,
+    for Yee and the isotropic 3D lifts of Table 1's Lehe and min.1 coefficient sets.  Every
+    scheme runs until the bunch has travelled `travel` cells (its own dt, 0.95 of its limit)
+    and is sampled every `sample` cells of travel: field energy in the x-window
+    [x_c - 150, x_c - 20) behind the bunch, 16 cells from the absorbing layers.  The bunch
+    starts on a neutralising background with zero fields (Gauss's law holds from the first
+    step); the background's static field stays near the start: samples whose window begins
+    within 48 cells of it are left out."""
+    dx = [1.0, 1.0, 1.0]
+    gam = 10.0
+    v = math.sqrt(1 - 1 / gam ** 2)
+    schemes = {"yee": (np.zeros((3, 3)), np.zeros(3)),
+               "lehe_lift": inputs.isotropic_theta(-0.021, 0.0, 0.125, 0.0),
+               "min1_lift": inputs.isotropic_theta(-0.125, -0.125, 0.110, 0.110)}
+    cases = {0: {"shape": (512, 256, 256), "start": (64.0, 128.0, 128.0), "dir": (1.0, 0.0, 0.0)},
+             45: {"shape": (384, 384, 128), "start": (48.0, 48.0, 64.0), "dir": (1.0, 1.0, 0.0)}}
+    out = {"experiment": "cherenkov_pic", "dtype": "f32", "travel_cells": travel,
+           "sample_every_cells": sample, "particles": n,
+           "bunch": {"gamma": gam, "sigma_par": sigma[0], "sigma_perp": sigma[1], "q_total": -1.0},
+           "absorber": {"cells": 16, "sigma": 0.1}, "courant": "0.95 of dt_max",
+           "window": "[x_c-150, x_c-20), margin 16; samples whose window starts within 48 cells "
+                     "of the start excluded", "angles": {}}
+    for ang, case in cases.items():
+        nx, ny, nz = case["shape"]
+        d = np.asarray(case["dir"]) / np.linalg.norm(case["dir"])
+        res = {"grid": list(case["shape"]), "direction": d.tolist(), "series": {}}
+        x0, u0 = inputs.gaussian_bunch(n, case["start"], sigma, case["dir"], gam, seed=31)
+        for name, (beta, delta) in schemes.items():
+            dtm, smin, _ = S.dt_max(beta, delta, dx, 3)
+            if smin < 0:
+                res["series"][name] = {"skipped": "not admissible (min S < 0)"}
+                continue
+            dt = 0.95 * dtm
+            sm = S.Simulation(case["shape"], dx, dt, beta, delta, dims=3, dtype="f32",
+                              absorb_cells=16, absorb_sigma=0.1)
+            sm.set_state([None] * 6)
+            sp = S.Species(torch.from_numpy(x0.astype(np.float32)).cuda(),
+                           torch.from_numpy(u0.astype(np.float32)).cuda(), -1.0 / n, -1.0)
+            series = []
+            steps = 0
+            t0 = time.perf_counter()
+            for k in range(1, int(travel // sample) + 1):
+                target = int(round(k * sample / (v * dt)))
+                sm.pic_step(target - steps, [sp])
+                steps = target
+                dist = v * dt * steps
+                xc = case["start"][0] + dist * d[0]
+                x_lo = int(math.floor(xc - 150))
+                if x_lo - case["start"][0] >= 48:
+                    e = float(sm.energy(x_lo % nx, 130, 16).item())
+                    series.append({"step": steps, "travel": dist, "energy_behind": e})
+            torch.cuda.synchronize()
+            el = time.perf_counter() - t0
+            sm.sync()
+            sm.close()
+            late = [r["energy_behind"] for r in series if r["travel"] >= travel / 2]
+            res["series"][name] = {"dt": dt, "steps": steps, "seconds": el,
+                                   "cycles_per_s": steps / el,
+                                   "mean_energy_second_half": float(np.mean(late)) if late else None,
+                                   "energy": series}
+        y = res["series"]["yee"].get("mean_energy_second_half")
+        for name in ("lehe_lift", "min1_lift"):
+            m = res["series"][name].get("mean_energy_second_half")
+            if y and m is not None:
+                res[f"ratio_{name}_over_yee"] = m / y
+        out["angles"][str(ang)] = res
     return out
 
 
@@ -425,8 +501,8 @@ def group(n=256):
 
 def main():
     p = argparse.ArgumentParser()
-    p.add_argument("what", choices=["dispersion", "cherenkov", "differentiable", "optimize",
-                                    "reproduce", "group"])
+    p.add_argument("what", choices=["dispersion", "cherenkov", "cherenkov_pic", "differentiable",
+                                    "optimize", "reproduce", "group"])
     p.add_argument("--mu", type=float, default=0.0)
     p.add_argument("--iters", type=int, default=50)
     a = p.parse_args()
@@ -434,6 +510,8 @@ def main():
         r = dispersion()
     elif a.what == "cherenkov":
         r = cherenkov()
+    elif a.what == "cherenkov_pic":
+        r = cherenkov_pic()
     elif a.what == "differentiable":
         r = differentiable()
     elif a.what == "reproduce":
