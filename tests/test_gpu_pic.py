@@ -207,6 +207,31 @@ def test_cold_plasma_oscillation_matches_oracle():
     sm.close()
 
 
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_deposit_rho_matches_oracle(dtype):
+    """Charge density at the nodes (first-order shape), two species, positions anywhere in the
+    box and a few outside it (wrapped), on a ragged grid."""
+    shape = (20, 13, 11)
+    dx = [1.0, 1.1, 0.9]
+    sm = S.Simulation(shape, dx, 0.3, np.zeros((3, 3)), np.zeros(3), dims=3, dtype=dtype)
+    xe, ue = inputs.particles(shape, dx, 1001, seed=41)
+    xi, ui = inputs.particles(shape, dx, 333, seed=42)
+    Lbox = np.array([shape[a] * dx[a] for a in range(3)])[:, None]
+    xi[:, :7] += Lbox * np.array([[1], [-1], [2]])          # outside the box: wrapped first
+    npd = TD[dtype][1]
+    xe, xi = xe.astype(npd).astype(np.float64), xi.astype(npd).astype(np.float64)
+    sps = [S.Species(_to_dev(xe, dtype), _to_dev(ue, dtype), -0.7, -1.0),
+           S.Species(_to_dev(xi, dtype), _to_dev(ui, dtype), 1.3, 0.01)]
+    got = sm.deposit_rho(sps).double().cpu().numpy()
+    sm.sync()
+    grid = (shape[2], shape[1], shape[0])
+    ref = (P.deposit_rho(P.Particles(xe, ue, -0.7, -1.0), grid, dx) +
+           P.deposit_rho(P.Particles(P.wrap_positions(xi, grid, dx), ui, 1.3, 0.01), grid, dx))
+    tol = 1e-13 if dtype == "f64" else 1e-5
+    assert np.max(np.abs(got - ref)) <= tol * np.max(np.abs(ref))
+    sm.close()
+
+
 # ---- the bunch workload at full size ----------------------------------------------------
 
 BUNCH_SHAPE = (512, 256, 256)
