@@ -183,27 +183,29 @@ template <typename T>
 __global__ void adjoint_E_kernel(Geom g, Mult<T> m, FieldSet<T> lam, const T* __restrict__ spy,
                                  const T* __restrict__ spz) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = blockIdx.y, k = blockIdx.z;
     if (i >= g.nx) return;
-    const long long c = pidx(g, i, j, k);
-    const long long Y = g.nxp;
-    const long long zp1 = zoff_a(g, k, 1), zm1 = zoff_a(g, k, -1), zm2 = zoff_a(g, k, -2);
-    const T* mux = lam.c[3];
-    const T* muy = lam.c[4];
-    const T* muz = lam.c[5];
+    for (int k = blockIdx.z; k < g.nz; k += gridDim.z)
+        for (int j = blockIdx.y; j < g.ny; j += gridDim.y) {
+            const long long c = pidx(g, i, j, k);
+            const long long Y = g.nxp;
+            const long long zp1 = zoff_a(g, k, 1), zm1 = zoff_a(g, k, -1), zm2 = zoff_a(g, k, -2);
+            const T* mux = lam.c[3];
+            const T* muy = lam.c[4];
+            const T* muz = lam.c[5];
 #define DTX(G) dstarT_at(G, c, -1, -2, 1, Y, -Y, zp1, zm1, m.cA[0], m.cD[0], m.cB[0][1], m.cB[0][2])
 #define DTY(G) dstarT_at(G, c, -Y, -2 * Y, Y, 1, -1, zp1, zm1, m.cA[1], m.cD[1], m.cB[1][0], m.cB[1][2])
 #define DTZ(G) dstarT_at(G, c, zm1, zm2, zp1, 1, -1, Y, -Y, m.cA[2], m.cD[2], m.cB[2][0], m.cB[2][1])
-    const T s0 = sp_at(g, spy, spz, j, k);
-    const T ex = s0 * lam.c[0][c] + (DTY(muz) - DTZ(muy));
-    const T ey = s0 * lam.c[1][c] + (DTZ(mux) - DTX(muz));
-    const T ez = s0 * lam.c[2][c] + (DTX(muy) - DTY(mux));
+            const T s0 = sp_at(g, spy, spz, j, k);
+            const T ex = s0 * lam.c[0][c] + (DTY(muz) - DTZ(muy));
+            const T ey = s0 * lam.c[1][c] + (DTZ(mux) - DTX(muz));
+            const T ez = s0 * lam.c[2][c] + (DTX(muy) - DTY(mux));
 #undef DTX
 #undef DTY
 #undef DTZ
-    store_images_a(g, lam.c[0], i, j, k, ex);
-    store_images_a(g, lam.c[1], i, j, k, ey);
-    store_images_a(g, lam.c[2], i, j, k, ez);
+            store_images_a(g, lam.c[0], i, j, k, ex);
+            store_images_a(g, lam.c[1], i, j, k, ey);
+            store_images_a(g, lam.c[2], i, j, k, ez);
+        }
 }
 
 template <typename T>
@@ -217,7 +219,8 @@ void launch_adjoint_B_v0(const Geom& g, const Mult<T>& m, FieldSet<T> lam, const
 template <typename T>
 void launch_adjoint_E_v0(const Geom& g, const Mult<T>& m, FieldSet<T> lam, const T* sponge_y,
                          const T* sponge_z, cudaStream_t st) {
-    dim3 blk(128), grd((g.nx + 127) / 128, g.ny, g.nz);
+    dim3 blk(128), grd((g.nx + 127) / 128, (unsigned)(g.ny < 65535 ? g.ny : 65535),
+                        (unsigned)(g.nz < 65535 ? g.nz : 65535));   // j, k loop in the kernel
     adjoint_E_kernel<T><<<grd, blk, 0, st>>>(g, m, lam, sponge_y, sponge_z);
 }
 

@@ -58,31 +58,33 @@ template <typename T>
 __global__ void faraday_v0_kernel(Geom g, Mult<T> m, FieldSet<T> s, const T* __restrict__ spy,
                                   const T* __restrict__ spz) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = blockIdx.y, k = blockIdx.z;
     if (i >= g.nx) return;
-    const long long c = pidx(g, i, j, k);
-    const long long Y = g.nxp;
-    const long long zp1 = zoff(g, k, 1), zm1 = zoff(g, k, -1), zp2 = zoff(g, k, 2);
-    const T* Ex = s.c[0];
-    const T* Ey = s.c[1];
-    const T* Ez = s.c[2];
-    // D*_x: axis x, transverse y then z;  D*_y: axis y, transverse x then z;  D*_z: axis z.
+    for (int k = blockIdx.z; k < g.nz; k += gridDim.z)
+        for (int j = blockIdx.y; j < g.ny; j += gridDim.y) {
+            const long long c = pidx(g, i, j, k);
+            const long long Y = g.nxp;
+            const long long zp1 = zoff(g, k, 1), zm1 = zoff(g, k, -1), zp2 = zoff(g, k, 2);
+            const T* Ex = s.c[0];
+            const T* Ey = s.c[1];
+            const T* Ez = s.c[2];
+            // D*_x: axis x, transverse y then z;  D*_y: axis y, transverse x then z;  D*_z: axis z.
 #define DSX(F) dstar_at(F, c, 1, 2, -1, Y, -Y, zp1, zm1, m.cA[0], m.cD[0], m.cB[0][1], m.cB[0][2])
 #define DSY(F) dstar_at(F, c, Y, 2 * Y, -Y, 1, -1, zp1, zm1, m.cA[1], m.cD[1], m.cB[1][0], m.cB[1][2])
 #define DSZ(F) dstar_at(F, c, zp1, zp2, zm1, 1, -1, Y, -Y, m.cA[2], m.cD[2], m.cB[2][0], m.cB[2][1])
-    T bx = s.c[3][c] + (DSZ(Ey) - DSY(Ez));
-    T by = s.c[4][c] + (DSX(Ez) - DSZ(Ex));
-    T bz = s.c[5][c] + (DSY(Ex) - DSX(Ey));
+            T bx = s.c[3][c] + (DSZ(Ey) - DSY(Ez));
+            T by = s.c[4][c] + (DSX(Ez) - DSZ(Ex));
+            T bz = s.c[5][c] + (DSY(Ex) - DSX(Ey));
 #undef DSX
 #undef DSY
 #undef DSZ
-    if (spy != nullptr) {
-        const T f = spy[j] * spz[k];
-        bx *= f; by *= f; bz *= f;
-    }
-    store_images(g, s.c[3], i, j, k, bx);
-    store_images(g, s.c[4], i, j, k, by);
-    store_images(g, s.c[5], i, j, k, bz);
+            if (spy != nullptr) {
+                const T f = spy[j] * spz[k];
+                bx *= f; by *= f; bz *= f;
+            }
+            store_images(g, s.c[3], i, j, k, bx);
+            store_images(g, s.c[4], i, j, k, by);
+            store_images(g, s.c[5], i, j, k, bz);
+        }
 }
 
 template <typename T>
@@ -90,42 +92,46 @@ __global__ void ampere_v0_kernel(Geom g, Mult<T> m, FieldSet<T> s, const T* __re
                                  const T* __restrict__ spz, const T* __restrict__ jyz,
                                  const T* __restrict__ jx_row) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = blockIdx.y, k = blockIdx.z;
     if (i >= g.nx) return;
-    const long long c = pidx(g, i, j, k);
-    const long long Y = g.nxp;
-    const long long zm1 = zoff(g, k, -1);
-    const T* Bx = s.c[3];
-    const T* By = s.c[4];
-    const T* Bz = s.c[5];
-    T ex = ampere_comp(s.c[0][c], Bz[c], Bz[c - Y], By[c], By[c + zm1], m.cE[1], m.cE[2]);
-    T ey = ampere_comp(s.c[1][c], Bx[c], Bx[c + zm1], Bz[c], Bz[c - 1], m.cE[2], m.cE[0]);
-    T ez = ampere_comp(s.c[2][c], By[c], By[c - 1], Bx[c], Bx[c - Y], m.cE[0], m.cE[1]);
-    if (jx_row != nullptr) {
-        // J_x^{n+1/2} at (i+1/2, j, k): x-profile x transverse profile, both tabulated.
-        const T jx = (jx_row[i] * jyz[j]) * jyz[g.ny + k];
-        ex = fma(-m.dt, jx, ex);
-    }
-    if (spy != nullptr) {
-        const T f = spy[j] * spz[k];
-        ex *= f; ey *= f; ez *= f;
-    }
-    store_images(g, s.c[0], i, j, k, ex);
-    store_images(g, s.c[1], i, j, k, ey);
-    store_images(g, s.c[2], i, j, k, ez);
+    for (int k = blockIdx.z; k < g.nz; k += gridDim.z)
+        for (int j = blockIdx.y; j < g.ny; j += gridDim.y) {
+            const long long c = pidx(g, i, j, k);
+            const long long Y = g.nxp;
+            const long long zm1 = zoff(g, k, -1);
+            const T* Bx = s.c[3];
+            const T* By = s.c[4];
+            const T* Bz = s.c[5];
+            T ex = ampere_comp(s.c[0][c], Bz[c], Bz[c - Y], By[c], By[c + zm1], m.cE[1], m.cE[2]);
+            T ey = ampere_comp(s.c[1][c], Bx[c], Bx[c + zm1], Bz[c], Bz[c - 1], m.cE[2], m.cE[0]);
+            T ez = ampere_comp(s.c[2][c], By[c], By[c - 1], Bx[c], Bx[c - Y], m.cE[0], m.cE[1]);
+            if (jx_row != nullptr) {
+                // J_x^{n+1/2} at (i+1/2, j, k): x-profile x transverse profile, both tabulated.
+                const T jx = (jx_row[i] * jyz[j]) * jyz[g.ny + k];
+                ex = fma(-m.dt, jx, ex);
+            }
+            if (spy != nullptr) {
+                const T f = spy[j] * spz[k];
+                ex *= f; ey *= f; ez *= f;
+            }
+            store_images(g, s.c[0], i, j, k, ex);
+            store_images(g, s.c[1], i, j, k, ey);
+            store_images(g, s.c[2], i, j, k, ez);
+        }
 }
 
 template <typename T>
 void launch_faraday_v0(const Geom& g, const Mult<T>& m, FieldSet<T> s, const T* sponge_y,
                        const T* sponge_z, cudaStream_t st) {
-    dim3 blk(128), grd((g.nx + 127) / 128, g.ny, g.nz);
+    dim3 blk(128), grd((g.nx + 127) / 128, (unsigned)(g.ny < 65535 ? g.ny : 65535),
+                        (unsigned)(g.nz < 65535 ? g.nz : 65535));   // j, k loop in the kernel
     faraday_v0_kernel<T><<<grd, blk, 0, st>>>(g, m, s, sponge_y, sponge_z);
 }
 
 template <typename T>
 void launch_ampere_v0(const Geom& g, const Mult<T>& m, FieldSet<T> s, const T* sponge_y,
                       const T* sponge_z, const T* jyz, const T* jx_row, cudaStream_t st) {
-    dim3 blk(128), grd((g.nx + 127) / 128, g.ny, g.nz);
+    dim3 blk(128), grd((g.nx + 127) / 128, (unsigned)(g.ny < 65535 ? g.ny : 65535),
+                        (unsigned)(g.nz < 65535 ? g.nz : 65535));   // j, k loop in the kernel
     ampere_v0_kernel<T><<<grd, blk, 0, st>>>(g, m, s, sponge_y, sponge_z, jyz, jx_row);
 }
 
@@ -139,30 +145,32 @@ template <typename T>
 __global__ void faraday_oop_kernel(Geom g, Mult<T> m, FieldSet<T> in, FieldSet<T> out,
                                    const T* __restrict__ spy, const T* __restrict__ spz) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = blockIdx.y, k = blockIdx.z;
     if (i >= g.nx) return;
-    const long long c = pidx(g, i, j, k);
-    const long long Y = g.nxp;
-    const long long zp1 = zoff(g, k, 1), zm1 = zoff(g, k, -1), zp2 = zoff(g, k, 2);
-    const T* Ex = in.c[0];
-    const T* Ey = in.c[1];
-    const T* Ez = in.c[2];
+    for (int k = blockIdx.z; k < g.nz; k += gridDim.z)
+        for (int j = blockIdx.y; j < g.ny; j += gridDim.y) {
+            const long long c = pidx(g, i, j, k);
+            const long long Y = g.nxp;
+            const long long zp1 = zoff(g, k, 1), zm1 = zoff(g, k, -1), zp2 = zoff(g, k, 2);
+            const T* Ex = in.c[0];
+            const T* Ey = in.c[1];
+            const T* Ez = in.c[2];
 #define DSX(F) dstar_at(F, c, 1, 2, -1, Y, -Y, zp1, zm1, m.cA[0], m.cD[0], m.cB[0][1], m.cB[0][2])
 #define DSY(F) dstar_at(F, c, Y, 2 * Y, -Y, 1, -1, zp1, zm1, m.cA[1], m.cD[1], m.cB[1][0], m.cB[1][2])
 #define DSZ(F) dstar_at(F, c, zp1, zp2, zm1, 1, -1, Y, -Y, m.cA[2], m.cD[2], m.cB[2][0], m.cB[2][1])
-    T bx = in.c[3][c] + (DSZ(Ey) - DSY(Ez));
-    T by = in.c[4][c] + (DSX(Ez) - DSZ(Ex));
-    T bz = in.c[5][c] + (DSY(Ex) - DSX(Ey));
+            T bx = in.c[3][c] + (DSZ(Ey) - DSY(Ez));
+            T by = in.c[4][c] + (DSX(Ez) - DSZ(Ex));
+            T bz = in.c[5][c] + (DSY(Ex) - DSX(Ey));
 #undef DSX
 #undef DSY
 #undef DSZ
-    if (spy != nullptr) {
-        const T f = spy[j] * spz[k];
-        bx *= f; by *= f; bz *= f;
-    }
-    store_images(g, out.c[3], i, j, k, bx);
-    store_images(g, out.c[4], i, j, k, by);
-    store_images(g, out.c[5], i, j, k, bz);
+            if (spy != nullptr) {
+                const T f = spy[j] * spz[k];
+                bx *= f; by *= f; bz *= f;
+            }
+            store_images(g, out.c[3], i, j, k, bx);
+            store_images(g, out.c[4], i, j, k, by);
+            store_images(g, out.c[5], i, j, k, bz);
+        }
 }
 
 template <typename T>
@@ -171,35 +179,38 @@ __global__ void ampere_current_kernel(Geom g, Mult<T> m, FieldSet<T> in, FieldSe
                                       const T* __restrict__ Jz, FieldSet<T> out,
                                       const T* __restrict__ spy, const T* __restrict__ spz) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = blockIdx.y, k = blockIdx.z;
     if (i >= g.nx) return;
-    const long long c = pidx(g, i, j, k);
-    const long long Y = g.nxp;
-    const long long zm1 = zoff(g, k, -1);
-    const T* Bx = bset.c[3];
-    const T* By = bset.c[4];
-    const T* Bz = bset.c[5];
-    T ex = ampere_comp(in.c[0][c], Bz[c], Bz[c - Y], By[c], By[c + zm1], m.cE[1], m.cE[2]);
-    T ey = ampere_comp(in.c[1][c], Bx[c], Bx[c + zm1], Bz[c], Bz[c - 1], m.cE[2], m.cE[0]);
-    T ez = ampere_comp(in.c[2][c], By[c], By[c - 1], Bx[c], Bx[c - Y], m.cE[0], m.cE[1]);
-    if (Jx != nullptr) {
-        ex = fma(-m.dt, Jx[c], ex);
-        ey = fma(-m.dt, Jy[c], ey);
-        ez = fma(-m.dt, Jz[c], ez);
-    }
-    if (spy != nullptr) {
-        const T f = spy[j] * spz[k];
-        ex *= f; ey *= f; ez *= f;
-    }
-    store_images(g, out.c[0], i, j, k, ex);
-    store_images(g, out.c[1], i, j, k, ey);
-    store_images(g, out.c[2], i, j, k, ez);
+    for (int k = blockIdx.z; k < g.nz; k += gridDim.z)
+        for (int j = blockIdx.y; j < g.ny; j += gridDim.y) {
+            const long long c = pidx(g, i, j, k);
+            const long long Y = g.nxp;
+            const long long zm1 = zoff(g, k, -1);
+            const T* Bx = bset.c[3];
+            const T* By = bset.c[4];
+            const T* Bz = bset.c[5];
+            T ex = ampere_comp(in.c[0][c], Bz[c], Bz[c - Y], By[c], By[c + zm1], m.cE[1], m.cE[2]);
+            T ey = ampere_comp(in.c[1][c], Bx[c], Bx[c + zm1], Bz[c], Bz[c - 1], m.cE[2], m.cE[0]);
+            T ez = ampere_comp(in.c[2][c], By[c], By[c - 1], Bx[c], Bx[c - Y], m.cE[0], m.cE[1]);
+            if (Jx != nullptr) {
+                ex = fma(-m.dt, Jx[c], ex);
+                ey = fma(-m.dt, Jy[c], ey);
+                ez = fma(-m.dt, Jz[c], ez);
+            }
+            if (spy != nullptr) {
+                const T f = spy[j] * spz[k];
+                ex *= f; ey *= f; ez *= f;
+            }
+            store_images(g, out.c[0], i, j, k, ex);
+            store_images(g, out.c[1], i, j, k, ey);
+            store_images(g, out.c[2], i, j, k, ez);
+        }
 }
 
 template <typename T>
 void launch_faraday_oop(const Geom& g, const Mult<T>& m, FieldSet<T> in, FieldSet<T> out,
                         const T* sponge_y, const T* sponge_z, cudaStream_t st) {
-    dim3 blk(128), grd((g.nx + 127) / 128, g.ny, g.nz);
+    dim3 blk(128), grd((g.nx + 127) / 128, (unsigned)(g.ny < 65535 ? g.ny : 65535),
+                        (unsigned)(g.nz < 65535 ? g.nz : 65535));   // j, k loop in the kernel
     faraday_oop_kernel<T><<<grd, blk, 0, st>>>(g, m, in, out, sponge_y, sponge_z);
 }
 
@@ -207,7 +218,8 @@ template <typename T>
 void launch_ampere_current(const Geom& g, const Mult<T>& m, FieldSet<T> in, FieldSet<T> bset,
                            const T* const J[3], FieldSet<T> out, const T* sponge_y,
                            const T* sponge_z, cudaStream_t st) {
-    dim3 blk(128), grd((g.nx + 127) / 128, g.ny, g.nz);
+    dim3 blk(128), grd((g.nx + 127) / 128, (unsigned)(g.ny < 65535 ? g.ny : 65535),
+                        (unsigned)(g.nz < 65535 ? g.nz : 65535));   // j, k loop in the kernel
     const T* Jx = J ? J[0] : nullptr;
     const T* Jy = J ? J[1] : nullptr;
     const T* Jz = J ? J[2] : nullptr;
