@@ -182,9 +182,9 @@ __device__ __forceinline__ Win<T> pick_win(int m, const Win<T>& a, const Win<T>&
 // window vanishes) and the other two axes b < c the weights; escale[a] = q / (dx_b dx_c)
 // turns the cumulative sum into -dt J_a.  `uni` (warp-uniform): every lane of the warp is
 // live with the same windows, so each face value is summed over the warp by shuffles and
-// lane 0 adds it once; otherwise every lane adds its own values.  The axis and b loops stay
-// rolled (operands picked by selects) to keep the kernel's code small: fully unrolled, the
-// reduction sites overflowed the instruction cache.
+// lane 0 adds it once; otherwise every lane adds its own values.  The axis, b and c loops stay
+// rolled (operands picked by selects) to keep the kernel's code small: unrolled, the
+// reduction sites made the kernel instruction-cache bound.
 template <typename T>
 __device__ __forceinline__ void deposit(const Sink<T>& sink, const Win<T>& wx, const Win<T>& wy,
                                         const Win<T>& wz, const T escale[3], bool uni) {
@@ -203,13 +203,14 @@ __device__ __forceinline__ void deposit(const Sink<T>& sink, const Win<T>& wx, c
             const T s0b = wb.S0(mb);
             const T dsb = pick4(mb, wb.dS[0], wb.dS[1], wb.dS[2], wb.dS[3]);
             const int ib = pick4(mb, wb.idx[0], wb.idx[1], wb.idx[2], wb.idx[3]);
-#pragma unroll
+#pragma unroll 1
             for (int mc = 0; mc < 4; ++mc) {
                 const T s0c = wc.S0(mc);
-                const T f = s0b * s0c + T(0.5) * dsb * s0c + T(0.5) * s0b * wc.dS[mc] +
-                            third * dsb * wc.dS[mc];
+                const T dsc = pick4(mc, wc.dS[0], wc.dS[1], wc.dS[2], wc.dS[3]);
+                const T f = s0b * s0c + T(0.5) * dsb * s0c + T(0.5) * s0b * dsc +
+                            third * dsb * dsc;
                 if (uni ? !__any_sync(FULL, f != T(0)) : f == T(0)) continue;
-                const int ic = wc.idx[mc];
+                const int ic = pick4(mc, wc.idx[0], wc.idx[1], wc.idx[2], wc.idx[3]);
                 T cum = T(0);
 #pragma unroll
                 for (int ma = 0; ma < 3; ++ma) {
