@@ -324,7 +324,14 @@ def pic_leg(S, inputs, beta, delta, dt, stream, world, args):
     sm.sync()
     sm.close()
     cells = float(nx * ny * nz)
+    peak, peak_kind = peaks()
+    t_push = max(t_cyc - t_fld, 1e-12) / k
+    push_gbs = 48.0 * PIC_N / t_push / 1e9   # particle state read + written, FP32
     return {"value": world * PIC_N * k / t_cyc / 1e9, "unit": "Gparticle-pushes/s",
+            "push_roofline": {"bound": "latency (gathers) and same-address reductions in L2, "
+                                       "not HBM", "algorithmic_bytes_per_push": 48,
+                              "achieved": push_gbs, "peak": peak, "unit": "GB/s",
+                              "frac": push_gbs / peak, "peak_kind": peak_kind},
             "workload": PIC_WORKLOAD, "particles": PIC_N, "cycles": k,
             "ms_per_cycle": t_cyc / k * 1e3, "field_ms_per_cycle": t_fld / k * 1e3,
             "push_ms_per_cycle": (t_cyc - t_fld) / k * 1e3,
