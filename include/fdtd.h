@@ -61,6 +61,7 @@ extern "C" {
 /* sources */
 #define FDTD_SRC_NONE  0
 #define FDTD_SRC_BUNCH 1
+#define FDTD_SRC_DENSE 2
 
 /* dispersion-norm weights (Sec. 4 and Eq. norm_x_axis) */
 #define FDTD_W_UNIFORM 0   /* w = 1 */
@@ -85,14 +86,21 @@ typedef struct {
     double delta[3];
 } fdtd_coeffs;
 
-/* Rigid Gaussian charge moving along +x (stand-in for a PIC beam).  Its current
- * J_x^{n+1/2} is evaluated inside the E update from the cell-integrated
- * Gaussian so that the discrete continuity equation of App. A holds exactly. */
+/* Current J^{n+1/2} in Ampere's law (App. A update equations).
+ * FDTD_SRC_BUNCH: a rigid Gaussian charge moving along +x (stand-in for a PIC beam); its
+ *   J_x^{n+1/2} is evaluated inside the E update from the cell-integrated Gaussian so that
+ *   the discrete continuity equation of App. A holds exactly.  Uses q .. sigma_perp.
+ * FDTD_SRC_DENSE: a current given on the grid: J[a] is a device array, dense [nz][ny][nx], of
+ *   the handle's dtype holding J_a at the E_a positions (NULL = 0), borrowed for the call and
+ *   applied in every step of it (one call per step for a current that changes in time).  The
+ *   step forms E^{n+1} without the current and subtracts dt J (times the sponge factor) from
+ *   it, which Ampere's law's linearity in J makes the same update. */
 typedef struct {
-    int32_t kind;          /* FDTD_SRC_NONE or FDTD_SRC_BUNCH */
-    double q, v;           /* charge, speed (units of c) */
-    double x0, y0, z0;     /* centre at absolute step 0 (length units) */
+    int32_t kind;          /* FDTD_SRC_NONE, FDTD_SRC_BUNCH or FDTD_SRC_DENSE */
+    double q, v;           /* bunch: charge, speed (units of c) */
+    double x0, y0, z0;     /* bunch: centre at absolute step 0 (length units) */
     double sigma_par, sigma_perp;
+    const void* J[3];      /* dense: J_x, J_y, J_z (device) */
 } fdtd_source;
 
 /* Probe: squared misfit of one E component on the plane i = x_index against a

@@ -28,6 +28,7 @@ FDTD_MEM_DEVICE = 0
 FDTD_MEM_HOST = 1
 FDTD_SRC_NONE = 0
 FDTD_SRC_BUNCH = 1
+FDTD_SRC_DENSE = 2
 FDTD_W_UNIFORM = 0
 FDTD_W_CONE_X = 1
 FDTD_W_GAUSS_Y = 2
@@ -70,7 +71,7 @@ class fdtd_coeffs(C.Structure):
 class fdtd_source(C.Structure):
     _fields_ = [("kind", C.c_int32), ("q", C.c_double), ("v", C.c_double), ("x0", C.c_double),
                 ("y0", C.c_double), ("z0", C.c_double), ("sigma_par", C.c_double),
-                ("sigma_perp", C.c_double)]
+                ("sigma_perp", C.c_double), ("J", C.c_void_p * 3)]
 
 
 class fdtd_probe(C.Structure):

@@ -30,6 +30,9 @@ void set_error(const char* fmt, ...) {
 }
 
 template <typename T>
+void launch_current(const Geom& g, T* const E[3], const T* const J[3], T dt, const T* sponge_y,
+                    const T* sponge_z, cudaStream_t st);
+template <typename T>
 void launch_bunch_table(int nx, int n, double x0, double vdt, double inv_sig, double scale,
                         double dx, double Lx, long long step0, T* out, cudaStream_t st);
 void launch_disp_norm(const double alpha[3], const double beta[3][3], const double delta[3],
@@ -677,6 +680,7 @@ static int step_impl(fdtd_handle* h, int n, const fdtd_source* src, const fdtd_p
         spz = spy + g.ny;
     }
     const bool bunch = src && src->kind == FDTD_SRC_BUNCH && n > 0;
+    const bool dense = src && src->kind == FDTD_SRC_DENSE && n > 0;
     const T* jyz = nullptr;
     if (bunch) {
         int rc = upload_bunch_yz<T>(h, src);
@@ -721,6 +725,21 @@ static int step_impl(fdtd_handle* h, int n, const fdtd_source* src, const fdtd_p
             launch_ampere_v0<T>(g, m, fs, spy, spz, jyz, jrow, h->stream);
         }
         CK(cudaGetLastError());
+        if (dense) {
+            // Ampere's law is linear in J: E^{n+1} = (E^{n+1} without J) - dt J
+            FieldSet<T> now = fieldset<T>(h, h->cur);
+            T* E[3] = {now.c[0], now.c[1], now.c[2]};
+            const T* J[3] = {(const T*)src->J[0], (const T*)src->J[1], (const T*)src->J[2]};
+            launch_current<T>(g, E, J, (T)h->dt, spy, spz, h->stream);
+            CK(cudaGetLastError());
+            launch_refresh_images<T>(g, E[0], E[1], E[2], h->stream);
+            CK(cudaGetLastError());
+            // the fused kernel wrote this step's history snapshot before the current was added
+            if (record && fused) {
+                int rc = snapshot<T>(h, s + 1);
+                if (rc) return rc;
+            }
+        }
         h->step += 1;
         if (probe) {
             const T* tgt = (const T*)probe->target + (size_t)(h->step - 1) * g.ny * g.nz;
@@ -743,7 +762,8 @@ static int step_impl(fdtd_handle* h, int n, const fdtd_source* src, const fdtd_p
 int fdtd_step(fdtd_handle* h, int32_t n, const fdtd_source* src, const fdtd_probe* probe,
               double* loss_dev, int32_t record) {
     if (!h || n < 0) { set_error("fdtd_step: bad argument"); return FDTD_EINVAL; }
-    if (src && src->kind != FDTD_SRC_NONE && src->kind != FDTD_SRC_BUNCH) {
+    if (src && src->kind != FDTD_SRC_NONE && src->kind != FDTD_SRC_BUNCH &&
+        src->kind != FDTD_SRC_DENSE) {
         set_error("unknown source kind %d", src->kind);
         return FDTD_EINVAL;
     }

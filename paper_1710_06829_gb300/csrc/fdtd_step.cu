@@ -242,6 +242,42 @@ template void launch_ampere_current<double>(const Geom&, const Mult<double>&, Fi
                                             FieldSet<double>, const double*, const double*,
                                             cudaStream_t);
 
+// E += -dt J (times the absorbing-layer factor) at the owned cells, J dense [nz][ny][nx] at the E
+// positions (NULL components skipped); the caller refreshes the images afterwards.
+template <typename T>
+__global__ void current_kernel(Geom g, T* __restrict__ E0, T* __restrict__ E1, T* __restrict__ E2,
+                               const T* __restrict__ J0, const T* __restrict__ J1,
+                               const T* __restrict__ J2, T mdt, const T* __restrict__ spy,
+                               const T* __restrict__ spz) {
+    const long long n = (long long)g.nx * g.ny * g.nz;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(t % g.nx);
+        const long long r = t / g.nx;
+        const int j = (int)(r % g.ny);
+        const int k = (int)(r / g.ny);
+        const T f = spy != nullptr ? spy[j] * spz[k] : T(1);
+        const long long c = pidx(g, i, j, k);
+        if (J0 != nullptr) E0[c] += (mdt * J0[t]) * f;
+        if (J1 != nullptr) E1[c] += (mdt * J1[t]) * f;
+        if (J2 != nullptr) E2[c] += (mdt * J2[t]) * f;
+    }
+}
+
+template <typename T>
+void launch_current(const Geom& g, T* const E[3], const T* const J[3], T dt, const T* sponge_y,
+                    const T* sponge_z, cudaStream_t st) {
+    const long long n = (long long)g.nx * g.ny * g.nz;
+    long long b = (n + 255) / 256;
+    if (b > 152LL * 32) b = 152LL * 32;
+    current_kernel<T><<<(unsigned)b, 256, 0, st>>>(g, E[0], E[1], E[2], J[0], J[1], J[2], -dt,
+                                                  sponge_y, sponge_z);
+}
+template void launch_current<float>(const Geom&, float* const[3], const float* const[3], float,
+                                    const float*, const float*, cudaStream_t);
+template void launch_current<double>(const Geom&, double* const[3], const double* const[3], double,
+                                     const double*, const double*, cudaStream_t);
+
 template void launch_faraday_v0<float>(const Geom&, const Mult<float>&, FieldSet<float>,
                                        const float*, const float*, cudaStream_t);
 template void launch_faraday_v0<double>(const Geom&, const Mult<double>&, FieldSet<double>,

@@ -19,10 +19,13 @@
 // Ampere's law is linear in J, so the cycle first forms E^{n+1} without the current (the
 // vacuum step kernel) and the push adds -dt J^{n+1/2} into its owned cells: no current
 // array, no extra pass over the grid; a small kernel then copies the owned cells near the x
-// and y ends to their periodic images (the ghosts the next step reads).  Warps move through the particle array together; when all 32
-// lanes of a warp share the same deposit windows (a dense bunch whose particles share a
-// cell), each face value is summed over the warp by shuffles and added once, which removes
-// most same-address global reductions; otherwise every lane adds its own values.
+// and y ends to their periodic images (the ghosts the next step reads).
+//
+// Warps move through the particle array together.  When all 32 particles of a warp sit in one
+// cell (a dense bunch, particles kept in cell order), the warp loads the 3 x 3 x 3 node block
+// of each field once (27 lanes) and every particle interpolates from it by shuffles, and each
+// face value of the current is summed over the warp by shuffles before one global addition;
+// otherwise every lane gathers and adds on its own.
 #include <climits>
 #include <cmath>
 

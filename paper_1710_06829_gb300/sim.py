@@ -35,6 +35,19 @@ class Bunch:
         self.s = L.fdtd_source(L.FDTD_SRC_BUNCH, q, v, x0, y0, z0, sigma_par, sigma_perp)
 
 
+class DenseCurrent:
+    """A current J^{n+1/2} on the grid (see fdtd_source in include/fdtd.h): three device tensors
+    (nz, ny, nx) of the simulation's dtype (None = 0), applied in every step of a call."""
+
+    def __init__(self, Jx=None, Jy=None, Jz=None):
+        self.J = [None if t is None else t.contiguous() for t in (Jx, Jy, Jz)]
+        for t in self.J:
+            assert t is None or t.is_cuda
+        ptrs = (L.C.c_void_p * 3)(*[None if t is None else t.data_ptr() for t in self.J])
+        self.s = L.fdtd_source(L.FDTD_SRC_DENSE, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, ptrs)
+        self.dtype = next((t.dtype for t in self.J if t is not None), None)
+
+
 class Probe:
     """Probe-plane misfit of E_component at x = x_index against target[(steps), nz, ny]."""
 
@@ -135,6 +148,8 @@ class Simulation:
              record=False):
         if probe is not None and probe.target.dtype != self.tdtype:
             raise TypeError("probe target dtype does not match the simulation dtype")
+        if isinstance(source, DenseCurrent) and source.dtype not in (None, self.tdtype):
+            raise TypeError("current dtype does not match the simulation dtype")
         L.fdtd_step(self.h, n, source.s if source is not None else None,
                     probe.s if probe is not None else None,
                     loss.data_ptr() if loss is not None else None, 1 if record else 0)
