@@ -146,7 +146,7 @@ def cherenkov(nsteps=2000, every=50, shape=(512, 256, 256)):
                "min1_lift": inputs.isotropic_theta(-0.125, -0.125, 0.110, 0.110)}
     out = {"experiment": "cherenkov", "grid": list(shape), "dtype": "f32", "steps": nsteps,
            "bunch": {"q": 1.0, "v": 0.999, "sigma_par": 4, "sigma_perp": 8, "x0": x0},
-           "absorber": {"cells": 16, "sigma": 0.1},
+           "absorber": {"cells": 16, "sigma": 0.3},
            "window": "[x_c-192, x_c-20), margin 16; samples within 64 cells of x0 excluded",
            "courant": "0.95 of dt_max", "series": {}}
 
@@ -163,7 +163,7 @@ def cherenkov(nsteps=2000, every=50, shape=(512, 256, 256)):
             continue
         dt = 0.95 * dtm
         sm = S.Simulation(shape, dx, dt, beta, delta, dims=3, dtype="f32", absorb_cells=16,
-                          absorb_sigma=0.1)
+                          absorb_sigma=0.3)
         sm.set_state([None] * 6)
         bunch = S.Bunch(1.0, 0.999, x0, ny / 2, nz / 2, 4.0, 8.0)
         series = []
@@ -214,7 +214,7 @@ def cherenkov_pic(travel=320.0, sample=16.0, n=1 << 21, sigma=(1.0, 2.0)):
     out = {"experiment": "cherenkov_pic", "dtype": "f32", "travel_cells": travel,
            "sample_every_cells": sample, "particles": n,
            "bunch": {"gamma": gam, "sigma_par": sigma[0], "sigma_perp": sigma[1], "q_total": -1.0},
-           "absorber": {"cells": 16, "sigma": 0.1}, "courant": "0.95 of dt_max",
+           "absorber": {"cells": 16, "sigma": 0.3}, "courant": "0.95 of dt_max",
            "window": "[x_c-150, x_c-20), margin 16; samples whose window starts within 48 cells "
                      "of the start excluded", "angles": {}}
     for ang, case in cases.items():
@@ -229,7 +229,7 @@ def cherenkov_pic(travel=320.0, sample=16.0, n=1 << 21, sigma=(1.0, 2.0)):
                 continue
             dt = 0.95 * dtm
             sm = S.Simulation(case["shape"], dx, dt, beta, delta, dims=3, dtype="f32",
-                              absorb_cells=16, absorb_sigma=0.1)
+                              absorb_cells=16, absorb_sigma=0.3)
             sm.set_state([None] * 6)
             sp = S.Species(torch.from_numpy(x0.astype(np.float32)).cuda(),
                            torch.from_numpy(u0.astype(np.float32)).cuda(), -1.0 / n, -1.0)

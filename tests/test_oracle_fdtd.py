@@ -279,3 +279,35 @@ def test_packet_centroid_moves_at_group_velocity():
     v = np.polyfit(ts, xs, 1)[0]
     assert vg > 1.005                      # the set is superluminal at lambda = 16 ...
     assert abs(v / vg - 1) < 2e-4          # ... and the packet follows d omega / d k
+
+
+@pytest.mark.parametrize("sigma", [0.3, 0.5])
+@pytest.mark.parametrize("scheme", ["yee", "extended"])
+def test_sponge_reflects_and_transmits_below_1e3(sigma, scheme):
+    """The absorbing layer (a reading; the paper has none): a Gaussian pulse (width 8, wavelength
+    16) meets a 16-cell layer at normal incidence; after 300 time units the reflected energy
+    (back in the interior behind the start) and the energy that crossed both layers of the
+    periodic y axis (ahead of the start) are each below 1e-3 of the initial energy."""
+    ny, nx, L, dt = 400, 4, 16, 0.5
+    if scheme == "yee":
+        beta, delta = np.zeros((3, 3)), np.zeros(3)
+    else:
+        beta = np.array([[0, 0.05, 0.05], [0.05, 0, 0.02], [0.05, 0.02, 0]])
+        delta = np.array([-0.03, -0.03, -0.03])
+    c = F.Coeffs(beta, delta, [1, 1, 1], dt)
+    y = np.arange(ny).astype(float)
+    yc, w, lam = 200.0, 8.0, 16.0
+    prof = lambda yy: np.exp(-((yy - yc) / w) ** 2) * np.cos(2 * np.pi * (yy - yc) / lam)
+    Ex = np.repeat(prof(y)[None, :, None], nx, axis=2)
+    Bz = -np.repeat(prof(y + 0.5 + 0.5 * dt)[None, :, None], nx, axis=2)   # moving along +y
+    s = F.State([Ex, 0 * Ex, 0 * Ex], [0 * Ex, 0 * Ex, Bz])
+    sponge = np.ones((1, ny, nx)) * F.sponge_profile(ny, L, sigma)[None, :, None]
+    e0 = F.energy(s)
+    for _ in range(600):
+        F.step(s, c, None, sponge)
+    refl = np.zeros((1, ny, nx))
+    refl[:, 220:ny - L, :] = 1
+    trans = np.zeros((1, ny, nx))
+    trans[:, L:200, :] = 1
+    assert F.energy(s, refl) / e0 < 1e-3
+    assert F.energy(s, trans) / e0 < 1e-3
