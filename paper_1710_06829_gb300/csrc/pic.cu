@@ -274,7 +274,7 @@ __device__ __forceinline__ T interp27(T val, const Loc<T>& a, const Loc<T>& b, c
 }
 
 template <typename T>
-__global__ void __launch_bounds__(THREADS, 2) push_kernel(PushArgs<T> a) {
+__global__ void __launch_bounds__(THREADS, 4) push_kernel(PushArgs<T> a) {
     const Geom& g = a.g;
     Sink<T> sink;
     sink.g = g;
