@@ -386,3 +386,115 @@ def test_group_norm_gradient_vs_central_differences(dims, wkind, wparam):
         dm[i] -= h
         assert gd[i] == pytest.approx((F(b, dp, dt) - F(b, dm, dt)) / (2 * h), rel=1e-6, abs=1e-9)
     assert gdt == pytest.approx((F(b, d, dt + h) - F(b, d, dt - h)) / (2 * h), rel=1e-6, abs=1e-9)
+
+
+# ---------------------------------------------------------------- the cone weight (Sec. 4)
+# Sec. 4 weights the norm by a function that is non-zero only inside a cone of directions; the
+# oracle reads it as w = 1 where k_x >= |k| cos(theta) (a cone of half-angle theta about +x).
+# These pins check that reading against closed-form volumes and moments of the cone inside the
+# positive octant [0, pi]^dims, and the weighted norm against a quadrature in cone-adapted
+# coordinates that never evaluates the weight function.  For tan(theta) <= 1 the cone's cross
+# section at k_x is a quarter disk (3D) or a segment (2D) of radius k_x tan(theta) <= pi, which
+# stays inside the box.
+
+
+def _cone_sums(N, dims, theta, wfun=None):
+    """Midpoint sums of w, w k_x, w k_y over the box, with the oracle's grid and weight."""
+    wfun = wfun or (lambda KX, KY, KZ: D.weight(KX, KY, KZ, D.WEIGHT_CONE_X, theta, np.ones(3)))
+    KX, KY, KZ, vol = D.midpoint_grid(N, np.ones(3), dims)
+    w = wfun(KX, KY, KZ)
+    return w.sum() * vol, (w * KX).sum() * vol, (w * KY).sum() * vol
+
+
+def _cone_closed_forms(dims, theta):
+    """Volume, first moment along x and along y of the cone inside the box."""
+    t = math.tan(theta)
+    pi = math.pi
+    if dims == 3:
+        # quarter disk of radius R = k_x t: area pi R^2 / 4, moment of k_y = R^3 / 3
+        return pi / 4 * t * t * pi ** 3 / 3, pi / 4 * t * t * pi ** 4 / 4, t ** 3 / 3 * pi ** 4 / 4
+    # segment 0 <= k_y <= k_x t: length R, moment of k_y = R^2 / 2
+    return t * pi ** 2 / 2, t * pi ** 3 / 3, t * t * pi ** 3 / 6
+
+
+@pytest.mark.parametrize("dims,N,tol", [(2, (512, 512, 1), 1e-4), (3, (96, 96, 96), 5e-4)])
+@pytest.mark.parametrize("deg", [30.0, 20.0])
+def test_cone_weight_volume_and_moments_closed_form(dims, N, tol, deg):
+    th = math.radians(deg)
+    got = _cone_sums(N, dims, th)
+    ref = _cone_closed_forms(dims, th)
+    for g, r in zip(got, ref):
+        assert g == pytest.approx(r, rel=tol)
+    # the midpoint sums converge to the closed forms
+    coarse = _cone_sums(tuple(max(1, n // 4) for n in N), dims, th)
+    assert abs(got[0] - ref[0]) <= abs(coarse[0] - ref[0]) + 1e-12
+
+
+def _gauss_cone(f, theta, dims, n=64):
+    """Integral of f(kx, ky, kz) over the cone inside the box, by Gauss-Legendre in cone
+    coordinates: k_x in [0, pi]; 3D: k_y = r cos(phi), k_z = r sin(phi), r in [0, k_x t],
+    phi in [0, pi/2] (Jacobian r); 2D: k_y in [0, k_x t]."""
+    x, wq = np.polynomial.legendre.leggauss(n)
+    t = math.tan(theta)
+    kx = 0.5 * math.pi * (x + 1)
+    wkx = 0.5 * math.pi * wq
+    if dims == 2:
+        KX = kx[:, None]
+        R = KX * t
+        KY = 0.5 * R * (x[None, :] + 1)
+        W = wkx[:, None] * 0.5 * R * wq[None, :]
+        return float(np.sum(W * f(KX, KY, 0.0 * KX)))
+    KX = kx[:, None, None]
+    R = KX * t
+    r = 0.5 * R * (x[None, :, None] + 1)
+    phi = 0.25 * math.pi * (x[None, None, :] + 1)
+    W = wkx[:, None, None] * (0.5 * R * wq[None, :, None]) * (0.25 * math.pi * wq[None, None, :]) * r
+    return float(np.sum(W * f(KX, r * np.cos(phi), r * np.sin(phi))))
+
+
+@pytest.mark.parametrize("dims,N,tol", [(2, (1024, 1024, 1), 2e-4), (3, (128, 128, 128), 2e-3)])
+def test_cone_weighted_norm_matches_cone_quadrature(dims, N, tol):
+    """Eq. (norm) with the cone weight, on an anisotropic coefficient set (so the cone's axis
+    matters), against the same integral taken only over the cone."""
+    th = math.radians(30.0)
+    beta = np.zeros((3, 3))
+    delta = np.zeros(3)
+    beta[0, 1], beta[1, 0], delta[0], delta[1] = 0.11, -0.02, -0.09, -0.03
+    if dims == 3:
+        beta[0, 2], beta[2, 0], beta[1, 2], beta[2, 1], delta[2] = 0.05, 0.07, -0.04, 0.01, -0.06
+    dx = np.ones(3)
+    dt = 0.9 * D.dt_max(beta, delta, dx, dims)
+
+    def integrand(kx, ky, kz):
+        S = D.S_paper(kx, ky, kz, beta, delta, dx, dims)
+        return (D.omega_from_S(S, dt) - np.sqrt(kx * kx + ky * ky + kz * kz)) ** 2
+
+    ref = _gauss_cone(integrand, th, dims)
+    assert ref == pytest.approx(_gauss_cone(integrand, th, dims, n=96), rel=1e-10)
+    got = D.norm(beta, delta, dt, dx, N, dims, D.WEIGHT_CONE_X, th)
+    assert got == pytest.approx(ref, rel=tol)
+    # the same scheme weighted by a cone about +y gives a different value (the axis is pinned)
+    def swapped(kx, ky, kz):
+        return integrand(ky, kx, kz)
+    assert abs(_gauss_cone(swapped, th, dims) / ref - 1) > 20 * tol
+
+
+@pytest.mark.parametrize("mistake", ["axis_y", "sin_for_cos", "degrees", "strict_complement"])
+def test_cone_pins_catch_planted_mistakes(mistake):
+    """Plausible misreadings of the cone weight each fail the closed-form pins above."""
+    th = math.radians(30.0)
+
+    def wrong(KX, KY, KZ):
+        kn = np.sqrt(KX * KX + KY * KY + KZ * KZ)
+        if mistake == "axis_y":
+            return (KY >= kn * math.cos(th)).astype(np.float64)
+        if mistake == "sin_for_cos":
+            return (KX >= kn * math.sin(th)).astype(np.float64)
+        if mistake == "degrees":
+            return (KX >= kn * math.cos(30.0)).astype(np.float64)
+        return (KX < kn * math.cos(th)).astype(np.float64)
+
+    for dims, N in [(2, (256, 256, 1)), (3, (48, 48, 48))]:
+        got = _cone_sums(N, dims, th, wrong)
+        ref = _cone_closed_forms(dims, th)
+        assert max(abs(g / r - 1) for g, r in zip(got, ref)) > 0.05, (dims, mistake)
