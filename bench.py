@@ -72,9 +72,10 @@ def parse():
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--n", type=int, default=N_CELLS)
-    p.add_argument("--part", default="all", choices=["all", "fwd32", "adj32", "pic"],
-                   help="fwd32: run only the FP32 forward steps (profiling driver); prints a "
-                        "short line that is not a bench result")
+    p.add_argument("--part", default="all", choices=["all", "fwd32", "adj32", "pic", "fwd64", "norm"],
+                   help="run one leg only (profiling driver: fwd32, adj32, pic, fwd64 = the FP64 "
+                        "step, norm = the dispersion norm + gradient over the n^3 k-grid); prints "
+                        "a short line that is not a bench result")
     return p.parse_args()
 
 
@@ -218,10 +219,7 @@ def barrier(world):
 # ---------------------------------------------------------------------------- reference arm
 
 
-def cpu_oracle_rate(n_cells, budget_s=15.0):
-    """FP64 numpy oracle forward rate on this host (bounded sample: whole steps at full size)."""
-    import numpy as np
-
+def _oracle_setup(n_cells):
     from oracle import dispersion as D
     from oracle import fdtd as F
     from paper_1710_06829_gb300 import inputs
@@ -230,21 +228,53 @@ def cpu_oracle_rate(n_cells, budget_s=15.0):
     shape = (n_cells, n_cells, n_cells)
     kx = 2 * math.pi * round(n_cells / LAMBDA) / n_cells
     fields = inputs.plane_wave(shape, (kx, 0, 0), (0, 0, 1), [1, 1, 1])
-    s = F.State(fields[:3], fields[3:])
-    c = F.Coeffs(beta, delta, [1, 1, 1], dt)
+    return F.State(fields[:3], fields[3:]), F.Coeffs(beta, delta, [1, 1, 1], dt)
+
+
+def _oracle_worker(args):
+    """One process: whole FP64 oracle steps on its own copy of the workload until the budget
+    is spent (at least one step); returns (steps, seconds)."""
+    n_cells, budget_s, max_steps = args
+    from oracle import fdtd as F
+    s, c = _oracle_setup(n_cells)
     steps = 0
     t0 = time.perf_counter()
     while True:
         F.step(s, c)
         steps += 1
         el = time.perf_counter() - t0
-        if el >= budget_s or steps >= 20:
-            break
-    cells = float(n_cells) ** 3
-    del np
-    return {"value": steps * cells / el / 1e9, "unit": "Gcell-updates/s", "cores": 1,
-            "kind": "oracle",
-            "sample": f"{steps} FP64 numpy forward steps at {n_cells}^3 in {el:.1f} s (single thread)"}
+        if el >= budget_s or steps >= max_steps:
+            return steps, el
+
+
+def cpu_oracle_rate(n_cells, budget_s=12.0, n_all=128):
+    """FP64 numpy oracle forward rate on this host: one process on the full grid (whole steps,
+    bounded sample), and one process per host core, each stepping its own n_all^3 copy of the
+    workload (aggregate rate).  numpy's elementwise arithmetic is single-threaded, so one
+    process uses one core."""
+    import multiprocessing as mp
+    steps, el = _oracle_worker((n_cells, budget_s, 20))
+    one = steps * float(n_cells) ** 3 / el / 1e9
+    cores = os.cpu_count() or 1
+    env = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS")}
+    os.environ["OMP_NUM_THREADS"] = os.environ["OPENBLAS_NUM_THREADS"] = "1"
+    try:
+        with mp.get_context("spawn").Pool(cores) as pool:
+            res = pool.map(_oracle_worker, [(n_all, budget_s, 1000)] * cores)
+    finally:
+        for k, v in env.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    wall = max(e for _, e in res)
+    allc = sum(st for st, _ in res) * float(n_all) ** 3 / wall / 1e9
+    return {"value": allc, "unit": "Gcell-updates/s", "cores": cores, "kind": "oracle",
+            "sample": f"{cores} processes (one per host core), each stepping its own {n_all}^3 copy "
+                      f"of the workload with the FP64 numpy oracle for ~{budget_s:.0f} s",
+            "single_core": {"value": one, "unit": "Gcell-updates/s", "cores": 1,
+                            "sample": f"{steps} FP64 numpy oracle steps on the full {n_cells}^3 grid "
+                                      f"in {el:.1f} s, one process"}}
 
 
 def run_reference(args):
@@ -286,6 +316,15 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------------------- our arm
+
+
+REPEATS = 5   # each timed region is repeated; the median per-step time is reported
+
+
+def time_median(fn, steps, stream, repeats=REPEATS):
+    """Median over `repeats` CUDA-event timings of `steps` calls, and the individual times."""
+    ts = [time_events(fn, steps, stream) for _ in range(repeats)]
+    return statistics.median(ts), ts
 
 
 def time_events(fn, steps, stream):
@@ -362,6 +401,26 @@ def run_ours(args):
     fields = [torch.from_numpy(f.astype(np.float32)) for f in fields64]
     stream = torch.cuda.current_stream()
 
+    if args.part == "norm":
+        for _ in range(max(1, args.warmup)):
+            S.disp_norm(beta, delta, dt, [1, 1, 1], 3, (n, n, n))
+        t = time_events(lambda: S.disp_norm(beta, delta, dt, [1, 1, 1], 3, (n, n, n)), args.steps, stream)
+        if rank == 0:
+            print(json.dumps({"part": "norm", "gpoints_per_s": cells * args.steps / t / 1e9,
+                              "ms_per_call": t / args.steps * 1e3}))
+        return
+    if args.part == "fwd64":
+        sm64 = S.Simulation(shape, [1, 1, 1], dt, beta, delta, dims=3, dtype="f64", stream=stream)
+        sm64.set_state([torch.from_numpy(f) for f in fields64])
+        for _ in range(max(1, args.warmup)):
+            sm64.step(1)
+        t = time_events(lambda: sm64.step(1), args.steps, stream)
+        sm64.close()
+        if rank == 0:
+            print(json.dumps({"part": "fwd64", "gcells_per_s": cells * args.steps / t / 1e9,
+                              "ms_per_step": t / args.steps * 1e3}))
+        return
+
     # --- forward FP32
     sm = S.Simulation(shape, [1, 1, 1], dt, beta, delta, dims=3, dtype="f32", stream=stream)
     sm.set_state(fields)
@@ -370,7 +429,7 @@ def run_ours(args):
     barrier(world)
     with Clocks(local) as clk:
         clk.mark_start()
-        t_fwd = time_events(lambda: sm.step(1), args.steps, stream)
+        t_fwd, t_fwd_all = time_median(lambda: sm.step(1), args.steps, stream)
         clk.mark_end()
     t_fwd = barrier_max(t_fwd, world)
     fwd = world * cells * args.steps / t_fwd / 1e9
@@ -386,10 +445,12 @@ def run_ours(args):
     sm.set_adjoint([f for f in fields])
     grad = torch.zeros(12, dtype=torch.float64, device="cuda")
     sm.step_adjoint(2, grad)    # warm-up
-    sm.step(seg, record=True)
-    torch.cuda.synchronize()
-    t_adj = time_events(lambda: sm.step_adjoint(seg, grad), 1, stream)
-    t_adj = barrier_max(t_adj, world)
+    t_adj_all = []
+    for _ in range(REPEATS):    # each repetition reverses a freshly recorded segment
+        sm.step(seg, record=True)
+        torch.cuda.synchronize()
+        t_adj_all.append(time_events(lambda: sm.step_adjoint(seg, grad), 1, stream))
+    t_adj = barrier_max(statistics.median(t_adj_all), world)
     adj = world * cells * seg / t_adj / 1e9
     if args.part == "adj32":
         sm.close()
@@ -444,7 +505,7 @@ def run_ours(args):
     for _ in range(3):
         sm64.step(1)
     k64 = max(3, args.steps // 50)
-    t64 = barrier_max(time_events(lambda: sm64.step(1), k64, stream), world)
+    t64 = barrier_max(time_median(lambda: sm64.step(1), k64, stream)[0], world)
     fwd64 = world * cells * k64 / t64 / 1e9
     sm64.close()
 
@@ -463,6 +524,9 @@ def run_ours(args):
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "grid": [n, n, n], "l2": "inputs larger than L2 "
                    "(state 6 x 4 B x 256^3 = 403 MB per copy)", "parallelism": f"replicas x{world}"},
+        "timing": {"repeats": REPEATS, "forward_region_ms": [t * 1e3 for t in t_fwd_all],
+                   "adjoint_region_ms": [t * 1e3 for t in t_adj_all],
+                   "note": "value, adjoint and fp64_forward are medians over the repetitions"},
         "adjoint": {"value": adj, "unit": "Gcell-updates/s", "steps": seg,
                     "roofline_frac": BYTES_ADJ32 * cells * seg / t_adj / 1e9 / peak},
         "dispersion_norm": {"value": norm_rate, "unit": "Gpoint/s", "grid": [n, n, n],
@@ -480,7 +544,7 @@ def run_ours(args):
                         f"{e2e_reps} repetitions)",
                 "link_h2d_gbs": link_bytes / t_h2d / 1e9, "link_d2h_gbs": link_bytes / t_d2h / 1e9,
                 "ceiling": e2e_ceiling, "frac_of_ceiling": e2e / e2e_ceiling},
-        "gpu_launches": args.steps * (1 if (n % 64 == 0 and n % 8 == 0) else 2),
+        "gpu_launches": REPEATS * args.steps * (1 if (n % 64 == 0 and n % 8 == 0) else 2),
         "clocks": clk.summary(),
     }
     if world == 1:

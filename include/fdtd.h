@@ -305,9 +305,12 @@ int disp_omega_eval(const fdtd_coeffs* coeffs, double dt, const double dx[3], in
  * statically on each device (512 KiB, kept until the process exits).
  * Limit: N[i] <= 4096 on every used axis, else FDTD_EINVAL (use disp_norm_eval).
  * The first call on a device (with that device current) looks the area's
- * address up; make it before any stream capture.  All calls share the one area,
- * so calls that overlap on the GPU (different streams, no ordering) race; calls
- * ordered on one stream are safe.  No part of the area must start at zero. */
+ * address up; make it before any stream capture.  The address is looked up again
+ * after the device's context changes (for instance after cudaDeviceReset), which
+ * makes that call a set-up call too.  All calls share the one area, so calls that
+ * overlap on the GPU (different streams, no ordering) race; calls ordered on one
+ * stream are safe.  The area needs no clearing: every entry is written before it
+ * is read within a call. */
 int disp_norm_eval_noalloc(const fdtd_coeffs* coeffs, double dt, const double dx[3],
                            int32_t dims, const int32_t N[3], int32_t weight, double weight_param,
                            double* out, void* stream);

@@ -1267,8 +1267,9 @@ int disp_omega_eval(const fdtd_coeffs* coeffs, double dt, const double dx[3], in
 //
 // The host never uses the array's name as a device address: on the first call on
 // a device (with that device current) cudaGetSymbolAddress yields its address,
-// which is cached per device and passed to the kernels.  That first call is the
-// set-up; make it before capturing any stream into a graph.
+// which is cached per device (with the context it belongs to) and passed to the
+// kernels.  That first call is the set-up; make it before capturing any stream into
+// a graph.
 // ---------------------------------------------------------------------------
 
 namespace {
@@ -1279,7 +1280,33 @@ constexpr int kNoallocMaxDevices = 64;
 
 static __device__ __align__(256) double g_norm_scratch[kNoallocDoubles];
 
-static double* g_norm_scratch_addr[kNoallocMaxDevices];
+// The array's address on a device is fixed for the life of the device's context; resetting the
+// device (cudaDeviceReset) and creating a new primary context loads the module again, and the
+// array may then sit elsewhere.  So the cached address is kept together with the context it
+// was looked up in, and is looked up again whenever the current context differs.
+struct NoallocSlot {
+    void* ctx;
+    double* addr;
+};
+static NoallocSlot g_norm_scratch_slot[kNoallocMaxDevices];
+
+// the calling thread's current context (driver API through the runtime's entry-point lookup, so
+// the library needs no link against the driver library); nullptr when it cannot be queried
+void* current_context() {
+    using Fn = CUresult (*)(CUcontext*);
+    static Fn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<Fn>(p);
+    });
+    CUcontext c = nullptr;
+    if (fn == nullptr || fn(&c) != CUDA_SUCCESS) return nullptr;
+    return c;
+}
 
 int noalloc_scratch_address(double** out) {
     int dev = -1;
@@ -1292,9 +1319,11 @@ int noalloc_scratch_address(double** out) {
         set_error("disp_norm_eval_noalloc: device ordinal %d out of range", dev);
         return FDTD_EINVAL;
     }
+    void* ctx = current_context();
     static std::mutex mu;
     std::lock_guard<std::mutex> lock(mu);
-    if (g_norm_scratch_addr[dev] == nullptr) {
+    NoallocSlot& slot = g_norm_scratch_slot[dev];
+    if (slot.addr == nullptr || slot.ctx != ctx) {
         void* p = nullptr;
         e = cudaGetSymbolAddress(&p, g_norm_scratch);
         if (e != cudaSuccess || p == nullptr) {
@@ -1302,9 +1331,11 @@ int noalloc_scratch_address(double** out) {
                       cudaGetErrorString(e));
             return FDTD_ECUDA;
         }
-        g_norm_scratch_addr[dev] = static_cast<double*>(p);
+        // the context may only exist once the runtime has set it up for the lookup above
+        slot.ctx = ctx != nullptr ? ctx : current_context();
+        slot.addr = static_cast<double*>(p);
     }
-    *out = g_norm_scratch_addr[dev];
+    *out = slot.addr;
     return FDTD_OK;
 }
 

@@ -49,3 +49,23 @@ def admissible_theta(seed, dims=3):
         if smin >= 0:
             return beta, delta
         s += 1000
+
+
+def max_elem_err(a_list, b_list):
+    """Per component c: max_i |a_c[i] - b_c[i]| / max_i |b_c[i]|, and the worst element's index."""
+    out = []
+    for a, b in zip(a_list, b_list):
+        a = np.asarray(a, dtype=np.float64)
+        b = np.asarray(b, dtype=np.float64)
+        d = np.abs(a - b)
+        i = int(np.argmax(d))
+        out.append((float(d.flat[i]) / max(float(np.max(np.abs(b))), 1e-300),
+                    np.unravel_index(i, d.shape)))
+    return out
+
+
+def assert_elementwise(a_list, b_list, tol, what=""):
+    """Element-by-element check of every component: |a - b| <= tol * max|b| at every cell
+    (a seam, ghost-image or edge-tile error in one cell cannot hide in a whole-field norm)."""
+    for c, (err, idx) in enumerate(max_elem_err(a_list, b_list)):
+        assert err <= tol, f"{what} component {c}: max error {err:.3e} x max|ref| at (z, y, x) = {idx}"

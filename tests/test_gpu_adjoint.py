@@ -4,7 +4,7 @@ import math
 import numpy as np
 import pytest
 
-from gpu_util import admissible_theta, exact_coeffs, rel_l2, rounded_coeffs
+from gpu_util import admissible_theta, assert_elementwise, exact_coeffs, rel_l2, rounded_coeffs
 from oracle import dispersion as D
 from oracle import fdtd as F
 
@@ -68,6 +68,7 @@ def test_adjoint_fp64_matches_oracle(shape, sponge):
     lam, gb, gd = gpu_adjoint(shape, dx, dt, beta, delta, "f64", fields, lam0, n, probe, **kw)
     rlam, rgb, rgd = oracle_adjoint(exact_coeffs(beta, delta, dx, dt, 3), fields, lam0, n, sp, probe)
     assert rel_l2(lam, rlam) <= 1e-12
+    assert_elementwise(lam, rlam, 1e-11, str(shape))
     scale = max(np.abs(rgb).max(), np.abs(rgd).max())
     assert np.max(np.abs(gb - rgb)) <= 1e-11 * scale
     assert np.max(np.abs(gd - rgd)) <= 1e-11 * scale
@@ -175,6 +176,7 @@ def test_batched_2d_adjoint_gradient_is_the_sum_over_members():
         rl, gb, gd = oracle_adjoint(c, [f[k:k + 1] for f in fields], [f[k:k + 1] for f in lam0], n,
                                     None, (1, 7, tgt[:, k:k + 1, :]))
         assert rel_l2([x[k:k + 1] for x in lam], rl) <= 1e-12
+        assert_elementwise([x[k:k + 1] for x in lam], rl, 1e-11, f"member {k}")
         gb_sum += gb
         gd_sum += gd
     scale = max(np.abs(gb_sum).max(), np.abs(gd_sum).max())
@@ -205,6 +207,8 @@ def test_adjoint_fp32_staged_kernel_matches_oracle(shape, sponge):
     rlam, rgb, rgd = oracle_adjoint(rounded_coeffs(beta, delta, dx, dt, 3, np.float32), f64, l64, n,
                                     sp, (probe[0], probe[1], probe[2].astype(np.float64)))
     assert rel_l2(lam, rlam) <= 5e-6
+    # FP32 round-off of 6 reverse steps (with the probe source), cell by cell
+    assert_elementwise(lam, rlam, 2e-5, str(shape))
     scale = max(np.abs(rgb).max(), np.abs(rgd).max())
     assert np.max(np.abs(gb - rgb)) <= 2e-5 * scale
     assert np.max(np.abs(gd - rgd)) <= 2e-5 * scale

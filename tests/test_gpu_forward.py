@@ -4,7 +4,7 @@ import math
 import numpy as np
 import pytest
 
-from gpu_util import admissible_theta, exact_coeffs, rel_l2, rounded_coeffs
+from gpu_util import admissible_theta, assert_elementwise, exact_coeffs, rel_l2, rounded_coeffs
 from oracle import dispersion as D
 from oracle import fdtd as F
 
@@ -48,6 +48,7 @@ def test_te_2d_fp64_matches_oracle(scheme):
     got = run_gpu(shape, dx, dt, beta, delta, 2, "f64", fields, 200)
     ref = run_oracle(exact_coeffs(beta, delta, dx, dt, 2), fields, 200)
     assert rel_l2(got, ref) <= 1e-12
+    assert_elementwise(got, ref, 1e-11, scheme)
 
 
 # ---------------------------------------------------------------- 3D, several tiles + ragged
@@ -67,10 +68,13 @@ def test_3d_random_fields_match_oracle(shape, dtype):
     if dtype == "f64":
         ref = run_oracle(exact_coeffs(beta, delta, dx, dt, 3), fields, n)
         assert rel_l2(got, ref) <= 1e-12
+        assert_elementwise(got, ref, 1e-11, str(shape))
     else:
         fields32 = [f.astype(np.float32).astype(np.float64) for f in fields]
         ref = run_oracle(rounded_coeffs(beta, delta, dx, dt, 3, np.float32), fields32, n)
         assert rel_l2(got, ref) <= 2e-6
+        # FP32 round-off after 40 steps, cell by cell
+        assert_elementwise(got, ref, 1e-5, str(shape))
 
 
 def test_1d_yee_courant_one_exact_on_gpu():
@@ -102,11 +106,13 @@ def test_sponge_and_bunch_match_oracle():
             ref = run_oracle(exact_coeffs(beta, delta, dx, dt, 3), fields, 25, sponge=sp,
                              bunch=F.Bunch(*bunch))
             assert rel_l2(got, ref) <= 1e-12
+            assert_elementwise(got, ref, 1e-11, dtype)
         else:
             f32 = [f.astype(np.float32).astype(np.float64) for f in fields]
             ref = run_oracle(rounded_coeffs(beta, delta, dx, dt, 3, np.float32), f32, 25,
                              sponge=sp.astype(np.float32).astype(np.float64), bunch=F.Bunch(*bunch))
             assert rel_l2(got, ref) <= 2e-6
+            assert_elementwise(got, ref, 1e-5, dtype)
 
 
 def test_host_buffers_roundtrip():
@@ -186,13 +192,23 @@ def closed_form_plane_wave(shape, dx, dt, coeffs, kvec, pol, n):
     return [a * e for e in E0] + [dt * acc * f for f in FE], a
 
 
-@pytest.mark.parametrize("direction,pol,lam", [((1, 0, 0), (0, 0, 1), 16), ((1, 1, 0), (0, 0, 1), 8),
-                                               ((1, 1, 1), (1, -1, 0), 32)])
-def test_full_size_plane_wave_fp32_1000_steps(direction, pol, lam):
+# Config 2: 256^3, three seeded coefficient sets, lambda in {4, 8, 16, 32} cells along x,
+# (1, 1, 0) and (1, 1, 1), Courant 0.95 of each scheme's limit, 1000 steps.  The bound (1e-5
+# relative L2) is against the oracle's closed-form discrete solution on the FP32-rounded
+# multipliers the kernels use (pure arithmetic round-off); the error against the exact
+# coefficients, which also contains the coefficient quantisation, is printed beside it.
+PW_DIRS = {"x": ((1, 0, 0), (0, 0, 1)), "xy": ((1, 1, 0), (0, 0, 1)), "xyz": ((1, 1, 1), (1, -1, 0))}
+PW_CASES = ([(s, lam, d) for s in (0, 1, 2) for lam in (4, 8, 16, 32) for d in ("x", "xyz")] +
+            [(0, lam, "xy") for lam in (4, 8, 16, 32)])
+
+
+@pytest.mark.parametrize("seed,lam,dname", PW_CASES)
+def test_full_size_plane_wave_fp32_1000_steps(seed, lam, dname):
     n_cells = 256
     shape = (n_cells, n_cells, n_cells)
     dx = [1.0, 1.0, 1.0]
-    beta, delta = admissible_theta(0)
+    direction, pol = PW_DIRS[dname]
+    beta, delta = admissible_theta(seed)
     dt = 0.95 * D.dt_max(beta, delta, dx, 3)
     dvec = np.array(direction, dtype=np.float64)
     m = max(1, round(n_cells / (lam * np.linalg.norm(dvec))))
@@ -201,7 +217,15 @@ def test_full_size_plane_wave_fp32_1000_steps(direction, pol, lam):
     got = run_gpu(shape, dx, dt, beta, delta, 3, "f32", [f.astype(np.float32) for f in fields], 1000)
     ref, _ = closed_form_plane_wave(shape, dx, dt, rounded_coeffs(beta, delta, dx, dt, 3, np.float32),
                                     kvec, pol, 1000)
-    assert rel_l2(got, ref) <= 1e-5
+    err = rel_l2(got, ref)
+    del ref
+    ref_x, _ = closed_form_plane_wave(shape, dx, dt, exact_coeffs(beta, delta, dx, dt, 3), kvec, pol,
+                                      1000)
+    err_x = rel_l2(got, ref_x)
+    lam_real = 2 * math.pi / np.linalg.norm(kvec)
+    print(f"\nplane-wave accuracy seed={seed} lambda={lam} (realised {lam_real:.3f}) dir={dname}: "
+          f"rel L2 vs rounded-multiplier oracle {err:.2e}, vs exact-coefficient oracle {err_x:.2e}")
+    assert err <= 1e-5
 
 
 @pytest.mark.parametrize("dtype", ["f32", "f64"])
@@ -254,6 +278,7 @@ def test_batched_2d_equals_independent_runs(dtype, shape):
         ref = run_oracle(c, f_k, 30, sponge=sp)
         err = rel_l2([g[k:k + 1] for g in got], ref)
         assert err <= (1e-12 if dtype == "f64" else 2e-6), (k, err)
+        assert_elementwise([g[k:k + 1] for g in got], ref, 1e-11 if dtype == "f64" else 1e-5, f"member {k}")
 
 
 def test_expired_wait_reports_timeout_and_handle_stays_usable():

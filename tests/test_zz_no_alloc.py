@@ -48,3 +48,22 @@ def test_noalloc_rejects_grids_beyond_the_static_scratch():
         L.disp_norm_eval_noalloc(c, _dt(beta, delta, dims), [1, 1, 1], dims, (4097, 8, 8))
     assert ei.value.status == L.FDTD_EINVAL
     assert "4096" in str(ei.value)
+
+
+def test_noalloc_calls_leave_device_memory_unchanged():
+    """The property the entry point exists for: after one warm-up call (which looks the scratch
+    address up), further calls take no device memory, whether from cudaMalloc or a pool (the
+    device's free memory, as the driver reports it, does not move)."""
+    torch = pytest.importorskip("torch")
+    (beta, delta), dims, N, w, wp = CASES[1]
+    c = L.make_coeffs(beta, delta)
+    dt = _dt(beta, delta, dims)
+    torch.cuda.synchronize()
+    L.disp_norm_eval_noalloc(c, dt, [1, 1, 1], dims, N, w, wp)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(5):
+        L.disp_norm_eval_noalloc(c, dt, [1, 1, 1], dims, N, w, wp)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
