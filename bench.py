@@ -72,7 +72,8 @@ def parse():
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--n", type=int, default=N_CELLS)
-    p.add_argument("--part", default="all", choices=["all", "fwd32", "adj32", "pic", "fwd64", "norm"],
+    p.add_argument("--slab", type=int, default=32, help="slab length of the temporally blocked leg")
+    p.add_argument("--part", default="all", choices=["all", "fwd32", "fwd32t2", "adj32", "pic", "fwd64", "norm"],
                    help="run one leg only (profiling driver: fwd32, adj32, pic, fwd64 = the FP64 "
                         "step, norm = the dispersion norm + gradient over the n^3 k-grid); prints "
                         "a short line that is not a bench result")
@@ -437,6 +438,22 @@ def run_ours(args):
         sm.close()
         if rank == 0:
             print(json.dumps({"part": "fwd32", "gcells_per_s": fwd, "ms_per_step": t_fwd / args.steps * 1e3}))
+        return
+
+    # --- the same steps temporally blocked (pairs slab by slab through L2)
+    sm.set_temporal_blocking(2, args.slab)
+    for _ in range(2):
+        sm.step(2)
+    k2 = max(1, args.steps // 2)
+    t_t2, _ = time_median(lambda: sm.step(2), k2, stream)
+    t_t2 = barrier_max(t_t2, world)
+    sm.set_temporal_blocking(1)
+    fwd_t2 = world * cells * 2 * k2 / t_t2 / 1e9
+    if args.part == "fwd32t2":
+        sm.close()
+        if rank == 0:
+            print(json.dumps({"part": "fwd32t2", "slab": args.slab, "gcells_per_s": fwd_t2,
+                              "ms_per_step": t_t2 / (2 * k2) * 1e3}))
         return
 
     # --- adjoint FP32 (record a segment, then reverse it)

@@ -144,7 +144,10 @@ int fdtd_get_step(fdtd_handle* h, int64_t* step);
  * the probe misfit sum_{j,k} (E_c^s[x_index, j, k] - T^s[j,k])^2 is added in
  * FP64 to *loss_dev (one device double).  If `record` is non-zero, E^n before
  * each step and E after the last one are stored in the handle's history
- * (n + 1 snapshots, replacing any earlier history) for fdtd_step_adjoint. */
+ * (n + 1 snapshots, replacing any earlier history) for fdtd_step_adjoint.
+ * The step kernels check every E value they write: a non-finite value (the fields
+ * blew up, or the state or the current held an infinity or NaN; a non-finite B
+ * reaches E in the same step) makes the next fdtd_sync return FDTD_ENONFINITE. */
 int fdtd_step(fdtd_handle* h, int32_t n, const fdtd_source* src, const fdtd_probe* probe,
               double* loss_dev, int32_t record);
 
@@ -258,9 +261,24 @@ int fdtd_deposit_rho(fdtd_handle* h, const fdtd_species* species, int32_t nspeci
  * handle stays usable.  Returns FDTD_EINVAL for tries outside the range. */
 int fdtd_selftest_wait_expiry(fdtd_handle* h, int32_t tries);
 
+/* Temporal blocking of the FP32 fused step (the multi-step blocking named as the next
+ * throughput lever for a memory-bound stencil; the paper itself describes no kernel).  With
+ * T = 2, fdtd_step advances pairs of leapfrog steps (App. A update equations, unchanged
+ * arithmetic: the fields are bitwise equal to T = 1) slab by slab along z: step n+1 of slab
+ * s+1, then step n+2 of slab s, so that the intermediate state (E^{n+1}, B^{n+1/2}) is read
+ * back from L2 while it is still resident, and the intermediate planes no later launch needs
+ * are dropped from L2 without being written to DRAM.  slab_planes (>= 3; 0 = 32) sets the slab
+ * length.  Applies to FP32 grids on the fused path (nx % 64 == 0, ny % 8 == 0) with at least
+ * two slabs, and to fdtd_step calls without a source, probe or history; other calls, and an
+ * odd last step, run one launch per step.  T = 1 (the default) restores one launch per step.
+ * Returns FDTD_EINVAL for other T or slab_planes in 1 .. 2. */
+int fdtd_set_temporal_blocking(fdtd_handle* h, int32_t T, int32_t slab_planes);
+
 /* Block until all work on the handle's stream has finished; reports any
- * asynchronous CUDA error, and FDTD_ETIMEOUT (clearing the flag) when a bounded
- * wait inside a kernel expired since the last call. */
+ * asynchronous CUDA error, FDTD_ETIMEOUT when a bounded wait inside a kernel
+ * expired since the last call, and FDTD_ENONFINITE when a step wrote a
+ * non-finite field value or met a non-finite particle since the last call.  The
+ * flags are cleared once reported. */
 int fdtd_sync(fdtd_handle* h);
 
 void fdtd_destroy(fdtd_handle* h);

@@ -47,7 +47,7 @@ STATUS_NAMES = {0: "FDTD_OK", -1: "FDTD_EINVAL", -2: "FDTD_EUNSTABLE", -3: "FDTD
 EXPORTS = ["fdtd_create", "fdtd_set_coeffs", "fdtd_set_state", "fdtd_get_state", "fdtd_get_step",
            "fdtd_step", "fdtd_checkpoint", "fdtd_set_adjoint", "fdtd_get_adjoint",
            "fdtd_step_adjoint", "fdtd_diagnostic", "fdtd_divergence", "fdtd_pic_step",
-           "fdtd_deposit_rho", "fdtd_selftest_wait_expiry",
+           "fdtd_deposit_rho", "fdtd_selftest_wait_expiry", "fdtd_set_temporal_blocking",
            "fdtd_sync", "fdtd_destroy", "disp_norm_eval",
            "disp_norm_eval_noalloc", "disp_group_norm_eval", "disp_omega_eval", "fdtd_coeff_update", "fdtd_dt_max", "fdtd_last_error"]
 
@@ -115,6 +115,7 @@ def load():
     lib.fdtd_divergence.argtypes = [P, I32, P]
     lib.fdtd_sync.argtypes = [P]
     lib.fdtd_selftest_wait_expiry.argtypes = [P, C.c_int32]
+    lib.fdtd_set_temporal_blocking.argtypes = [P, C.c_int32, C.c_int32]
     lib.fdtd_destroy.argtypes = [P]
     lib.fdtd_destroy.restype = None
     lib.disp_norm_eval.argtypes = [C.POINTER(fdtd_coeffs), D, pd, I32, C.POINTER(I32), I32, D,
@@ -234,6 +235,10 @@ def fdtd_sync(h):
 
 def fdtd_selftest_wait_expiry(h, tries):
     check(load().fdtd_selftest_wait_expiry(h, tries))
+
+
+def fdtd_set_temporal_blocking(h, T, slab_planes=0):
+    check(load().fdtd_set_temporal_blocking(h, T, slab_planes))
 
 
 def fdtd_destroy(h):

@@ -263,7 +263,7 @@ adjE_kernel(const __grid_constant__ FusedMaps maps, Geom g, Mult<float> m, Field
     }
     if (failed) {
         if (tid == 0) {
-            atomicExch(err, 1);
+            atomicOr(err, ERR_WAIT);
             if (it == 0) mbar_wait(&bar[NS], 0);
             for (int u = it; u < issued; ++u) mbar_wait(&bar[u % NS], (uint32_t)((u / NS) & 1));
         }

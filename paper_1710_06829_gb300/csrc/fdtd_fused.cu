@@ -123,6 +123,7 @@ step_fused_kernel(const __grid_constant__ FusedMaps maps, Geom g, Mult<T> m, Fie
 
     const T mdt = -m.dt;
     bool failed = false;
+    T fin = T(0);   // non-finite detection (nonfinite_acc): stays 0 while every E value is finite
     int it = 0;
     for (; it < niter; ++it) {
         const int p = z0 - 1 + it;
@@ -214,6 +215,7 @@ step_fused_kernel(const __grid_constant__ FusedMaps maps, Geom g, Mult<T> m, Fie
                     ey *= f;
                     ez *= f;
                 }
+                fin = nonfinite_acc(nonfinite_acc(nonfinite_acc(fin, ex), ey), ez);
                 store_img(g, out.c[0], i, j, pw, ex);
                 store_img(g, out.c[1], i, j, pw, ey);
                 store_img(g, out.c[2], i, j, pw, ez);
@@ -231,10 +233,11 @@ step_fused_kernel(const __grid_constant__ FusedMaps maps, Geom g, Mult<T> m, Fie
             issued = it + D + 2;
         }
     }
+    if (!(fin == T(0))) atomicOr(err, ERR_FIELD);
     if (failed) {
         // drain the copies this CTA still has in flight (bounded), then report
         if (tid == 0) {
-            atomicExch(err, 1);
+            atomicOr(err, ERR_WAIT);
             if (it == 0) mbar_wait(&bar[NS], 0);
             for (int u = it; u < issued; ++u) mbar_wait(&bar[u % NS], (uint32_t)((u / NS) & 1));
         }
@@ -262,6 +265,9 @@ static EncodeTiledFn encode_fn() {
     return fn;
 }
 
+void launch_fused32_range(const FusedMaps& maps, FieldSet<float> in, const Geom& g,
+                          const Mult<float>& m, FieldSet<float> out, const float* spy,
+                          const float* spz, int zs, int ze, int* err, cudaStream_t st);
 bool fused32_supported(const Geom& g);
 int fused32_ebox_w();
 bool fused32_prepare();
@@ -327,6 +333,50 @@ FusedPlan* fused_plan_create(const Geom& g, T* const set0[6], T* const set1[6]) 
 }
 
 void fused_plan_destroy(FusedPlan* p) { delete p; }
+
+void launch_step_fused32_range(const FusedPlan* plan, int in_set, const Geom& g,
+                               const Mult<float>& m, FieldSet<float> in, FieldSet<float> out,
+                               const float* sponge_y, const float* sponge_z, int zs, int ze,
+                               int* err, cudaStream_t st) {
+    launch_fused32_range(plan->maps[in_set], in, g, m, out, sponge_y, sponge_z, zs, ze, err, st);
+}
+
+// ---------------------------------------------------------------- L2 discard
+
+// Drops the 128-byte lines [lo[c], hi[c]) (line indices of absolute addresses) of six arrays
+// from L2 without writing them back (discard.global.L2); their contents become undefined.
+__global__ void discard_l2_kernel(unsigned long long lo0, unsigned long long lo1,
+                                  unsigned long long lo2, unsigned long long lo3,
+                                  unsigned long long lo4, unsigned long long lo5,
+                                  unsigned long long n) {
+    const unsigned long long lo[6] = {lo0, lo1, lo2, lo3, lo4, lo5};
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    for (unsigned long long t = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; t < 6 * n;
+         t += stride) {
+        const unsigned long long a = (lo[t / n] + t % n) * 128ull;
+        asm volatile("discard.global.L2 [%0], 128;" ::"l"(a) : "memory");
+    }
+}
+
+void launch_discard_planes(const Geom& g, size_t esz, void* const arr[6], int p0, int p1,
+                           cudaStream_t st) {
+    if (p1 <= p0) return;
+    const unsigned long long pb = (unsigned long long)g.plane * esz;
+    unsigned long long lo[6];
+    unsigned long long n = ~0ull;
+    for (int c = 0; c < 6; ++c) {
+        const unsigned long long b = reinterpret_cast<unsigned long long>(arr[c]);
+        const unsigned long long first = (b + p0 * pb + 127) / 128, last = (b + p1 * pb) / 128;
+        lo[c] = first;
+        const unsigned long long nc = last > first ? last - first : 0;
+        n = nc < n ? nc : n;   // the arrays have equal sizes and alignments in practice
+    }
+    if (n == 0) return;
+    const unsigned long long total = 6 * n;
+    const int blk = 256;
+    const int grd = (int)((total + blk - 1) / blk < 4096 ? (total + blk - 1) / blk : 4096);
+    discard_l2_kernel<<<grd, blk, 0, st>>>(lo[0], lo[1], lo[2], lo[3], lo[4], lo[5], n);
+}
 
 template <typename T>
 void launch_step_fused(const FusedPlan* plan, int in_set, const Geom& g, const Mult<T>& m,

@@ -264,8 +264,11 @@ struct fdtd_handle {
     FusedMaps lam_maps;                 // .e[c]: TMA descriptors of lambda_B component c (FP32)
     bool lam_staged = false;            // lam_maps valid: the staged FP32 adjoint E kernel runs
     FusedPlan* plan;    // TMA descriptors of both state sets (nullptr: reference-form kernels)
-    int* err_dev;       // bit 1: a bounded wait inside a kernel expired; bit 2: a particle
-                        // with a non-finite (or out-of-range) position or momentum
+    int* err_dev;       // ERR_WAIT: a bounded wait inside a kernel expired; ERR_PARTICLE: a
+                        // particle with a non-finite (or out-of-range) position or momentum;
+                        // ERR_FIELD: a step wrote a non-finite field value
+    int tblock = 1;     // temporal blocking: 1 (one launch per step) or 2 (pairs by slabs)
+    int tslab = 32;     // slab length in planes of the blocked schedule
 
     void* arr(int set, int c) { return state + ((size_t)set * 6 + c) * g.total * esz; }
     void* lam_arr(int c) { return lam + (size_t)c * g.total * esz; }
@@ -668,6 +671,63 @@ static int snapshot(fdtd_handle* h, int snap) {
     return FDTD_OK;
 }
 
+// Two leapfrog steps, temporally blocked through L2 (FP32 fused path, no current, probe or
+// history).  The z axis is cut into S slabs [b_s, b_{s+1}) of at least 3 planes.  With A the
+// current state set and B the other one, step 1 (A -> B) and step 2 (B -> A) run slab by slab,
+// step 2 trailing one slab behind step 1:
+//     1(0) 1(1)  | 1(2) 2(1) | 1(3) 2(2) | ... | 1(S-1) 2(S-2) |  2(S-1) 2(0)
+// so that step 2 of slab s reads the intermediate state (E^{n+1}, B^{n+1/2}) of slabs s-1 .. s+1
+// shortly after step 1 wrote it, from L2 rather than DRAM.  Ordering (every slab >= 3 planes):
+// step 2 of slab s needs B planes b_s - 2 .. b_{s+1} + 1, written by step 1 of slabs s-1 .. s+1;
+// step 2 of slab s overwrites the A planes of slab s, which step 1 of slab s+1 (launched just
+// before) still reads (down to b_{s+1} - 2) and step 1 of slabs >= s+2 never reads; step 1 of
+// slab 0 reads the A planes nz-2, nz-1 and step 1 of slab S-1 the A planes 0, 1 before step 2
+// of those slabs runs (2(0) comes last).  Intermediate planes that no later step-2 launch reads
+// are dropped from L2 without being written back (launch_discard_planes), so the pair moves
+// the state through DRAM about once in each direction instead of twice; set B holds undefined
+// values afterwards (nothing reads it before the next step overwrites it).
+static int step_pair_blocked(fdtd_handle* h, const Mult<float>& m, const float* spy,
+                             const float* spz) {
+    const Geom& g = h->g;
+    const int S = g.nz / h->tslab;
+    const int A = h->cur, B = 1 - h->cur;
+    FieldSet<float> fa = fieldset<float>(h, A), fb = fieldset<float>(h, B);
+    void* bset[6];
+    for (int c = 0; c < 6; ++c) bset[c] = fb.c[c];
+    auto b = [&](int s) { return (int)((long long)s * g.nz / S); };
+    auto step1 = [&](int s) {
+        launch_step_fused32_range(h->plan, A, g, m, fa, fb, spy, spz, b(s), b(s + 1), h->err_dev,
+                                  h->stream);
+    };
+    auto step2 = [&](int s) {
+        launch_step_fused32_range(h->plan, B, g, m, fb, fa, spy, spz, b(s), b(s + 1), h->err_dev,
+                                  h->stream);
+    };
+    // B planes still needed by step 2 of slab 0: nz-2, nz-1, 0 .. b_1 + 1; the rest of the
+    // intermediate state is dropped as soon as step 2 has passed it
+    int dropped = b(1) + 2;
+    auto drop_to = [&](int hi) {
+        if (hi > dropped) {
+            launch_discard_planes(g, sizeof(float), bset, dropped, hi, h->stream);
+            dropped = hi;
+        }
+    };
+    step1(0);
+    step1(1);
+    for (int s = 1; s + 1 < S; ++s) {
+        step1(s + 1);
+        step2(s);
+        drop_to(b(s + 1) - 2);   // step 2 of slab s+1 reads from b_{s+1} - 2 on
+    }
+    step2(S - 1);
+    step2(0);
+    drop_to(g.nz);
+    launch_discard_planes(g, sizeof(float), bset, 0, b(1) + 2 < g.nz ? b(1) + 2 : g.nz, h->stream);
+    CK(cudaGetLastError());
+    h->step += 2;
+    return FDTD_OK;
+}
+
 template <typename T>
 static int step_impl(fdtd_handle* h, int n, const fdtd_source* src, const fdtd_probe* probe,
                      double* loss, int record) {
@@ -700,6 +760,16 @@ static int step_impl(fdtd_handle* h, int n, const fdtd_source* src, const fdtd_p
         h->hist_step0 = h->step;
     }
     const bool fused = h->plan != nullptr;
+    if constexpr (std::is_same<T, float>::value) {
+        // temporally blocked pairs: FP32 fused path, no current, probe or history, >= 2 slabs
+        if (h->tblock == 2 && fused && !bunch && !dense && !probe && !record &&
+            g.nz / h->tslab >= 2) {
+            for (; n >= 2; n -= 2) {
+                int rc = step_pair_blocked(h, m, spy, spz);
+                if (rc) return rc;
+            }
+        }
+    }
     for (int s = 0; s < n; ++s) {
         if (record && !fused) {
             int rc = snapshot<T>(h, s);
@@ -722,7 +792,7 @@ static int step_impl(fdtd_handle* h, int n, const fdtd_source* src, const fdtd_p
         } else {
             FieldSet<T> fs = fieldset<T>(h, h->cur);
             launch_faraday_v0<T>(g, m, fs, spy, spz, h->stream);
-            launch_ampere_v0<T>(g, m, fs, spy, spz, jyz, jrow, h->stream);
+            launch_ampere_v0<T>(g, m, fs, spy, spz, jyz, jrow, h->err_dev, h->stream);
         }
         CK(cudaGetLastError());
         if (dense) {
@@ -974,9 +1044,19 @@ __global__ void wait_expiry_kernel(uint32_t tries, int* err) {
     if (threadIdx.x == 0) {
         mbar_init(&bar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        if (!mbar_wait_n(&bar, 0, tries)) atomicExch(err, 1);
+        if (!mbar_wait_n(&bar, 0, tries)) atomicOr(err, ERR_WAIT);
         asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(&bar)) : "memory");
     }
+}
+
+int fdtd_set_temporal_blocking(fdtd_handle* h, int32_t T, int32_t slab_planes) {
+    if (!h || (T != 1 && T != 2) || slab_planes < 0 || (slab_planes > 0 && slab_planes < 3)) {
+        set_error("fdtd_set_temporal_blocking: T must be 1 or 2 and slab_planes 0 or >= 3");
+        return FDTD_EINVAL;
+    }
+    h->tblock = T;
+    h->tslab = slab_planes > 0 ? slab_planes : 32;
+    return FDTD_OK;
 }
 
 int fdtd_selftest_wait_expiry(fdtd_handle* h, int32_t tries) {
@@ -997,9 +1077,14 @@ int fdtd_sync(fdtd_handle* h) {
     CK(cudaMemcpy(&flag, h->err_dev, sizeof(int), cudaMemcpyDeviceToHost));
     if (flag) {
         cudaMemset(h->err_dev, 0, sizeof(int));
-        if (flag & 1) {
+        if (flag & ERR_WAIT) {
             set_error("a bounded wait inside a step kernel expired; the state is not valid");
             return FDTD_ETIMEOUT;
+        }
+        if (flag & ERR_FIELD) {
+            set_error("a step wrote a non-finite field value (the fields blew up, or the state or "
+                      "the current held an infinity or NaN)");
+            return FDTD_ENONFINITE;
         }
         set_error("a particle position or momentum was not finite; such particles were left "
                   "unchanged and deposited nothing");
@@ -1058,7 +1143,7 @@ static int pic_impl(fdtd_handle* h, int n, const fdtd_species* sp, int nsp) {
         } else {
             launch_faraday_oop<T>(g, m, cur, nxt, spy, spz, h->stream);
             CK(cudaGetLastError());
-            launch_ampere_current<T>(g, m, cur, nxt, nullptr, nxt, spy, spz, h->stream);
+            launch_ampere_current<T>(g, m, cur, nxt, nullptr, nxt, spy, spz, h->err_dev, h->stream);
         }
         CK(cudaGetLastError());
         for (int q = 0; q < nsp; ++q) {

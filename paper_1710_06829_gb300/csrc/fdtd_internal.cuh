@@ -84,6 +84,19 @@ __device__ __forceinline__ T ampere_comp(T e, T p0, T pm, T q0, T qm, T c1, T c2
     return e + fma(c1, p0 - pm, -t);
 }
 
+// Non-finite detection folded into the E update: acc accumulates v * 0, which is 0 for every
+// finite v and NaN once an infinite or NaN v passes, so one comparison after the march tells
+// whether any E value a thread wrote was not finite.  A non-finite B^{n+1/2} always reaches
+// E^{n+1} of the same step (every D x B term has a non-zero multiplier), so checking E covers
+// both fields.  Error-flag bits of the handle: 1 = a bounded wait expired, 2 = a particle was
+// not finite, 4 = a field value was not finite.
+constexpr int ERR_WAIT = 1, ERR_PARTICLE = 2, ERR_FIELD = 4;
+
+template <typename T>
+__device__ __forceinline__ T nonfinite_acc(T acc, T v) {
+    return fma(v, T(0), acc);
+}
+
 template <typename T>
 struct FieldSet {
     T* c[6];   // Ex, Ey, Ez, Bx, By, Bz (padded)
@@ -96,7 +109,7 @@ void launch_faraday_v0(const Geom& g, const Mult<T>& m, FieldSet<T> s, const T* 
                        const T* sponge_z, cudaStream_t st);
 template <typename T>
 void launch_ampere_v0(const Geom& g, const Mult<T>& m, FieldSet<T> s, const T* sponge_y,
-                      const T* sponge_z, const T* jyz, const T* jx_row, cudaStream_t st);
+                      const T* sponge_z, const T* jyz, const T* jx_row, int* err, cudaStream_t st);
 
 // Fused leapfrog step: reads (E^n, B^{n-1/2}) from state set `in_set`, writes
 // (E^{n+1}, B^{n+1/2}) to `out` (padded, images included).  hist_E (entries
@@ -111,6 +124,16 @@ template <typename T>
 void launch_step_fused(const FusedPlan* plan, int in_set, const Geom& g, const Mult<T>& m,
                        FieldSet<T> in, FieldSet<T> out, const T* sponge_y, const T* sponge_z,
                        const T* jyz, const T* jx_row, T* hist_E[3], int* err, cudaStream_t st);
+
+// FP32 fused step on the planes zs .. ze-1 only (no current, no history)
+void launch_step_fused32_range(const FusedPlan* plan, int in_set, const Geom& g,
+                               const Mult<float>& m, FieldSet<float> in, FieldSet<float> out,
+                               const float* sponge_y, const float* sponge_z, int zs, int ze,
+                               int* err, cudaStream_t st);
+// Drop the planes p0 .. p1-1 of six padded arrays from L2 without writing them back (whole
+// 128-byte lines inside the range only); their contents become undefined.
+void launch_discard_planes(const Geom& g, size_t esz, void* const arr[6], int p0, int p1,
+                           cudaStream_t st);
 
 template <typename T>
 void launch_adjoint_B_v0(const Geom& g, const Mult<T>& m, FieldSet<T> lam, const T* E_hist[3],

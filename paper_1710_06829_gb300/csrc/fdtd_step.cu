@@ -90,9 +90,10 @@ __global__ void faraday_v0_kernel(Geom g, Mult<T> m, FieldSet<T> s, const T* __r
 template <typename T>
 __global__ void ampere_v0_kernel(Geom g, Mult<T> m, FieldSet<T> s, const T* __restrict__ spy,
                                  const T* __restrict__ spz, const T* __restrict__ jyz,
-                                 const T* __restrict__ jx_row) {
+                                 const T* __restrict__ jx_row, int* __restrict__ err) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= g.nx) return;
+    T fin = T(0);   // non-finite detection (nonfinite_acc)
     for (int k = blockIdx.z; k < g.nz; k += gridDim.z)
         for (int j = blockIdx.y; j < g.ny; j += gridDim.y) {
             const long long c = pidx(g, i, j, k);
@@ -113,10 +114,12 @@ __global__ void ampere_v0_kernel(Geom g, Mult<T> m, FieldSet<T> s, const T* __re
                 const T f = spy[j] * spz[k];
                 ex *= f; ey *= f; ez *= f;
             }
+            fin = nonfinite_acc(nonfinite_acc(nonfinite_acc(fin, ex), ey), ez);
             store_images(g, s.c[0], i, j, k, ex);
             store_images(g, s.c[1], i, j, k, ey);
             store_images(g, s.c[2], i, j, k, ez);
         }
+    if (!(fin == T(0))) atomicOr(err, ERR_FIELD);
 }
 
 template <typename T>
@@ -129,10 +132,10 @@ void launch_faraday_v0(const Geom& g, const Mult<T>& m, FieldSet<T> s, const T* 
 
 template <typename T>
 void launch_ampere_v0(const Geom& g, const Mult<T>& m, FieldSet<T> s, const T* sponge_y,
-                      const T* sponge_z, const T* jyz, const T* jx_row, cudaStream_t st) {
+                      const T* sponge_z, const T* jyz, const T* jx_row, int* err, cudaStream_t st) {
     dim3 blk(128), grd((g.nx + 127) / 128, (unsigned)(g.ny < 65535 ? g.ny : 65535),
                         (unsigned)(g.nz < 65535 ? g.nz : 65535));   // j, k loop in the kernel
-    ampere_v0_kernel<T><<<grd, blk, 0, st>>>(g, m, s, sponge_y, sponge_z, jyz, jx_row);
+    ampere_v0_kernel<T><<<grd, blk, 0, st>>>(g, m, s, sponge_y, sponge_z, jyz, jx_row, err);
 }
 
 // ---------------------------------------------------------------------------
@@ -177,9 +180,11 @@ template <typename T>
 __global__ void ampere_current_kernel(Geom g, Mult<T> m, FieldSet<T> in, FieldSet<T> bset,
                                       const T* __restrict__ Jx, const T* __restrict__ Jy,
                                       const T* __restrict__ Jz, FieldSet<T> out,
-                                      const T* __restrict__ spy, const T* __restrict__ spz) {
+                                      const T* __restrict__ spy, const T* __restrict__ spz,
+                                      int* __restrict__ err) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= g.nx) return;
+    T fin = T(0);   // non-finite detection (nonfinite_acc)
     for (int k = blockIdx.z; k < g.nz; k += gridDim.z)
         for (int j = blockIdx.y; j < g.ny; j += gridDim.y) {
             const long long c = pidx(g, i, j, k);
@@ -200,10 +205,12 @@ __global__ void ampere_current_kernel(Geom g, Mult<T> m, FieldSet<T> in, FieldSe
                 const T f = spy[j] * spz[k];
                 ex *= f; ey *= f; ez *= f;
             }
+            fin = nonfinite_acc(nonfinite_acc(nonfinite_acc(fin, ex), ey), ez);
             store_images(g, out.c[0], i, j, k, ex);
             store_images(g, out.c[1], i, j, k, ey);
             store_images(g, out.c[2], i, j, k, ez);
         }
+    if (!(fin == T(0))) atomicOr(err, ERR_FIELD);
 }
 
 template <typename T>
@@ -217,14 +224,14 @@ void launch_faraday_oop(const Geom& g, const Mult<T>& m, FieldSet<T> in, FieldSe
 template <typename T>
 void launch_ampere_current(const Geom& g, const Mult<T>& m, FieldSet<T> in, FieldSet<T> bset,
                            const T* const J[3], FieldSet<T> out, const T* sponge_y,
-                           const T* sponge_z, cudaStream_t st) {
+                           const T* sponge_z, int* err, cudaStream_t st) {
     dim3 blk(128), grd((g.nx + 127) / 128, (unsigned)(g.ny < 65535 ? g.ny : 65535),
                         (unsigned)(g.nz < 65535 ? g.nz : 65535));   // j, k loop in the kernel
     const T* Jx = J ? J[0] : nullptr;
     const T* Jy = J ? J[1] : nullptr;
     const T* Jz = J ? J[2] : nullptr;
     ampere_current_kernel<T><<<grd, blk, 0, st>>>(g, m, in, bset, Jx, Jy, Jz, out, sponge_y,
-                                                  sponge_z);
+                                                  sponge_z, err);
 }
 
 template void launch_faraday_oop<float>(const Geom&, const Mult<float>&, FieldSet<float>,
@@ -236,11 +243,11 @@ template void launch_faraday_oop<double>(const Geom&, const Mult<double>&, Field
 template void launch_ampere_current<float>(const Geom&, const Mult<float>&, FieldSet<float>,
                                            FieldSet<float>, const float* const[3],
                                            FieldSet<float>, const float*, const float*,
-                                           cudaStream_t);
+                                           int*, cudaStream_t);
 template void launch_ampere_current<double>(const Geom&, const Mult<double>&, FieldSet<double>,
                                             FieldSet<double>, const double* const[3],
                                             FieldSet<double>, const double*, const double*,
-                                            cudaStream_t);
+                                            int*, cudaStream_t);
 
 // E += -dt J (times the absorbing-layer factor) at the owned cells, J dense [nz][ny][nx] at the E
 // positions (NULL components skipped); the caller refreshes the images afterwards.
@@ -284,10 +291,10 @@ template void launch_faraday_v0<double>(const Geom&, const Mult<double>&, FieldS
                                         const double*, const double*, cudaStream_t);
 template void launch_ampere_v0<float>(const Geom&, const Mult<float>&, FieldSet<float>,
                                       const float*, const float*, const float*, const float*,
-                                      cudaStream_t);
+                                      int*, cudaStream_t);
 template void launch_ampere_v0<double>(const Geom&, const Mult<double>&, FieldSet<double>,
                                        const double*, const double*, const double*,
-                                       const double*, cudaStream_t);
+                                       const double*, int*, cudaStream_t);
 
 // ---------------------------------------------------------------------------
 // rigid bunch: x-profile table for n consecutive steps

@@ -69,6 +69,15 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, i
         : "memory");
 }
 
+// L2 prefetch of one tensor-map box (no shared memory is written and there is no completion
+// to wait for; a box reaching past the array is clipped like a load)
+__device__ __forceinline__ void tma_prefetch_3d(const CUtensorMap* map, int x, int y, int z) {
+    asm volatile("cp.async.bulk.prefetch.tensor.3d.L2.global.tile [%0, {%1, %2, %3}];" ::"l"(
+                     reinterpret_cast<uint64_t>(map)),
+                 "r"(x), "r"(y), "r"(z)
+                 : "memory");
+}
+
 template <typename T>
 __device__ __forceinline__ void store_img(const Geom& g, T* F, int i, int j, int k, T v) {
     const long long base = (long long)k * g.nyp;

@@ -291,7 +291,7 @@ __global__ void __launch_bounds__(THREADS, 4) push_kernel(PushArgs<T> a) {
             x = a.x[0][p]; y = a.x[1][p]; z = a.x[2][p];
             ux = a.u[0][p]; uy = a.u[1][p]; uz = a.u[2][p];
             if (!finite3(x, y, z) || !finite3(ux, uy, uz)) {
-                atomicOr(a.err, 2);
+                atomicOr(a.err, ERR_PARTICLE);
                 live = false;
             } else {
                 x = into_box(x, a.L[0]); y = into_box(y, a.L[1]); z = into_box(z, a.L[2]);
@@ -427,7 +427,7 @@ rho_kernel(Geom g, const T* __restrict__ x0, const T* __restrict__ x1, const T* 
          p += (long long)gridDim.x * blockDim.x) {
         T x = x0[p], y = x1[p], z = x2[p];
         if (!finite3(x, y, z)) {
-            atomicOr(err, 2);
+            atomicOr(err, ERR_PARTICLE);
             continue;
         }
         x = into_box(x, Lx); y = into_box(y, Ly); z = into_box(z, Lz);

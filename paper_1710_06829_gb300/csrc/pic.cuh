@@ -18,7 +18,7 @@ void launch_faraday_oop(const Geom& g, const Mult<T>& m, FieldSet<T> in, FieldSe
 template <typename T>
 void launch_ampere_current(const Geom& g, const Mult<T>& m, FieldSet<T> in, FieldSet<T> bset,
                            const T* const J[3], FieldSet<T> out, const T* sponge_y,
-                           const T* sponge_z, cudaStream_t st);
+                           const T* sponge_z, int* err, cudaStream_t st);
 
 // Per-particle gather (E^n, B^n = (B0 + B1) / 2), Boris push, move, and Esirkepov's current as
 // -dt J^{n+1/2} added into the owned cells of Eout (E^{n+1} without the current, padded; times

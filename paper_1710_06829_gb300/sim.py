@@ -237,6 +237,10 @@ class Simulation:
     def sync(self):
         L.fdtd_sync(self.h)
 
+    def set_temporal_blocking(self, T, slab_planes=0):
+        """T = 2: FP32 steps advance in pairs, slab by slab through L2 (fdtd_set_temporal_blocking)."""
+        L.fdtd_set_temporal_blocking(self.h, T, slab_planes)
+
 
 def disp_norm(beta, delta, dt, dx, dims, N, weight=L.FDTD_W_UNIFORM, weight_param=0.0,
               stream=None):

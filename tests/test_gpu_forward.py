@@ -304,3 +304,79 @@ def test_expired_wait_reports_timeout_and_handle_stays_usable():
     st = F.run(F.State(fields[:3], fields[3:]), F.Coeffs(beta, delta, dx, dt), 3)
     for g, r in zip(got, st.E + st.B):
         assert np.max(np.abs(g - r)) <= 1e-12 * max(1.0, np.max(np.abs(r)))
+
+
+# (64, 16, 12) takes the fused kernels (FP32 and FP64), (36, 13, 7) the reference-form ones
+@pytest.mark.parametrize("dtype,shape", [("f32", (64, 16, 12)), ("f64", (64, 16, 12)),
+                                         ("f32", (36, 13, 7)), ("f64", (36, 13, 7))])
+@pytest.mark.parametrize("bad", [float("nan"), float("inf")])
+def test_nonfinite_field_is_reported(dtype, shape, bad):
+    """A non-finite value in the fields (what a blow-up leaves) is detected by the step kernels
+    as they write E: the next fdtd_sync returns FDTD_ENONFINITE once and clears the flag; the
+    handle then steps a finite state correctly."""
+    beta, delta = admissible_theta(4)
+    dx = [1.0, 1.0, 1.0]
+    dt = 0.9 * D.dt_max(beta, delta, dx, 3)
+    fields = inputs.random_fields(shape, 13)
+    broken = [f.copy() for f in fields]
+    broken[4][shape[2] // 2, 5, 7] = bad          # one B_y value
+    sm = S.Simulation(shape, dx, dt, beta, delta, dims=3, dtype=dtype)
+    sm.set_state([torch.from_numpy(f) for f in broken])
+    sm.step(2)
+    with pytest.raises(FdtdError) as ei:
+        sm.sync()
+    assert ei.value.status == L.FDTD_ENONFINITE
+    assert "non-finite" in str(ei.value)
+    sm.sync()                                     # reported once, then cleared
+    sm.set_state([torch.from_numpy(f) for f in fields])
+    sm.step(3)
+    sm.sync()
+    got = [t.double().cpu().numpy() for t in sm.get_state()]
+    sm.close()
+    if dtype == "f64":
+        ref = run_oracle(exact_coeffs(beta, delta, dx, dt, 3), fields, 3)
+        assert_elementwise(got, ref, 1e-12)
+    else:
+        f32 = [f.astype(np.float32).astype(np.float64) for f in fields]
+        ref = run_oracle(rounded_coeffs(beta, delta, dx, dt, 3, np.float32), f32, 3)
+        assert_elementwise(got, ref, 1e-5)
+
+
+# slab lengths: (64, 8, 20) / 4 -> 5 slabs; (128, 16, 33) / 5 -> 6 slabs of 5-6 planes;
+# (64, 16, 9) / 3 -> 3 slabs; (64, 8, 8) / 4 -> 2 slabs; 256^3 / 32 -> the bench's 8 slabs
+@pytest.mark.parametrize("shape,slab,sponge", [((64, 8, 20), 4, False), ((128, 16, 33), 5, True),
+                                               ((64, 16, 9), 3, False), ((64, 8, 8), 4, True),
+                                               ((256, 256, 256), 32, False)])
+@pytest.mark.parametrize("n", [4, 5])
+def test_temporal_blocking_bitwise_equals_single_steps(shape, slab, sponge, n):
+    """Temporally blocked pairs (slab-interleaved through L2, intermediate planes discarded from
+    L2) give the same bits as one launch per step; an odd last step runs unblocked."""
+    if shape[2] == 256 and n == 5:
+        pytest.skip("one full-size case suffices")
+    beta, delta = admissible_theta(3)
+    dx = [1.0, 1.0, 1.0]
+    dt = 0.95 * D.dt_max(beta, delta, dx, 3)
+    fields = [torch.from_numpy(f.astype(np.float32)) for f in inputs.random_fields(shape, 17)]
+    kw = dict(absorb_cells=2, absorb_sigma=0.2) if sponge else {}
+    outs = []
+    for T in (1, 2):
+        sm = S.Simulation(shape, dx, dt, beta, delta, dims=3, dtype="f32", **kw)
+        sm.set_temporal_blocking(T, slab)
+        sm.set_state(fields)
+        sm.step(n)
+        sm.step(2)      # a second call continues from the blocked result
+        sm.sync()
+        assert sm.step_index == n + 2
+        outs.append(sm.get_state())
+        sm.close()
+    for a, b in zip(*outs):
+        assert torch.equal(a, b)
+
+
+def test_temporal_blocking_arguments():
+    sm = S.Simulation((64, 8, 8), [1, 1, 1], 0.3, np.zeros((3, 3)), np.zeros(3), dims=3, dtype="f32")
+    for T, slab in ((3, 0), (2, 2), (0, 0), (2, -1)):
+        with pytest.raises(FdtdError):
+            sm.set_temporal_blocking(T, slab)
+    sm.set_temporal_blocking(2, 0)
+    sm.close()
