@@ -115,19 +115,71 @@ def peaks():
 
 
 class Clocks:
-    """nvidia-smi sampler; samples inside [mark_start, mark_end] describe the timed region."""
+    """SM clock and clock-event-reason samples inside [mark_start, mark_end].
+
+    Samples come from NVML (libnvidia-ml through ctypes) every 2 ms on a background thread, so
+    that a timed region of a few milliseconds still holds samples; where NVML cannot be loaded
+    the sampler falls back to nvidia-smi at 50 ms (and, for a region shorter than that, to the
+    samples nearest to it).  Nothing here changes a GPU setting: clocks and reasons are read."""
 
     FIELDS = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    # NVML clock-event reason bits
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown"}
 
     def __init__(self, index=0):
         self.proc = None
         self.path = os.path.join(tempfile.gettempdir(), f"fdtd_bench_clocks_{os.getpid()}.csv")
         self.index = index
         self.t0 = self.t1 = None
+        self.nvml = None
+        self.samples = []
+        self.stop = False
+        self.thread = None
+
+    def _nvml_open(self):
+        import ctypes as C
+        lib = C.CDLL("libnvidia-ml.so.1")
+        if lib.nvmlInit_v2() != 0:
+            raise RuntimeError("nvmlInit failed")
+        h = C.c_void_p()
+        ok = False
+        try:   # the NVML device of this process's CUDA device, by PCI bus id
+            import torch
+            pr = torch.cuda.get_device_properties(self.index)
+            bus = f"{pr.pci_domain_id:08x}:{pr.pci_bus_id:02x}:{pr.pci_device_id:02x}.0".encode()
+            ok = lib.nvmlDeviceGetHandleByPciBusId_v2(C.c_char_p(bus), C.byref(h)) == 0
+        except Exception:  # noqa: BLE001
+            ok = False
+        if not ok and lib.nvmlDeviceGetHandleByIndex_v2(C.c_uint(self.index), C.byref(h)) != 0:
+            raise RuntimeError("no NVML handle")
+        mx = C.c_uint()
+        lib.nvmlDeviceGetMaxClockInfo(h, 1, C.byref(mx))   # 1 = NVML_CLOCK_SM
+        reasons_fn = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            lib.nvmlDeviceGetCurrentClocksThrottleReasons
+        self.nvml = (C, lib, h, reasons_fn, mx.value)
+
+    def _poll(self):
+        C, lib, h, reasons_fn, _ = self.nvml
+        clk = C.c_uint()
+        rs = C.c_ulonglong()
+        while not self.stop:
+            t = time.time()
+            if lib.nvmlDeviceGetClockInfo(h, 1, C.byref(clk)) == 0 and reasons_fn(h, C.byref(rs)) == 0:
+                self.samples.append((t, clk.value, rs.value))
+            time.sleep(0.002)
 
     def __enter__(self):
+        try:
+            import threading
+            self._nvml_open()
+            self.thread = threading.Thread(target=self._poll, daemon=True)
+            self.thread.start()
+            return self
+        except Exception:  # noqa: BLE001
+            self.nvml = None
         try:
             os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.fh = open(self.path, "w")
@@ -150,6 +202,13 @@ class Clocks:
         time.sleep(0.15)
 
     def __exit__(self, *a):
+        if self.thread is not None:
+            self.stop = True
+            self.thread.join(timeout=2)
+            try:
+                self.nvml[1].nvmlShutdown()
+            except Exception:  # noqa: BLE001
+                pass
         if self.proc is not None:
             self.proc.terminate()
             try:
@@ -159,6 +218,18 @@ class Clocks:
             self.fh.close()
 
     def summary(self):
+        if self.nvml is not None:
+            inside = [(c, r) for t, c, r in self.samples if self.t0 <= t <= self.t1]
+            window = "timed region (NVML, 2 ms period)"
+            if len(inside) < 2:
+                mid = 0.5 * (self.t0 + self.t1)
+                near = sorted(self.samples, key=lambda x: abs(x[0] - mid))[:3]
+                inside = [(c, r) for _, c, r in near]
+                window = "nearest samples (NVML)"
+            reasons = sorted({n for _, r in inside for b, n in self.REASONS.items() if r & b})
+            sm = [c for c, _ in inside]
+            return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": self.nvml[4],
+                    "reasons": reasons, "samples": len(inside), "window": window}
         import datetime as _dt
         try:
             rows = []
