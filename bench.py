@@ -617,6 +617,11 @@ def run_ours(args):
                    "note": "value, adjoint and fp64_forward are medians over the repetitions"},
         "adjoint": {"value": adj, "unit": "Gcell-updates/s", "steps": seg,
                     "roofline_frac": BYTES_ADJ32 * cells * seg / t_adj / 1e9 / peak},
+        "temporal_blocking": {"value": fwd_t2, "unit": "Gcell-updates/s", "slab_planes": args.slab,
+                              "ms_per_step": t_t2 / (2 * k2) * 1e3,
+                              "effective_frac": BYTES_FWD32 * cells * 2 * k2 / t_t2 / 1e9 / peak,
+                              "note": "pairs of steps slab by slab through L2 "
+                                      "(fdtd_set_temporal_blocking); off by default: slower"},
         "dispersion_norm": {"value": norm_rate, "unit": "Gpoint/s", "grid": [n, n, n],
                             "note": "value and 13-entry gradient, FP64"},
         "fp64_forward": {"value": fwd64, "unit": "Gcell-updates/s",
