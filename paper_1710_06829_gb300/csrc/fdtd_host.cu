@@ -15,6 +15,8 @@
 #include <type_traits>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "fdtd_tma.cuh"
 #include "pic.cuh"
 
@@ -341,6 +343,17 @@ static int upload_bunch_yz(fdtd_handle* h, const fdtd_source* src) {
 
 const char* fdtd_last_error(void) { return g_err; }
 
+// NVTX range around an entry point that launches GPU work: the range names the call in a
+// profiler's timeline (ncu --nvtx, nsys); without a tool attached NVTX does nothing.
+namespace {
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
+}  // namespace
+
 int fdtd_dt_max(const fdtd_coeffs* coeffs, const double dx[3], int32_t dims, double* dt_max,
                 double* s_min, double* s_max) {
     if (!coeffs || !dx || dims < 1 || dims > 3) {
@@ -548,6 +561,7 @@ static int copy_out(fdtd_handle* h, void* const fields[6], int32_t mem, T* const
 }
 
 int fdtd_set_state(fdtd_handle* h, void* const fields[6], int32_t mem, int64_t step0) {
+    NvtxRange nvtx_range("fdtd_set_state");
     if (!h || (mem != FDTD_MEM_DEVICE && mem != FDTD_MEM_HOST)) {
         set_error("fdtd_set_state: bad argument");
         return FDTD_EINVAL;
@@ -566,6 +580,7 @@ int fdtd_set_state(fdtd_handle* h, void* const fields[6], int32_t mem, int64_t s
 }
 
 int fdtd_get_state(fdtd_handle* h, void* const fields[6], int32_t mem) {
+    NvtxRange nvtx_range("fdtd_get_state");
     if (!h || !fields || (mem != FDTD_MEM_DEVICE && mem != FDTD_MEM_HOST)) {
         set_error("fdtd_get_state: bad argument");
         return FDTD_EINVAL;
@@ -602,6 +617,7 @@ static int ensure_lam(fdtd_handle* h) {
 }
 
 int fdtd_set_adjoint(fdtd_handle* h, void* const fields[6], int32_t mem) {
+    NvtxRange nvtx_range("fdtd_set_adjoint");
     if (!h || (mem != FDTD_MEM_DEVICE && mem != FDTD_MEM_HOST)) {
         set_error("fdtd_set_adjoint: bad argument");
         return FDTD_EINVAL;
@@ -619,6 +635,7 @@ int fdtd_set_adjoint(fdtd_handle* h, void* const fields[6], int32_t mem) {
 }
 
 int fdtd_get_adjoint(fdtd_handle* h, void* const fields[6], int32_t mem) {
+    NvtxRange nvtx_range("fdtd_get_adjoint");
     if (!h || !fields || (mem != FDTD_MEM_DEVICE && mem != FDTD_MEM_HOST)) {
         set_error("fdtd_get_adjoint: bad argument");
         return FDTD_EINVAL;
@@ -831,6 +848,7 @@ static int step_impl(fdtd_handle* h, int n, const fdtd_source* src, const fdtd_p
 
 int fdtd_step(fdtd_handle* h, int32_t n, const fdtd_source* src, const fdtd_probe* probe,
               double* loss_dev, int32_t record) {
+    NvtxRange nvtx_range("fdtd_step");
     if (!h || n < 0) { set_error("fdtd_step: bad argument"); return FDTD_EINVAL; }
     if (src && src->kind != FDTD_SRC_NONE && src->kind != FDTD_SRC_BUNCH &&
         src->kind != FDTD_SRC_DENSE) {
@@ -862,6 +880,7 @@ int fdtd_step(fdtd_handle* h, int32_t n, const fdtd_source* src, const fdtd_prob
 }
 
 int fdtd_checkpoint(fdtd_handle* h, int32_t slot, int32_t op) {
+    NvtxRange nvtx_range("fdtd_checkpoint");
     if (!h || slot < 0 || (op != 0 && op != 1)) { set_error("fdtd_checkpoint: bad argument"); return FDTD_EINVAL; }
     const size_t arr = (size_t)h->g.total * h->esz;
     if ((size_t)slot >= h->ckpt.size()) {
@@ -958,6 +977,7 @@ static int adjoint_impl(fdtd_handle* h, int n, const fdtd_probe* probe, double* 
 }
 
 int fdtd_step_adjoint(fdtd_handle* h, int32_t n, const fdtd_probe* probe, double* grad_dev) {
+    NvtxRange nvtx_range("fdtd_step_adjoint");
     if (!h || n < 0 || !grad_dev) { set_error("fdtd_step_adjoint: bad argument"); return FDTD_EINVAL; }
     if (h->hist_len < n + 1) {
         set_error("history holds %d snapshots, %d reverse steps need %d", h->hist_len, n, n + 1);
@@ -985,6 +1005,7 @@ static int ensure_dpart(fdtd_handle* h) {
 }
 
 int fdtd_diagnostic(fdtd_handle* h, int32_t kind, const double* params, double* out_dev) {
+    NvtxRange nvtx_range("fdtd_diagnostic");
     if (!h || !params || !out_dev) { set_error("fdtd_diagnostic: NULL argument"); return FDTD_EINVAL; }
     int rc = ensure_dpart(h);
     if (rc) return rc;
@@ -1024,6 +1045,7 @@ int fdtd_diagnostic(fdtd_handle* h, int32_t kind, const double* params, double* 
 }
 
 int fdtd_divergence(fdtd_handle* h, int32_t which, double* out_dev) {
+    NvtxRange nvtx_range("fdtd_divergence");
     if (!h || !out_dev || which < 0 || which > 2) {
         set_error("fdtd_divergence: bad argument");
         return FDTD_EINVAL;
@@ -1182,6 +1204,7 @@ static int pic_impl(fdtd_handle* h, int n, const fdtd_species* sp, int nsp) {
 }
 
 int fdtd_pic_step(fdtd_handle* h, int32_t n, const fdtd_species* species, int32_t nspecies) {
+    NvtxRange nvtx_range("fdtd_pic_step");
     if (!h || n < 0) { set_error("fdtd_pic_step: bad argument"); return FDTD_EINVAL; }
     int rc = check_species(h, species, nspecies, "fdtd_pic_step");
     if (rc) return rc;
@@ -1206,6 +1229,7 @@ static int rho_impl(fdtd_handle* h, const fdtd_species* sp, int nsp, T* rho) {
 
 int fdtd_deposit_rho(fdtd_handle* h, const fdtd_species* species, int32_t nspecies,
                      void* rho_dev) {
+    NvtxRange nvtx_range("fdtd_deposit_rho");
     if (!h || !rho_dev) { set_error("fdtd_deposit_rho: bad argument"); return FDTD_EINVAL; }
     int rc = check_species(h, species, nspecies, "fdtd_deposit_rho");
     if (rc) return rc;
@@ -1242,6 +1266,7 @@ void fdtd_destroy(fdtd_handle* h) {
 int disp_norm_eval(const fdtd_coeffs* coeffs, double dt, const double dx[3], int32_t dims,
                    const int32_t N[3], int32_t weight, double weight_param, double* out,
                    void* stream) {
+    NvtxRange nvtx_range("disp_norm_eval");
     if (!coeffs || !dx || !N || !out || dims < 1 || dims > 3) {
         set_error("disp_norm_eval: bad argument");
         return FDTD_EINVAL;
@@ -1284,6 +1309,7 @@ int disp_norm_eval(const fdtd_coeffs* coeffs, double dt, const double dx[3], int
 int disp_group_norm_eval(const fdtd_coeffs* coeffs, double dt, const double dx[3], int32_t dims,
                          const int32_t N[3], int32_t weight, double weight_param, double* out,
                          void* stream) {
+    NvtxRange nvtx_range("disp_group_norm_eval");
     if (!coeffs || !dx || !N || !out || dims < 1 || dims > 3) {
         set_error("disp_group_norm_eval: bad argument");
         return FDTD_EINVAL;
@@ -1324,6 +1350,7 @@ int disp_group_norm_eval(const fdtd_coeffs* coeffs, double dt, const double dx[3
 
 int disp_omega_eval(const fdtd_coeffs* coeffs, double dt, const double dx[3], int32_t dims,
                     const double* k_dev, int32_t n, double* omega_dev, void* stream) {
+    NvtxRange nvtx_range("disp_omega_eval");
     if (!coeffs || !dx || !k_dev || !omega_dev || n < 0 || dims < 1 || dims > 3) {
         set_error("disp_omega_eval: bad argument");
         return FDTD_EINVAL;
@@ -1429,6 +1456,7 @@ int noalloc_scratch_address(double** out) {
 int disp_norm_eval_noalloc(const fdtd_coeffs* coeffs, double dt, const double dx[3], int32_t dims,
                            const int32_t N[3], int32_t weight, double weight_param, double* out,
                            void* stream) {
+    NvtxRange nvtx_range("disp_norm_eval_noalloc");
     if (!coeffs || !dx || !N || !out || dims < 1 || dims > 3) {
         set_error("disp_norm_eval_noalloc: bad argument");
         return FDTD_EINVAL;

@@ -284,3 +284,24 @@ def test_adjoint_fp32_256_transpose_and_gradient_vs_fp64():
         del Mu, MTl
     g32, g64 = grads["f32"], grads["f64"]
     assert np.max(np.abs(g32 - g64)) <= 1e-4 * np.max(np.abs(g64))
+
+
+def test_adjoint_fp32_256_reverse_step_matches_oracle():
+    """Full size (256^3, the bench's grid and launch configuration), one reverse step of the
+    staged FP32 kernels against the oracle adjoint run on the FP32-rounded multipliers: lambda
+    element by element, and the 12-entry coefficient gradient."""
+    n = 256
+    shape = (n, n, n)
+    dx = [1.0, 1.0, 1.0]
+    beta, delta = admissible_theta(0)
+    dt = 0.95 * D.dt_max(beta, delta, dx, 3)
+    u = [f.astype(np.float32) for f in inputs.random_fields(shape, 61)]
+    lam0 = [f.astype(np.float32) for f in inputs.random_fields(shape, 62)]
+    lam, gb, gd = gpu_adjoint(shape, dx, dt, beta, delta, "f32", u, lam0, 1)
+    rlam, rgb, rgd = oracle_adjoint(rounded_coeffs(beta, delta, dx, dt, 3, np.float32),
+                                    [f.astype(np.float64) for f in u],
+                                    [f.astype(np.float64) for f in lam0], 1)
+    assert_elementwise(lam, rlam, 1e-5, "256^3 reverse step")
+    scale = max(np.abs(rgb).max(), np.abs(rgd).max())
+    assert np.max(np.abs(gb - rgb)) <= 1e-4 * scale
+    assert np.max(np.abs(gd - rgd)) <= 1e-4 * scale
