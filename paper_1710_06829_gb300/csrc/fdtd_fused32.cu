@@ -24,13 +24,25 @@
 // ring and the register prefetch already cover (cp.async.bulk.prefetch.tensor), which keeps
 // more DRAM reads in flight per CTA than the shared-memory ring alone can hold.
 //
+// Tensor memory holds each thread's own rows across planes.  A thread's own row of E^n plane P
+// is used in four consecutive iterations (as plane p+2, p+1, p, p-1; E_z in three), and its own
+// rows of B^{n+1/2} come back in the E phase of the next two iterations.  Registers cannot
+// carry them (the kernel sits at 128 registers for three CTAs per SM), and shared memory is the
+// pipe that limits the kernel, so each own row is read from the shared ring once, when it is
+// newest, written to the thread's TMEM lane (tcgen05.st, 32x32b.x4: four cells) and read back
+// from there (tcgen05.ld) in the later iterations: 13 of the 36 16-byte shared-memory reads per
+// thread and plane become TMEM reads.  The CTA allocates 128 TMEM columns (three CTAs per SM:
+// 384 of 512) and releases them on every exit path.
+//
 // Per-cell arithmetic is dstar_diff / ampere_comp on the same differences in the same order as
 // the reference-form kernels (dstar_taps): the fields are bitwise equal.  Every mbarrier wait is
 // bounded (fdtd_tma.cuh); on expiry the CTA raises *err, drains its copies in flight (bounded)
 // and returns.
+#include <algorithm>
 #include <cstring>
 
 #include "fdtd_seg.cuh"
+#include "fdtd_tmem.cuh"
 
 namespace fdtd {
 namespace f32seg {
@@ -89,34 +101,12 @@ constexpr uint32_t UNIT_BYTES = 3u * EPL * 4;
 constexpr uint32_t PRO_BYTES = 9u * EPL * 4;
 static_assert(W == 4, "the segment code below is written for 16-byte vectors of four cells");
 
-// The three D* operators (times dt) on the four cells at in-plane index e of a field whose
-// plane slots are Fm (p-1), F0 (p), F1 (p+1), F2 (p+2); the taps come from seg::taps_*.
-__device__ __forceinline__ void dstar_z(const float* Fm, const float* F0, const float* F1,
-                                        const float* F2, int e, bool lb, bool rb, float cA,
-                                        float cD, float cBx, float cBy, float out[4]) {
-    taps_z<EW>(Fm, F0, F1, F2, e, lb, rb,
-               [&](int u, float da, float a2, float am1, float bp, float bm, float cp, float cm) {
-                   out[u] = dstar_diff(da, a2, am1, bp, bm, cp, cm, cA, cD, cBx, cBy);
-               });
-}
+// TMEM columns per thread (see the kernel): own rows of E_x, E_y (4 planes), E_z (3 planes),
+// B_x, B_y (3 planes), B_z (2 planes), four columns per row of four cells
+constexpr uint32_t TM_COLS = 128;   // allocation per CTA (3 CTAs per SM: 384 of 512 columns)
+constexpr int COL_EX = 0, COL_EY = 16, COL_EZ = 32, COL_BX = 44, COL_BY = 56, COL_BZ = 68;
+constexpr int COL_HALO = 76;        // the halo warp shares quadrant 0 with warp 0: its own columns
 
-__device__ __forceinline__ void dstar_y(const float* Fm, const float* F0, const float* F1, int e,
-                                        bool lb, bool rb, float cA, float cD, float cBx,
-                                        float cBz, float out[4]) {
-    taps_y<EW>(Fm, F0, F1, e, lb, rb,
-               [&](int u, float da, float a2, float am1, float bp, float bm, float cp, float cm) {
-                   out[u] = dstar_diff(da, a2, am1, bp, bm, cp, cm, cA, cD, cBx, cBz);
-               });
-}
-
-__device__ __forceinline__ void dstar_x(const float* Fm, const float* F0, const float* F1, int e,
-                                        bool lb, bool rb, float cA, float cD, float cBy,
-                                        float cBz, float out[4]) {
-    taps_x<EW>(Fm, F0, F1, e, lb, rb,
-               [&](int u, float da, float a2, float am1, float bp, float bm, float cp, float cm) {
-                   out[u] = dstar_diff(da, a2, am1, bp, bm, cp, cm, cA, cD, cBy, cBz);
-               });
-}
 
 __global__ void __launch_bounds__(NT, 3)
 step_kernel(const __grid_constant__ FusedMaps maps, Geom g, Mult<float> m, Mult2 m2, FieldSet<float> in,
@@ -196,7 +186,17 @@ step_kernel(const __grid_constant__ FusedMaps maps, Geom g, Mult<float> m, Mult2
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
+    // TMEM: warp 0 allocates the CTA's columns; the address goes through shared memory (the
+    // 128-byte header before the rings) to every thread
+    uint32_t* tm_slot = reinterpret_cast<uint32_t*>(smem);
+    if (tid < 32) tm_alloc<TM_COLS>(tm_slot);
+    tm_fence_before();
     __syncthreads();
+    tm_fence_after();
+    const uint32_t tm_base = *tm_slot;
+    const int warp = tid >> 5;
+    // this thread's TMEM lane (quadrant of its warp) and column base
+    const uint32_t tb = tm_base + ((uint32_t)(32 * (warp & 3)) << 16) + (warp == 4 ? COL_HALO : 0);
     int issued = 0;
     if (tid == PRODUCER) {
         mbar_expect_tx(&bar[NS], PRO_BYTES);
@@ -249,9 +249,10 @@ step_kernel(const __grid_constant__ FusedMaps maps, Geom g, Mult<float> m, Mult2
     int pw = wrapz(z0 - 1), qw = wrapz(z0 - 2);
     int s_m = 0;
     int r3 = (z0 + 5) % 3, r2 = (z0 + 5) % 2;
+    int e3 = 0;   // it mod 3: TMEM slot rotation of E_z and of the own B^{n+1/2} rows
     for (; !failed && it <= niter; ++it, qw = pw, pw = (pw + 1 == g.nz ? 0 : pw + 1),
                                    s_m = (s_m + 1 == NE ? 0 : s_m + 1), r3 = (r3 == 2 ? 0 : r3 + 1),
-                                   r2 ^= 1) {
+                                   r2 ^= 1, e3 = (e3 == 2 ? 0 : e3 + 1)) {
         const int p = z0 - 1 + it;
         // E^n ring slots of planes p-1 .. p+2
         const int s_0 = s_m + 1 == NE ? 0 : s_m + 1;
@@ -267,11 +268,17 @@ step_kernel(const __grid_constant__ FusedMaps maps, Geom g, Mult<float> m, Mult2
             ok = ok && mbar_wait(&bar[it % NS], (uint32_t)((it / NS) & 1));
         }
         ok = __all_sync(FULL, ok);   // keeps the shuffles below warp-uniform
-        // E^n(p-1) of the own cells: read once, used by the B taps and the E update
-        const Q4 E0x = ldq(Pm, e), E0y = ldq(Pm + ESLOT, e), E0z = ldq(Pm + 2 * ESLOT, e);
+        // TMEM columns of the own rows: E_x, E_y of plane p-1+k in slot (it+k) & 3, E_z of plane
+        // p-1+k in slot (it+k) mod 3; own B^{n+1/2} rows of plane p in slot it mod 3 (B_z: it & 1)
+        const int e3p = e3 == 2 ? 0 : e3 + 1, e3pp = e3p == 2 ? 0 : e3p + 1;
+        auto cx = [&](int k) { return tb + COL_EX + 4 * ((it + k) & 3); };
+        auto cy = [&](int k) { return tb + COL_EY + 4 * ((it + k) & 3); };
+        const uint32_t cz0 = tb + COL_EZ + 4 * e3, cz1 = tb + COL_EZ + 4 * e3p,
+                       cz2 = tb + COL_EZ + 4 * e3pp;
         // ---- B^{n+1/2}(p)
-        // B^{n+1/2} ring slots: plane p (current), p-1, p-2
-        const int r3m = r3 == 0 ? 2 : r3 - 1, r3mm = r3m == 0 ? 2 : r3m - 1;
+        // B^{n+1/2} ring slots: plane p (current) and p-1 (its rows y-1 and the halo column feed
+        // the E phase; the own rows come from TMEM)
+        const int r3m = r3 == 0 ? 2 : r3 - 1;
         if (ok && it < niter) {
 #pragma unroll
             for (int c = 0; c < 3; ++c)
@@ -283,25 +290,80 @@ step_kernel(const __grid_constant__ FusedMaps maps, Geom g, Mult<float> m, Mult2
             // shifted along x, which does not keep pairs aligned)
             u64 dz2[2], dy2[2], b2[3][2];
             float t[W];
+            // own rows: the newest plane comes from shared memory (E_x, E_y of p+2; E_z of p+1)
+            // and goes to TMEM; the older planes come from TMEM (at the first iteration every
+            // own row comes from shared memory and is written to TMEM)
+            Q4 ym_, y0_, y1_, zm_, z0_, z1_;
+            const Q4 y2_ = ldq(P2 + ESLOT, e);
+            z1_ = ldq(P1 + 2 * ESLOT, e);
+            if (it == 0) {
+                ym_ = ldq(Pm + ESLOT, e);
+                y0_ = ldq(P0 + ESLOT, e);
+                y1_ = ldq(P1 + ESLOT, e);
+                zm_ = ldq(Pm + 2 * ESLOT, e);
+                z0_ = ldq(P0 + 2 * ESLOT, e);
+                tm_st(cx(0), ldq(Pm, e));
+                tm_st(cx(1), ldq(P0, e));
+                tm_st(cx(2), ldq(P1, e));   // read back from TMEM from the next iteration on
+                tm_st(cy(0), ym_);
+                tm_st(cy(1), y0_);
+                tm_st(cy(2), y1_);
+                tm_st(cz0, zm_);
+                tm_st(cz1, z0_);
+            } else {
+                tm_ld(cy(0), ym_);
+                tm_ld(cy(1), y0_);
+                tm_ld(cy(2), y1_);
+                tm_ld(cz0, zm_);
+                tm_ld(cz1, z0_);
+                tm_wait_ld(ym_, y0_, y1_, zm_, z0_);
+            }
+            tm_st(cy(3), y2_);
+            tm_st(cz2, z1_);
             // B_x = B_x + (D*_z E_y - D*_y E_z)
-            dstar_z2<EW>(Pm + ESLOT, P0 + ESLOT, P1 + ESLOT, P2 + ESLOT, e, lb, rb, m2.cA[2], m2.cD[2],
-                         m2.cB[2][0], m2.cB[2][1], dz2);
-            dstar_y2<EW>(Pm + 2 * ESLOT, P0 + 2 * ESLOT, P1 + 2 * ESLOT, e, lb, rb, m2.cA[1], m2.cD[1],
-                         m2.cB[1][0], m2.cB[1][2], dy2);
+            dstar_z2<EW>(P0 + ESLOT, P1 + ESLOT, y0_, y1_, y2_, ym_, e, lb, rb, m2.cA[2], m2.cD[2],
+                      m2.cB[2][0], m2.cB[2][1], dz2);
+            dstar_y2<EW>(Pm + 2 * ESLOT, P0 + 2 * ESLOT, P1 + 2 * ESLOT, z0_, z1_, zm_, e, lb, rb,
+                      m2.cA[1], m2.cD[1], m2.cB[1][0], m2.cB[1][2], dy2);
 #pragma unroll
             for (int h = 0; h < 2; ++h)
                 b2[0][h] = add2(pk(bo[0][2 * h], bo[0][2 * h + 1]), sub2(dz2[h], dy2[h]));
             // B_y = B_y + (D*_x E_z - D*_z E_x)
-            dstar_x(Pm + 2 * ESLOT, P0 + 2 * ESLOT, P1 + 2 * ESLOT, e, lb, rb, m.cA[0], m.cD[0],
-                    m.cB[0][1], m.cB[0][2], t);
-            dstar_z2<EW>(Pm, P0, P1, P2, e, lb, rb, m2.cA[2], m2.cD[2], m2.cB[2][0], m2.cB[2][1], dz2);
+            dstar_x4<EW>(Pm + 2 * ESLOT, P0 + 2 * ESLOT, P1 + 2 * ESLOT, z0_, z1_, zm_, e, lb, rb,
+                     m.cA[0], m.cD[0], m.cB[0][1], m.cB[0][2], t);
+            Q4 xm_, x0_, x1_;
+            const Q4 x2_ = ldq(P2, e);
+            if (it == 0) {   // written to TMEM in this iteration: not read back before a wait
+                xm_ = ldq(Pm, e);
+                x0_ = ldq(P0, e);
+                x1_ = ldq(P1, e);
+            } else {
+                tm_ld(cx(0), xm_);
+                tm_ld(cx(1), x0_);
+                tm_ld(cx(2), x1_);
+                tm_wait_ld(xm_, x0_, x1_);
+            }
+            tm_st(cx(3), x2_);
+            dstar_z2<EW>(P0, P1, x0_, x1_, x2_, xm_, e, lb, rb, m2.cA[2], m2.cD[2], m2.cB[2][0],
+                      m2.cB[2][1], dz2);
 #pragma unroll
             for (int h = 0; h < 2; ++h)
                 b2[1][h] = add2(pk(bo[1][2 * h], bo[1][2 * h + 1]), sub2(pk(t[2 * h], t[2 * h + 1]), dz2[h]));
             // B_z = B_z + (D*_y E_x - D*_x E_y)
-            dstar_y2<EW>(Pm, P0, P1, e, lb, rb, m2.cA[1], m2.cD[1], m2.cB[1][0], m2.cB[1][2], dy2);
-            dstar_x(Pm + ESLOT, P0 + ESLOT, P1 + ESLOT, e, lb, rb, m.cA[0], m.cD[0], m.cB[0][1],
-                    m.cB[0][2], t);
+            dstar_y2<EW>(Pm, P0, P1, x0_, x1_, xm_, e, lb, rb, m2.cA[1], m2.cD[1], m2.cB[1][0],
+                      m2.cB[1][2], dy2);
+            if (it == 0) {
+                ym_ = ldq(Pm + ESLOT, e);
+                y0_ = ldq(P0 + ESLOT, e);
+                y1_ = ldq(P1 + ESLOT, e);
+            } else {
+                tm_ld(cy(0), ym_);
+                tm_ld(cy(1), y0_);
+                tm_ld(cy(2), y1_);
+                tm_wait_ld(ym_, y0_, y1_);
+            }
+            dstar_x4<EW>(Pm + ESLOT, P0 + ESLOT, P1 + ESLOT, y0_, y1_, ym_, e, lb, rb, m.cA[0],
+                     m.cD[0], m.cB[0][1], m.cB[0][2], t);
 #pragma unroll
             for (int h = 0; h < 2; ++h)
                 b2[2][h] = add2(pk(bo[2][2 * h], bo[2][2 * h + 1]), sub2(dy2[h], pk(t[2 * h], t[2 * h + 1])));
@@ -325,6 +387,11 @@ step_kernel(const __grid_constant__ FusedMaps maps, Geom g, Mult<float> m, Mult2
                 stv(sB + (3 + r3) * BSLOT, bi, byv);
                 stv(sB + (6 + r2) * BSLOT, bi, bzv);
             }
+            if (b_own) {   // warp-uniform (warps 0-3)
+                tm_st(tb + COL_BX + 4 * e3, bxv);
+                tm_st(tb + COL_BY + 4 * e3, byv);
+                tm_st(tb + COL_BZ + 4 * (it & 1), bzv);
+            }
             if (p >= z0 && b_own) {
                 const unsigned po = (unsigned)pw * plane;
                 put_seg(out.c[3], po, dst, bxv);
@@ -338,11 +405,21 @@ step_kernel(const __grid_constant__ FusedMaps maps, Geom g, Mult<float> m, Mult2
             const float* Bxc = sB + r3m * BSLOT;
             const float* Byc = sB + (3 + r3m) * BSLOT;
             const float* Bzc = sB + (6 + (r2 ^ 1)) * BSLOT;
-            const float* Bxp = sB + r3mm * BSLOT;
-            const float* Byp = sB + (3 + r3mm) * BSLOT;
-            const Q4 Bz4 = ldq(Bzc, bi), By4 = ldq(Byc, bi);
-            const Q4 Bzy = ldq(Bzc, bi - BW), Byz = ldq(Byp, bi), Bx = ldq(Bxc, bi),
-                     Bxz = ldq(Bxp, bi), Bxy = ldq(Bxc, bi - BW);
+            // own rows: B^{n+1/2} of planes p-1 (slot (it-1) mod 3, B_z (it-1) & 1) and p-2 (slot
+            // (it-2) mod 3) and E^n of plane p-1 from TMEM; rows y-1 from the shared ring
+            const int b1s = e3 == 0 ? 2 : e3 - 1, b2s = b1s == 0 ? 2 : b1s - 1;
+            Q4 Bz4, By4, Byz, Bx, Bxz, E0x, E0y, E0z;
+            tm_ld(tb + COL_BZ + 4 * ((it + 1) & 1), Bz4);
+            tm_ld(tb + COL_BY + 4 * b1s, By4);
+            tm_ld(tb + COL_BY + 4 * b2s, Byz);
+            tm_ld(tb + COL_BX + 4 * b1s, Bx);
+            tm_ld(tb + COL_BX + 4 * b2s, Bxz);
+            tm_wait_ld(Bz4, By4, Byz, Bx, Bxz);
+            tm_ld(cx(0), E0x);
+            tm_ld(cy(0), E0y);
+            tm_ld(cz0, E0z);
+            tm_wait_ld(E0x, E0y, E0z);
+            const Q4 Bzy = ldq(Bzc, bi - BW), Bxy = ldq(Bxc, bi - BW);
             float Bz[W + 1], By[W + 1];   // [0] = value at x-1, [1 + u] = cell u
 #pragma unroll
             for (int u = 0; u < W; ++u) {
@@ -404,6 +481,7 @@ step_kernel(const __grid_constant__ FusedMaps maps, Geom g, Mult<float> m, Mult2
                 put_seg(h2, po, dst, ez);
             }
         }
+        tm_wait_st();
         bool ok_next = true;
         if (tid == PRODUCER && it + 1 < niter)
             ok_next = mbar_wait(&bar[(it + 1) % NS], (uint32_t)(((it + 1) / NS) & 1));
@@ -431,6 +509,12 @@ step_kernel(const __grid_constant__ FusedMaps maps, Geom g, Mult<float> m, Mult2
         }
         __syncthreads();
     }
+    // release the TMEM columns (every path reaches this point)
+    tm_wait_st();
+    tm_fence_before();
+    __syncthreads();
+    tm_fence_after();
+    if (tid < 32) tm_dealloc<TM_COLS>(tm_base);
 }
 
 }  // namespace f32seg
@@ -458,6 +542,34 @@ int resident_slots(const void* kernel, int threads, size_t smem) {
     return sms * per_sm;
 }
 
+// Resident CTAs of the step kernel on the whole device, from its own limits: shared memory
+// (with the per-CTA reservation), registers (allocated per warp in units of 256), threads, the
+// CTA limit and its TMEM columns (512 per SM).  The occupancy API is not used here: for a
+// kernel that allocates tensor memory it reports fewer resident CTAs than actually run (one
+// where three fit), which made the z-chunk choice launch too few CTAs on small grids.
+static int resident_slots_tmem(const void* kernel, int threads, size_t smem, int tmem_cols) {
+    int dev = 0, sms = 0, smem_sm = 0, resv = 0, regs_sm = 0, thr_sm = 0, blk_sm = 0;
+    cudaFuncAttributes fa;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&resv, cudaDevAttrReservedSharedMemoryPerBlock, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&thr_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&blk_sm, cudaDevAttrMaxBlocksPerMultiprocessor, dev) != cudaSuccess ||
+        cudaFuncGetAttributes(&fa, kernel) != cudaSuccess || sms <= 0)
+        return 0;
+    const long long per_cta_smem = (long long)smem + fa.sharedSizeBytes + resv;
+    const int warps = (threads + 31) / 32;
+    const long long regs_warp = ((long long)fa.numRegs * 32 + 255) / 256 * 256;
+    int n = blk_sm;
+    if (per_cta_smem > 0) n = (int)std::min<long long>(n, smem_sm / per_cta_smem);
+    if (regs_warp > 0) n = (int)std::min<long long>(n, regs_sm / (regs_warp * warps));
+    n = std::min(n, thr_sm / (warps * 32));
+    n = std::min(n, 512 / tmem_cols);
+    return n > 0 ? sms * n : 0;
+}
+
 int zchunk_len(int tiles_xy, int nz, int slots, int tz_min, int tz_max) {
     // A CTA marches tz planes plus about two planes of fixed cost (the z-halo B plane and the
     // prologue copies); CTAs run in waves of `slots`.  Minimise waves x (tz + 2) over chunk
@@ -482,7 +594,7 @@ int zchunk_len(int tiles_xy, int nz, int slots, int tz_min, int tz_max) {
 static int fused32_tz(const Geom& g) {
     using namespace f32seg;
     static int slots = -1;
-    if (slots < 0) slots = resident_slots((const void*)step_kernel, NT, SMEM);
+    if (slots < 0) slots = resident_slots_tmem((const void*)step_kernel, NT, SMEM, TM_COLS);
     // measured at 256^3 (456 resident CTAs): 37-plane chunks (2 full waves) 0.218 ms per step,
     // 32-plane chunks (2.25 waves) 0.269 ms
     return zchunk_len((g.nx / TX) * (g.ny / TY), g.nz, slots, 16, 64);
@@ -506,7 +618,7 @@ void launch_fused32_range(const FusedMaps& maps, FieldSet<float> in, const Geom&
                           const float* spz, int zs, int ze, int* err, cudaStream_t st) {
     using namespace f32seg;
     static int slots = -1;
-    if (slots < 0) slots = resident_slots((const void*)step_kernel, NT, SMEM);
+    if (slots < 0) slots = resident_slots_tmem((const void*)step_kernel, NT, SMEM, TM_COLS);
     const int tiles = (g.nx / TX) * (g.ny / TY);
     const int len = ze - zs;
     const int tz = zchunk_len(tiles, len, slots, 2, 64);

@@ -209,15 +209,22 @@ __device__ __forceinline__ u64 dstar_pair(u64 da, u64 a2, u64 am1, u64 sb, u64 s
     return v;
 }
 
-// D*_z (x then y transverse) on the four cells at e, as two cell pairs; as taps_z + dstar_diff
+// The D* operators (times dt) on the four cells at in-plane index e, with the thread's own row
+// of each plane passed in (the kernel keeps those in tensor memory) and the other rows and the
+// row-end scalars read from the shared-memory planes Fm (p-1), F0 (p), F1 (p+1):
+//   dstar_z2: D*_z (transverse x, then y) on two cell pairs; c0, c1, c2, cm = own rows of
+//             planes p, p+1, p+2, p-1;
+//   dstar_y2: D*_y (transverse x, then z) on two cell pairs; a0, b1, bm = own rows of p, p+1, p-1;
+//   dstar_x4: D*_x (transverse y, then z) per cell;  R, Z1, Zm = own rows of p, p+1, p-1.
+// The differences and their rounding order are those of taps_z / taps_y / taps_x followed by
+// dstar_diff (dstar_pair on cell pairs), so every kernel's B is bitwise the same.
 template <int EW>
-__device__ __forceinline__ void dstar_z2(const float* Fm, const float* F0, const float* F1,
-                                         const float* F2, int e, bool lb, bool rb, u64 cA,
-                                         u64 cD, u64 cBx, u64 cBy, u64 out[2]) {
-    const Q4 c1 = ldq(F1, e), c0 = ldq(F0, e), c2 = ldq(F2, e), cm = ldq(Fm, e);
+__device__ __forceinline__ void dstar_z2(const float* F0, const float* F1, const Q4& c0,
+                                         const Q4& c1, const Q4& c2, const Q4& cm, int e, bool lb,
+                                         bool rb, u64 cA, u64 cD, u64 cBx, u64 cBy, u64 out[2]) {
     const Q4 p1 = ldq(F1, e + EW), p0 = ldq(F0, e + EW), m1 = ldq(F1, e - EW),
              m0 = ldq(F0, e - EW);
-    const u64 dlo = sub2(lo2(c1), lo2(c0)), dhi = sub2(hi2(c1), hi2(c0));   // F1 - F0, x .. x+3
+    const u64 dlo = sub2(lo2(c1), lo2(c0)), dhi = sub2(hi2(c1), hi2(c0));
     float d[6];
     upk(dlo, d[1], d[2]);
     upk(dhi, d[3], d[4]);
@@ -231,15 +238,13 @@ __device__ __forceinline__ void dstar_z2(const float* Fm, const float* F0, const
     out[1] = dstar_pair(dhi, hi2(c2), hi2(cm), pk(d[4] + d[2], d[5] + d[3]), syhi, cA, cD, cBx, cBy);
 }
 
-// D*_y (x then z transverse), as taps_y + dstar_diff
 template <int EW>
-__device__ __forceinline__ void dstar_y2(const float* Fm, const float* F0, const float* F1, int e,
-                                         bool lb, bool rb, u64 cA, u64 cD, u64 cBx, u64 cBz,
-                                         u64 out[2]) {
-    const Q4 a0 = ldq(F0, e), a1 = ldq(F0, e + EW), a2 = ldq(F0, e + 2 * EW),
-             am = ldq(F0, e - EW);
-    const Q4 b1 = ldq(F1, e), b1p = ldq(F1, e + EW), bm = ldq(Fm, e), bmp = ldq(Fm, e + EW);
-    const u64 dlo = sub2(lo2(a1), lo2(a0)), dhi = sub2(hi2(a1), hi2(a0));   // F0(y+1) - F0(y)
+__device__ __forceinline__ void dstar_y2(const float* Fm, const float* F0, const float* F1,
+                                         const Q4& a0, const Q4& b1, const Q4& bm, int e, bool lb,
+                                         bool rb, u64 cA, u64 cD, u64 cBx, u64 cBz, u64 out[2]) {
+    const Q4 a1 = ldq(F0, e + EW), a2 = ldq(F0, e + 2 * EW), am = ldq(F0, e - EW);
+    const Q4 b1p = ldq(F1, e + EW), bmp = ldq(Fm, e + EW);
+    const u64 dlo = sub2(lo2(a1), lo2(a0)), dhi = sub2(hi2(a1), hi2(a0));
     float d[6];
     upk(dlo, d[1], d[2]);
     upk(dhi, d[3], d[4]);
@@ -251,6 +256,45 @@ __device__ __forceinline__ void dstar_y2(const float* Fm, const float* F0, const
     const u64 szhi = add2(sub2(hi2(b1p), hi2(b1)), sub2(hi2(bmp), hi2(bm)));
     out[0] = dstar_pair(dlo, lo2(a2), lo2(am), pk(d[2] + d[0], d[3] + d[1]), szlo, cA, cD, cBx, cBz);
     out[1] = dstar_pair(dhi, hi2(a2), hi2(am), pk(d[4] + d[2], d[5] + d[3]), szhi, cA, cD, cBx, cBz);
+}
+
+template <int EW>
+__device__ __forceinline__ void dstar_x4(const float* Fm, const float* F0, const float* F1,
+                                         const Q4& R, const Q4& Z1, const Q4& Zm, int e, bool lb,
+                                         bool rb, float cA, float cD, float cBy, float cBz,
+                                         float out[4]) {
+    const Q4 Yp = ldq(F0, e + EW), Ym = ldq(F0, e - EW);
+    float r[7];
+    float yp[5], ym[5], z1[5], zm[5];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        r[1 + u] = R.v[u];
+        yp[u] = Yp.v[u];
+        ym[u] = Ym.v[u];
+        z1[u] = Z1.v[u];
+        zm[u] = Zm.v[u];
+    }
+    r[0] = from_left(R.v[3]);
+    r[5] = from_right(R.v[0]);
+    r[6] = from_right(R.v[1]);
+    yp[4] = from_right(Yp.v[0]);
+    ym[4] = from_right(Ym.v[0]);
+    z1[4] = from_right(Z1.v[0]);
+    zm[4] = from_right(Zm.v[0]);
+    if (lb) r[0] = F0[e - 1];
+    if (rb) {
+        r[5] = F0[e + 4];
+        r[6] = F0[e + 5];
+        yp[4] = F0[e + EW + 4];
+        ym[4] = F0[e - EW + 4];
+        z1[4] = F1[e + 4];
+        zm[4] = Fm[e + 4];
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+        out[u] = dstar_diff(r[u + 2] - r[u + 1], r[u + 3], r[u], yp[u + 1] - yp[u],
+                            ym[u + 1] - ym[u], z1[u + 1] - z1[u], zm[u + 1] - zm[u], cA, cD, cBy,
+                            cBz);
 }
 
 }  // namespace seg
