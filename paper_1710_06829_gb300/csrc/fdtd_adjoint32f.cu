@@ -1,0 +1,523 @@
+// FP32 reverse leapfrog step in one kernel: mu, lambda_E and the coefficient gradient.
+//
+// One reverse step (derivation in fdtd_adjoint.cu) maps the adjoint state (lambda_E, lambda_B)
+// attached to u^{n+1} to the one attached to u^n:
+//   l_E = S lambda_E,   mu = S (lambda_B + dt G^T l_E),
+//   lambda_E' = l_E + dt F^T mu,   lambda_B' = mu,   g_theta += dt <mu, (dF/dtheta) E^n>.
+// F^T mu is formed with the transposed extended stencils DT_a (reach -2 .. +1 along a, +-1
+// across; see fdtd_adjoint32e.cu), and the gradient in its transposed form.  With alpha
+// eliminated by Eq. (alpha), D*_a is affine in (delta_a, beta_ab, beta_ac), and over the
+// periodic grid
+//   sum_c mu(c) (dD*_a/dtheta F)(c) = sum_c F(c) (T_theta mu)(c),
+//   T_delta_a mu = (mu[-2a] - mu[+a]) - 3 d(0),   T_beta_ab mu = (d(-b) + d(+b)) - 2 d(0),
+// with d(k) = mu[k-a] - mu[k]: the very differences DT_a combines,
+//   DT_a mu = cA d(0) + cD (mu[-2a] - mu[+a]) + cBb (d(-b) + d(+b)) + cBc (d(-c) + d(+c)).
+// So one set of mu taps gives both lambda_E' and the gradient terms, and E^n is read at the
+// own cells only.  (The sum equals that of the forward form; only the rounding order differs.)
+// Each DT_a mu_m that enters lambda_E'_k with sign s adds s E^n_k (T_theta mu_m) to the
+// gradient of D*_a's coefficients.
+//
+// A CTA owns a 64 x 8 (x, y) tile and a chunk of z planes z0 .. zend-1 and marches z:
+//   phase A, plane p: mu(p) on the tile and on the halo the transposed stencils reach
+//     (x0-2 .. x0+64, y0-2 .. y0+8), from lambda_E planes p and p+1 (TMA boxes 72 x 12 at
+//     x0-4, y0-2 in a five-slot shared ring, copies two planes ahead) and lambda_B(p) (read
+//     from HBM one plane ahead); mu goes to a five-plane shared ring and, for the own cells
+//     of planes z0 .. zend-1, to lambda_B';
+//   phase B, plane q = p-2: lambda_E'(q) and the gradient terms of the own cells, from mu
+//     planes q-2 .. q+1 (formed in the four previous iterations), lambda_E(q) (ring) and
+//     E^n(q) (HBM, one plane ahead).
+// One block barrier per plane.  mu of the halo planes z0-2, z0-1 and zend is recomputed by
+// each chunk.  The result goes to the other adjoint state set: CTAs of neighbouring tiles
+// read halos of lambda_E and lambda_B, so an in-place update would race.
+//
+// Tasks of phase A (four-cell row segment at x0+bx, row y0+by):
+//   t <  128: own rows by = t / 16, bx = 4 (t % 16) (these threads also run phase B)
+//   t in [128, 144): row -1;  [144, 160): row -2;  [160, 176): row 8   (bx = 4 (t % 16))
+//   t in [176, 186): bx = -4, rows -1 .. 8;   t in [186, 195): bx = 64, rows -1 .. 7
+//   t >= 195: a copy of task 194 whose result is dropped (the warp's shuffles need every
+//   lane); thread PRODUCER waits for and issues the TMA copies.
+// Every mbarrier wait is bounded; on expiry the CTA raises *err, drains its copies in flight
+// (bounded) and returns.
+#include "fdtd_seg.cuh"
+
+namespace fdtd {
+namespace adj32f {
+
+using namespace seg;
+
+constexpr int W = 4, TX = 64, TY = 8;
+constexpr int NSEG = TX / W;
+constexpr int NOWN = NSEG * TY;                                 // 128 own segments
+constexpr int NT = 2 * NOWN;                                    // 256 threads: two groups
+constexpr int PRODUCER = NT - 16;                               // lane 16 of the last warp
+constexpr int LW = TX + 8, LH = TY + 4, LPL = LW * LH;          // lambda_E box 72 x 12
+constexpr int LSLOT = ((LPL * 4 + 127) / 128) * 128 / 4;
+constexpr int MH = TY + 3, MPL = LW * MH;                       // mu plane 72 x 11
+constexpr int MSLOT = ((MPL * 4 + 127) / 128) * 128 / 4;
+constexpr int NL = 5, NM = 5, NS = 2;
+constexpr size_t OFF_M = (size_t)NL * 3 * LSLOT * 4;
+constexpr size_t OFF_Y = OFF_M + (size_t)NM * 3 * MSLOT * 4;      // DT_x mu_z, 2 x 128 x 4
+constexpr size_t OFF_BAR = OFF_Y + (size_t)2 * NOWN * W * 4;
+constexpr size_t SMEM = OFF_BAR + (size_t)(NS + 1) * 8;
+constexpr uint32_t UNIT_BYTES = 3u * LPL * 4;
+static_assert(LW == 72 && LH == 12, "the lambda_E boxes are the 72 x 12 boxes of encode_ebox_f32");
+
+// Accumulates s w(u) (T_delta, T_beta_b, T_beta_c) into acc[0..2] for the four cells
+template <bool NEG>
+__device__ __forceinline__ void bracket_acc(float* acc, float w, float d0, float t2, float sb,
+                                            float sc) {
+    const float ww = NEG ? -w : w;
+    acc[0] = fmaf(ww, fmaf(-3.0f, d0, t2), acc[0]);
+    acc[1] = fmaf(ww, fmaf(-2.0f, d0, sb), acc[1]);
+    acc[2] = fmaf(ww, fmaf(-2.0f, d0, sc), acc[2]);
+}
+
+// DT_z of a mu component with plane slots Gmm (q-2), Gm (q-1), G0 (q), Gp (q+1) on the four
+// cells at e (transverse x, then y); gradient terms of D*_z (delta_z, beta_zx, beta_zy)
+template <bool NEG>
+__device__ __forceinline__ void dtz_g(const float* Gmm, const float* Gm, const float* G0,
+                                      const float* Gp, int e, bool lb, bool rb, float cA, float cD,
+                                      float cBx, float cBy, const float* w, float* acc,
+                                      float out[4]) {
+    const Q4 cm = ldq(Gm, e), c0 = ldq(G0, e), cmm = ldq(Gmm, e), cp = ldq(Gp, e);
+    const Q4 ym = ldq(Gm, e - LW), y0m = ldq(G0, e - LW), yp = ldq(Gm, e + LW),
+             y0p = ldq(G0, e + LW);
+    float d[6];   // d[k] = G(q-1) - G(q) at x-1+k
+#pragma unroll
+    for (int u = 0; u < 4; ++u) d[1 + u] = cm.v[u] - c0.v[u];
+    d[0] = from_left(d[4]);
+    d[5] = from_right(d[1]);
+    if (lb) d[0] = Gm[e - 1] - G0[e - 1];
+    if (rb) d[5] = Gm[e + 4] - G0[e + 4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const float dym = ym.v[u] - y0m.v[u], dyp = yp.v[u] - y0p.v[u];
+        out[u] = dstar_diff(d[1 + u], cmm.v[u], cp.v[u], d[u], d[2 + u], dym, dyp, cA, cD, cBx, cBy);
+        bracket_acc<NEG>(acc, w[u], d[1 + u], cmm.v[u] - cp.v[u], d[u] + d[2 + u], dym + dyp);
+    }
+}
+
+// DT_y (transverse x, then z); gradient terms of D*_y (delta_y, beta_yx, beta_yz)
+template <bool NEG>
+__device__ __forceinline__ void dty_g(const float* Gm, const float* G0, const float* Gp, int e,
+                                      bool lb, bool rb, float cA, float cD, float cBx, float cBz,
+                                      const float* w, float* acc, float out[4]) {
+    const Q4 a0 = ldq(G0, e), am = ldq(G0, e - LW), amm = ldq(G0, e - 2 * LW),
+             ap = ldq(G0, e + LW);
+    const Q4 zm = ldq(Gm, e), zmy = ldq(Gm, e - LW), zp = ldq(Gp, e), zpy = ldq(Gp, e - LW);
+    float d[6];   // d[k] = G(y-1) - G(y) at x-1+k, plane q
+#pragma unroll
+    for (int u = 0; u < 4; ++u) d[1 + u] = am.v[u] - a0.v[u];
+    d[0] = from_left(d[4]);
+    d[5] = from_right(d[1]);
+    if (lb) d[0] = G0[e - LW - 1] - G0[e - 1];
+    if (rb) d[5] = G0[e - LW + 4] - G0[e + 4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const float dzm = zmy.v[u] - zm.v[u], dzp = zpy.v[u] - zp.v[u];
+        out[u] = dstar_diff(d[1 + u], amm.v[u], ap.v[u], d[u], d[2 + u], dzm, dzp, cA, cD, cBx, cBz);
+        bracket_acc<NEG>(acc, w[u], d[1 + u], amm.v[u] - ap.v[u], d[u] + d[2 + u], dzm + dzp);
+    }
+}
+
+// DT_x (transverse y, then z); gradient terms of D*_x (delta_x, beta_xy, beta_xz)
+template <bool NEG>
+__device__ __forceinline__ void dtx_g(const float* Gm, const float* G0, const float* Gp, int e,
+                                      bool lb, bool rb, float cA, float cD, float cBy, float cBz,
+                                      const float* w, float* acc, float out[4]) {
+    const Q4 R = ldq(G0, e), Ym = ldq(G0, e - LW), Yp = ldq(G0, e + LW), Zm = ldq(Gm, e),
+             Zp = ldq(Gp, e);
+    float r[7];                         // G(q) at x-2 .. x+4
+    float ym[5], yp[5], zm[5], zp[5];   // x-1 .. x+3
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        r[2 + u] = R.v[u];
+        ym[1 + u] = Ym.v[u];
+        yp[1 + u] = Yp.v[u];
+        zm[1 + u] = Zm.v[u];
+        zp[1 + u] = Zp.v[u];
+    }
+    r[0] = from_left(R.v[2]);
+    r[1] = from_left(R.v[3]);
+    r[6] = from_right(R.v[0]);
+    ym[0] = from_left(Ym.v[3]);
+    yp[0] = from_left(Yp.v[3]);
+    zm[0] = from_left(Zm.v[3]);
+    zp[0] = from_left(Zp.v[3]);
+    if (lb) {
+        r[0] = G0[e - 2];
+        r[1] = G0[e - 1];
+        ym[0] = G0[e - LW - 1];
+        yp[0] = G0[e + LW - 1];
+        zm[0] = Gm[e - 1];
+        zp[0] = Gp[e - 1];
+    }
+    if (rb) r[6] = G0[e + 4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const float d0 = r[u + 1] - r[u + 2];
+        const float dym = ym[u] - ym[u + 1], dyp = yp[u] - yp[u + 1];
+        const float dzm = zm[u] - zm[u + 1], dzp = zp[u] - zp[u + 1];
+        out[u] = dstar_diff(d0, r[u], r[u + 3], dym, dyp, dzm, dzp, cA, cD, cBy, cBz);
+        bracket_acc<NEG>(acc, w[u], d0, r[u] - r[u + 3], dym + dyp, dzm + dzp);
+    }
+}
+
+__global__ void __launch_bounds__(NT, 2)
+adjF_kernel(const __grid_constant__ FusedMaps maps, Geom g, Mult<float> m, FieldSet<float> lam,
+            FieldSet<float> out, const float* __restrict__ e_x, const float* __restrict__ e_y,
+            const float* __restrict__ e_z, const float* __restrict__ spy,
+            const float* __restrict__ spz, double* __restrict__ partials, int tz,
+            int* __restrict__ err) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    float* sL = reinterpret_cast<float*>(smem);
+    float* sM = reinterpret_cast<float*>(smem + OFF_M);
+    float* sY = reinterpret_cast<float*>(smem + OFF_Y);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + OFF_BAR);
+
+    const int ntx = g.nx / TX, nty = g.ny / TY;
+    int w = blockIdx.x;
+    const int tx = w % ntx;
+    w /= ntx;
+    const int ty = w % nty;
+    const int zc = w / nty;
+    const int x0 = tx * TX, y0 = ty * TY, z0 = zc * tz;
+    const int zend = min(z0 + tz, g.nz);
+    const int niter = zend - z0;   // planes of lambda_E'
+    const int tid = threadIdx.x;
+    const bool edge = (x0 < PX) || (x0 + TX > g.nx - PX) || (y0 < PY) || (y0 + TY > g.ny - PY);
+
+    auto wrapz = [&](int q) {
+        int r = q % g.nz;
+        return r < 0 ? r + g.nz : r;
+    };
+    // ring slot of plane P (P >= z0-4): lambda_E and mu rings alike
+    auto slot = [&](int P) { return (P - z0 + 4) % NL; };
+    // unit u: the three lambda_E boxes of plane z0-1+u (the leading plane of iteration u)
+    auto issue_unit = [&](int u) {
+        const int P = z0 - 1 + u;
+        uint64_t* b = &bar[u % NS];
+        mbar_expect_tx(b, UNIT_BYTES);
+        for (int c = 0; c < 3; ++c)
+            tma_load_3d(sL + (slot(P) * 3 + c) * LSLOT, &maps.e[c], x0, y0, wrapz(P), b);
+    };
+
+    // ---- phase A task of this thread (segment at x0+abx, row y0+aby)
+    int abx = TX, aby = TY - 1;   // no task: a copy of the last right-column task
+    bool has_task = true;
+    if (tid < 6 * NSEG) {   // group 0: own rows 0 .. 5
+        aby = tid / NSEG;
+        abx = W * (tid % NSEG);
+    } else if (tid < NOWN) {
+        has_task = false;
+    } else {
+        const int t = tid - NOWN;
+        if (t < 2 * NSEG) {   // own rows 6, 7
+            aby = 6 + t / NSEG;
+            abx = W * (t % NSEG);
+        } else if (t < 5 * NSEG) {   // halo rows -1, -2, 8
+            const int r = t / NSEG - 2;
+            aby = r == 0 ? -1 : r == 1 ? -2 : TY;
+            abx = W * (t % NSEG);
+        } else if (t < 5 * NSEG + 10) {   // left column, rows -1 .. 8
+            abx = -W;
+            aby = t - 5 * NSEG - 1;
+        } else if (t < 5 * NSEG + 19) {   // right column, rows -1 .. 7
+            abx = TX;
+            aby = t - 5 * NSEG - 11;
+        } else {
+            has_task = false;
+        }
+    }
+    // lanes of a 16-segment row get x+1 of their last cell from the next lane
+    const bool row16 = abx >= 0 && abx < TX;
+    const bool a_rb = !has_task || !row16 || abx == TX - W;
+    const bool a_own = has_task && row16 && aby >= 0 && aby < TY;
+    const int ea = (aby + 2) * LW + (abx + 4);
+    int jwa = (y0 + aby) % g.ny;
+    if (jwa < 0) jwa += g.ny;
+    const int jwap = jwa + 1 == g.ny ? 0 : jwa + 1;
+    const unsigned plane = (unsigned)g.plane;
+    const unsigned a_off = (unsigned)((y0 + aby + PY) * g.nxp + (x0 + abx + PX));
+    const SegOut adst = seg_out(g, x0 + (a_own ? abx : 0), y0 + (a_own ? aby : 0), edge);
+
+    // ---- phase B: own segment o of this thread, group 0 (warps 0-3) or 1 (warps 4-7)
+    const bool grp1 = tid >= NOWN;
+    const int o = tid & (NOWN - 1);
+    const int by = o / NSEG, bx = W * (o % NSEG);
+    const bool lb = bx == 0, rb = bx == TX - W;
+    const int e = (by + 2) * LW + (bx + 4);
+    const int jw = y0 + by;
+    const SegOut dst = seg_out(g, x0 + bx, jw, edge);
+
+    if (tid == PRODUCER) {
+        for (int s = 0; s <= NS; ++s) mbar_init(&bar[s], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    __syncthreads();
+    int issued = 0;
+    const int nunits = niter + 3;   // lambda_E planes z0-1 .. zend+1
+    if (tid == PRODUCER) {
+        const int P = z0 - 2;
+        mbar_expect_tx(&bar[NS], UNIT_BYTES);
+        for (int c = 0; c < 3; ++c)
+            tma_load_3d(sL + (slot(P) * 3 + c) * LSLOT, &maps.e[c], x0, y0, wrapz(P), &bar[NS]);
+        for (int u = 0; u < 2 && u < nunits; ++u) {
+            issue_unit(u);
+            issued = u + 1;
+        }
+    }
+
+    // lambda_B of the phase A segment and the two E^n components of phase B (group 0: E_x,
+    // E_y; group 1: E_y, E_z), read from HBM one plane ahead into *n, moved to *o when used
+    float bo[3][W], bn[3][W], eo[2][W], en[2][W];
+    const float* ea0 = grp1 ? e_y : e_x;
+    const float* ea1 = grp1 ? e_z : e_y;
+    auto load_b = [&](int pw, float (&to)[3][W]) {
+        const unsigned off = (unsigned)pw * plane + a_off;
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            unpackv(*reinterpret_cast<const float4*>(lam.c[3 + c] + off), to[c]);
+    };
+    auto load_e = [&](int qw, float (&to)[2][W]) {
+        const unsigned off = (unsigned)qw * plane + dst.ro;
+        unpackv(__ldg(reinterpret_cast<const float4*>(ea0 + off)), to[0]);
+        unpackv(__ldg(reinterpret_cast<const float4*>(ea1 + off)), to[1]);
+    };
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int u = 0; u < W; ++u) bn[c][u] = 0.0f;
+    load_b(wrapz(z0 - 2), bn);
+    load_e(wrapz(z0), en);
+
+    // gradient partial sums: group 0 holds D*_y, D*_z (entries 3..8), group 1 D*_x, D*_y (0..5).
+    // racc: the plane's FP32 sum; gs, gc: Kahan-compensated FP32 running sum over the planes
+    // (FP64 arithmetic runs at 1/64 of the FP32 rate on this part: a per-plane FP64 add kept its
+    // pipe 41 % busy); FP64 only in the block and grid reductions
+    float racc[6], gs[6], gc[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        racc[k] = 0.0f;
+        gs[k] = 0.0f;
+        gc[k] = 0.0f;
+    }
+    // lambda_E'_y(q) = S lE_y + (DT_z mu_x - DT_x mu_z): group 0 forms DT_z mu_x and keeps it
+    // with S and lE_y; group 1 passes DT_x mu_z through sY; group 0 completes it after the
+    // next block barrier
+    float ya[W], yl[W], ys0 = 0.0f;
+    unsigned ypo = 0;
+    bool ypend = false;
+    bool failed = false;
+    int it = 0;
+    {
+        bool ok0 = true;
+        if (tid == PRODUCER) ok0 = mbar_wait(&bar[NS], 0) && mbar_wait(&bar[0], 0);
+        failed = __syncthreads_or(!ok0);
+    }
+    // iteration it: phase A on plane p = z0-2+it (p <= zend), phase B on q = p-2
+    // (z0 <= q < zend); the last iteration only completes lambda_E'_y of plane zend-1
+    for (; !failed && it <= niter + 4; ++it) {
+        const int p = z0 - 2 + it;
+        const int q = p - 2;
+        bool ok = true;
+        if (it < nunits) {
+            if (it == 0) ok = mbar_wait(&bar[NS], 0);
+            ok = ok && mbar_wait(&bar[it % NS], (uint32_t)((it / NS) & 1));
+        }
+        ok = __all_sync(FULL, ok);   // keeps the shuffles below warp-uniform
+        // ---- lambda_E'_y of the previous plane (group 0)
+        if (ok && !grp1 && ypend) {
+            const Q4 b = ldq(sY + ((it + 1) & 1) * NOWN * W, o * W);
+            float v[W];
+#pragma unroll
+            for (int u = 0; u < W; ++u) v[u] = ys0 * yl[u] + (ya[u] - b.v[u]);
+            put_seg(out.c[1], ypo, dst, v);
+            ypend = false;
+        }
+        // ---- phase A: mu(p)
+        if (ok && p <= zend) {
+            const int pw = wrapz(p), pw1 = wrapz(p + 1);
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+#pragma unroll
+                for (int u = 0; u < W; ++u) bo[c][u] = bn[c][u];
+            if (p + 1 <= zend) load_b(pw1, bn);
+            const float* L0 = sL + slot(p) * 3 * LSLOT;
+            const float* L1 = sL + slot(p + 1) * 3 * LSLOT;
+            const Q4 ex = ldq(L0, ea), ey = ldq(L0 + LSLOT, ea), ez = ldq(L0 + 2 * LSLOT, ea);
+            const Q4 exy = ldq(L0, ea + LW), ezy = ldq(L0 + 2 * LSLOT, ea + LW);
+            const Q4 exz = ldq(L1, ea), eyz = ldq(L1 + LSLOT, ea);
+            float ey4 = from_right(ey.v[0]), ez4 = from_right(ez.v[0]);
+            if (a_rb) {
+                ey4 = L0[LSLOT + ea + 4];
+                ez4 = L0[2 * LSLOT + ea + 4];
+            }
+            float s0 = 1.0f, syp = 1.0f, szp = 1.0f;
+            if (spy != nullptr) {
+                s0 = spy[jwa] * spz[pw];
+                syp = spy[jwap] * spz[pw];
+                szp = spy[jwa] * spz[pw1];
+            }
+            float mux[W], muy[W], muz[W];
+#pragma unroll
+            for (int u = 0; u < W; ++u) {
+                const float ex0 = s0 * ex.v[u], ey0 = s0 * ey.v[u], ez0 = s0 * ez.v[u];
+                const float ezx = s0 * (u < W - 1 ? ez.v[u + 1] : ez4);
+                const float eyx = s0 * (u < W - 1 ? ey.v[u + 1] : ey4);
+                const float nx_ = bo[0][u] + (m.cE[2] * (ey0 - szp * eyz.v[u]) - m.cE[1] * (ez0 - syp * ezy.v[u]));
+                const float ny_ = bo[1][u] + (m.cE[0] * (ez0 - ezx) - m.cE[2] * (ex0 - szp * exz.v[u]));
+                const float nz_ = bo[2][u] + (m.cE[1] * (ex0 - syp * exy.v[u]) - m.cE[0] * (ey0 - eyx));
+                mux[u] = s0 * nx_;
+                muy[u] = s0 * ny_;
+                muz[u] = s0 * nz_;
+            }
+            if (has_task) {
+                float* M = sM + slot(p) * 3 * MSLOT;
+                stv(M, ea, mux);
+                stv(M + MSLOT, ea, muy);
+                stv(M + 2 * MSLOT, ea, muz);
+            }
+            if (a_own && p >= z0 && p < zend) {   // mu -> lambda_B' (own cells and their images)
+                const unsigned po = (unsigned)pw * plane;
+                put_seg(out.c[3], po, adst, mux);
+                put_seg(out.c[4], po, adst, muy);
+                put_seg(out.c[5], po, adst, muz);
+            }
+        }
+        // ---- phase B: lambda_E'(q) and the gradient terms (warp-uniform)
+        if (ok && q >= z0 && q < zend) {
+            const int qw = wrapz(q);
+#pragma unroll
+            for (int c = 0; c < 2; ++c)
+#pragma unroll
+                for (int u = 0; u < W; ++u) eo[c][u] = en[c][u];
+            if (q + 1 < zend) load_e(wrapz(q + 1), en);
+            const float* Gmm = sM + slot(q - 2) * 3 * MSLOT;
+            const float* Gm = sM + slot(q - 1) * 3 * MSLOT;
+            const float* G0 = sM + slot(q) * 3 * MSLOT;
+            const float* Gp = sM + slot(q + 1) * 3 * MSLOT;
+            const float* Lq = sL + slot(q) * 3 * LSLOT;
+            const float s0 = spy != nullptr ? spy[jw] * spz[qw] : 1.0f;
+            const unsigned po = (unsigned)qw * plane;
+            float t1[W], t2[W], v[W];
+            if (!grp1) {
+                // lambda_E'_x = S lE_x + (DT_y mu_z - DT_z mu_y)
+                dty_g<false>(Gm + 2 * MSLOT, G0 + 2 * MSLOT, Gp + 2 * MSLOT, e, lb, rb, m.cA[1],
+                             m.cD[1], m.cB[1][0], m.cB[1][2], eo[0], racc + 0, t1);
+                dtz_g<true>(Gmm + MSLOT, Gm + MSLOT, G0 + MSLOT, Gp + MSLOT, e, lb, rb, m.cA[2],
+                            m.cD[2], m.cB[2][0], m.cB[2][1], eo[0], racc + 3, t2);
+                const Q4 lx = ldq(Lq, e);
+#pragma unroll
+                for (int u = 0; u < W; ++u) v[u] = s0 * lx.v[u] + (t1[u] - t2[u]);
+                put_seg(out.c[0], po, dst, v);
+                // DT_z mu_x of lambda_E'_y
+                dtz_g<false>(Gmm, Gm, G0, Gp, e, lb, rb, m.cA[2], m.cD[2], m.cB[2][0], m.cB[2][1],
+                             eo[1], racc + 3, ya);
+                const Q4 ly = ldq(Lq + LSLOT, e);
+#pragma unroll
+                for (int u = 0; u < W; ++u) yl[u] = ly.v[u];
+                ys0 = s0;
+                ypo = po;
+                ypend = true;
+            } else {
+                // DT_x mu_z of lambda_E'_y, to group 0
+                dtx_g<true>(Gm + 2 * MSLOT, G0 + 2 * MSLOT, Gp + 2 * MSLOT, e, lb, rb, m.cA[0],
+                            m.cD[0], m.cB[0][1], m.cB[0][2], eo[0], racc + 0, t1);
+                stv(sY + (it & 1) * NOWN * W, o * W, t1);
+                // lambda_E'_z = S lE_z + (DT_x mu_y - DT_y mu_x)
+                dtx_g<false>(Gm + MSLOT, G0 + MSLOT, Gp + MSLOT, e, lb, rb, m.cA[0], m.cD[0],
+                             m.cB[0][1], m.cB[0][2], eo[1], racc + 0, t1);
+                dty_g<true>(Gm, G0, Gp, e, lb, rb, m.cA[1], m.cD[1], m.cB[1][0], m.cB[1][2], eo[1],
+                            racc + 3, t2);
+                const Q4 lz = ldq(Lq + 2 * LSLOT, e);
+#pragma unroll
+                for (int u = 0; u < W; ++u) v[u] = s0 * lz.v[u] + (t1[u] - t2[u]);
+                put_seg(out.c[2], po, dst, v);
+            }
+#pragma unroll
+            for (int k = 0; k < 6; ++k) {   // compensated add of the plane's partial sum
+                const float y = racc[k] - gc[k];
+                const float t = gs[k] + y;
+                gc[k] = (t - gs[k]) - y;
+                gs[k] = t;
+                racc[k] = 0.0f;
+            }
+        }
+        bool ok_next = true;
+        if (tid == PRODUCER && it + 1 < nunits)
+            ok_next = mbar_wait(&bar[(it + 1) % NS], (uint32_t)(((it + 1) / NS) & 1));
+        if (__syncthreads_or(!ok || !ok_next)) {
+            failed = true;
+            break;
+        }
+        // the slot of plane q (last read by this iteration's phase B) takes plane p+3
+        if (tid == PRODUCER && it + 2 < nunits) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            issue_unit(it + 2);
+            issued = it + 3;
+        }
+    }
+    if (failed) {
+        if (tid == PRODUCER) {
+            atomicOr(err, ERR_WAIT);
+            if (it == 0) mbar_wait(&bar[NS], 0);
+            for (int u = it; u < issued; ++u) mbar_wait(&bar[u % NS], (uint32_t)((u / NS) & 1));
+        }
+        __syncthreads();
+        return;
+    }
+    // block reduction of the FP64 accumulators: entry k of group 0 is coefficient 3 + k,
+    // entry k of group 1 coefficient k
+    __shared__ double red[NT / 32][9];
+    const int wp = tid >> 5, l = tid & 31;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        double v = (double)gs[k] - (double)gc[k];
+        for (int s = 16; s > 0; s >>= 1) v += __shfl_down_sync(FULL, v, s);
+        if (l == 0) red[wp][grp1 ? k : 3 + k] = v;
+    }
+    if (l < 3) red[wp][grp1 ? 6 + l : l] = 0.0;
+    __syncthreads();
+    if (tid < 9) {
+        double v = 0.0;
+        for (int ww = 0; ww < NT / 32; ++ww) v += red[ww][tid];
+        partials[(long long)blockIdx.x * 9 + tid] += v;
+    }
+}
+
+}  // namespace adj32f
+
+bool adjoint32f_supported(const Geom& g) {
+    return g.nx % adj32f::TX == 0 && g.ny % adj32f::TY == 0 && g.nx >= adj32f::TX &&
+           g.ny >= adj32f::TY && g.total < (1LL << 31);
+}
+
+bool adjoint32f_prepare() {
+    return cudaFuncSetAttribute(adj32f::adjF_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)adj32f::SMEM) == cudaSuccess;
+}
+
+static int adjoint32f_tz(const Geom& g) {
+    static int slots = -1;
+    if (slots < 0) slots = resident_slots((const void*)adj32f::adjF_kernel, adj32f::NT, adj32f::SMEM);
+    return zchunk_len((g.nx / adj32f::TX) * (g.ny / adj32f::TY), g.nz, slots, 16, 64);
+}
+
+int adjoint32f_blocks(const Geom& g) {
+    const int tz = adjoint32f_tz(g);
+    return (g.nx / adj32f::TX) * (g.ny / adj32f::TY) * ((g.nz + tz - 1) / tz);
+}
+
+// maps.e[c]: 72 x 12 boxes of lambda_E component c of the input set `lam`; E: the forward
+// E^n of the step (padded arrays); the result goes to `out` (the other set)
+void launch_adjoint32_fused(const FusedMaps& maps, const Geom& g, const Mult<float>& m,
+                            FieldSet<float> lam, FieldSet<float> out, const float* const E[3],
+                            const float* spy, const float* spz, double* partials, int* err,
+                            cudaStream_t st) {
+    adj32f::adjF_kernel<<<adjoint32f_blocks(g), adj32f::NT, adj32f::SMEM, st>>>(
+        maps, g, m, lam, out, E[0], E[1], E[2], spy, spz, partials, adjoint32f_tz(g), err);
+}
+
+}  // namespace fdtd

@@ -58,6 +58,13 @@ void launch_adjoint32_B(const FusedMaps& maps, const Geom& g, const Mult<float>&
                         int* err, cudaStream_t st);
 bool adjoint32e_supported(const Geom& g);
 bool adjoint32e_prepare();
+bool adjoint32f_supported(const Geom& g);
+bool adjoint32f_prepare();
+int adjoint32f_blocks(const Geom& g);
+void launch_adjoint32_fused(const FusedMaps& maps, const Geom& g, const Mult<float>& m,
+                            FieldSet<float> lam, FieldSet<float> out, const float* const E[3],
+                            const float* spy, const float* spz, double* partials, int* err,
+                            cudaStream_t st);
 void launch_adjoint32_E(const FusedMaps& maps, const Geom& g, const Mult<float>& m,
                         FieldSet<float> lam, const float* spy, const float* spz, int* err,
                         cudaStream_t st);
@@ -265,6 +272,12 @@ struct fdtd_handle {
     std::vector<FusedMaps> hist_maps;   // TMA descriptors of each history snapshot (FP32 adjoint)
     FusedMaps lam_maps;                 // .e[c]: TMA descriptors of lambda_B component c (FP32)
     bool lam_staged = false;            // lam_maps valid: the staged FP32 adjoint E kernel runs
+    // FP32 one-kernel reverse step: two adjoint state sets (the kernel writes the other one),
+    // lam_emaps[s].e[c] the TMA descriptors of lambda_E component c of set s
+    bool lam_fused = false;
+    int lam_sets = 1, lam_cur = 0;
+    FusedMaps lam_emaps[2];
+    int adj_split = 0;                  // FDTD_ADJOINT_SPLIT=1: the two-kernel reverse step
     FusedPlan* plan;    // TMA descriptors of both state sets (nullptr: reference-form kernels)
     int* err_dev;       // ERR_WAIT: a bounded wait inside a kernel expired; ERR_PARTICLE: a
                         // particle with a non-finite (or out-of-range) position or momentum;
@@ -273,7 +286,8 @@ struct fdtd_handle {
     int tslab = 32;     // slab length in planes of the blocked schedule
 
     void* arr(int set, int c) { return state + ((size_t)set * 6 + c) * g.total * esz; }
-    void* lam_arr(int c) { return lam + (size_t)c * g.total * esz; }
+    void* lam_arr(int c) { return lam_arr_set(lam_cur, c); }
+    void* lam_arr_set(int set, int c) { return lam + ((size_t)set * 6 + c) * g.total * esz; }
     void* hist_arr(int snap, int c) { return hist + ((size_t)snap * 3 + c) * g.total * esz; }
 };
 
@@ -447,6 +461,9 @@ int fdtd_create(const fdtd_grid* grid, const double dx[3], double dt, const fdtd
     // FDTD_FUSED=0 in the environment selects the reference-form kernels (same arithmetic).
     const char* env = getenv("FDTD_FUSED");
     h->use_fused = !(env && env[0] == '0');
+    // FDTD_ADJOINT_SPLIT=1 selects the two-kernel FP32 reverse step (mu, then lambda_E, in place)
+    const char* env_split = getenv("FDTD_ADJOINT_SPLIT");
+    h->adj_split = env_split && env_split[0] == '1';
     if (h->use_fused) {
         if (G.dtype == FDTD_F32) {
             float* s0[6];
@@ -604,10 +621,23 @@ int fdtd_get_step(fdtd_handle* h, int64_t* step) {
 static int ensure_lam(fdtd_handle* h) {
     if (h->lam) return FDTD_OK;
     const size_t arr = (size_t)h->g.total * h->esz;
-    CK(cudaMalloc(&h->lam, 6 * arr));
-    CK(cudaMemsetAsync(h->lam, 0, 6 * arr, h->stream));
+    const bool fused = h->grid.dtype == FDTD_F32 && h->plan && !h->adj_split &&
+                       adjoint32f_supported(h->g) && adjoint32f_prepare();
+    h->lam_sets = fused ? 2 : 1;
+    h->lam_cur = 0;
+    CK(cudaMalloc(&h->lam, (size_t)h->lam_sets * 6 * arr));
+    CK(cudaMemsetAsync(h->lam, 0, (size_t)h->lam_sets * 6 * arr, h->stream));
     h->lam_staged = false;
-    if (h->grid.dtype == FDTD_F32 && h->plan && adjoint32e_supported(h->g) && adjoint32e_prepare()) {
+    h->lam_fused = false;
+    if (fused) {
+        bool ok = true;
+        for (int s = 0; s < 2; ++s)
+            for (int c = 0; c < 3; ++c)
+                ok = ok && encode_ebox_f32(&h->lam_emaps[s].e[c], h->g, (float*)h->lam_arr_set(s, c));
+        h->lam_fused = ok;   // otherwise the two-kernel reverse step runs on set 0
+    }
+    if (!h->lam_fused && h->grid.dtype == FDTD_F32 && h->plan && adjoint32e_supported(h->g) &&
+        adjoint32e_prepare()) {
         bool ok = true;
         for (int c = 0; c < 3; ++c)
             ok = ok && encode_ebox_f32(&h->lam_maps.e[c], h->g, (float*)h->lam_arr(3 + c));
@@ -918,7 +948,8 @@ static int adjoint_impl(fdtd_handle* h, int n, const fdtd_probe* probe, double* 
     int rc = ensure_lam(h);
     if (rc) return rc;
     const bool staged = std::is_same<T, float>::value && !h->hist_maps.empty();
-    const int nblk = staged ? adjoint32_blocks(g) : adjoint_B_blocks(g);
+    const bool one_kernel = staged && h->lam_fused;
+    const int nblk = one_kernel ? adjoint32f_blocks(g) : staged ? adjoint32_blocks(g) : adjoint_B_blocks(g);
     if (h->npart < nblk) {
         if (h->partials) cudaFree(h->partials);
         h->partials = nullptr;
@@ -926,9 +957,9 @@ static int adjoint_impl(fdtd_handle* h, int n, const fdtd_probe* probe, double* 
         h->npart = nblk;
     }
     CK(cudaMemsetAsync(h->partials, 0, (size_t)nblk * 9 * sizeof(double), h->stream));
-    FieldSet<T> lam = lamset<T>(h);
     const int top = h->hist_len - 1;   // newest snapshot index
     for (int r = 0; r < n; ++r) {
+        FieldSet<T> lam = lamset<T>(h);
         const int snap_after = top - r;        // E^{s+1}
         const int snap_before = top - r - 1;   // E^{s}
         const long long s_after = h->hist_step0 + snap_after;
@@ -940,6 +971,17 @@ static int adjoint_impl(fdtd_handle* h, int n, const fdtd_probe* probe, double* 
         }
         const T* E[3] = {(const T*)h->hist_arr(snap_before, 0), (const T*)h->hist_arr(snap_before, 1),
                          (const T*)h->hist_arr(snap_before, 2)};
+        if constexpr (std::is_same<T, float>::value) {
+            if (one_kernel) {   // lambda^{s+1} (set lam_cur) -> lambda^s (the other set)
+                FieldSet<float> nxt;
+                for (int c = 0; c < 6; ++c) nxt.c[c] = (float*)h->lam_arr_set(h->lam_cur ^ 1, c);
+                launch_adjoint32_fused(h->lam_emaps[h->lam_cur], g, m, lam, nxt, E, spy, spz,
+                                       h->partials, h->err_dev, h->stream);
+                CK(cudaGetLastError());
+                h->lam_cur ^= 1;
+                continue;
+            }
+        }
         if constexpr (std::is_same<T, float>::value) {
             if (staged)
                 launch_adjoint32_B(h->hist_maps[snap_before], g, m, lam, spy, spz, h->partials,

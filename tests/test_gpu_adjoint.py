@@ -305,3 +305,34 @@ def test_adjoint_fp32_256_reverse_step_matches_oracle():
     scale = max(np.abs(rgb).max(), np.abs(rgd).max())
     assert np.max(np.abs(gb - rgb)) <= 1e-4 * scale
     assert np.max(np.abs(gd - rgd)) <= 1e-4 * scale
+
+
+@pytest.mark.parametrize("shape,sponge", [((64, 8, 3), False), ((128, 16, 37), True),
+                                          ((192, 24, 75), False), ((64, 16, 1), False),
+                                          ((64, 8, 9), True)])
+def test_one_kernel_reverse_step_equals_two_kernel_step(shape, sponge, monkeypatch):
+    """The one-kernel FP32 reverse step (default: mu on the tile and its halo, lambda_E two planes
+    behind, gradient from the transposed brackets) against the two-kernel step
+    (FDTD_ADJOINT_SPLIT=1: mu in place, then lambda_E), same inputs and probe, 4 reverse steps:
+    lambda bitwise equal (the same arithmetic per value), the gradient equal up to the order of
+    the FP32 partial sums (forward brackets on E^n there, transposed brackets on mu here)."""
+    beta, delta = admissible_theta(7)
+    dx = [1.0, 1.0, 1.0]
+    dt = 0.9 * D.dt_max(beta, delta, dx, 3)
+    fields = [f.astype(np.float32) for f in inputs.random_fields(shape, 71)]
+    lam0 = [f.astype(np.float32) for f in inputs.random_fields(shape, 72)]
+    n = 4
+    nx, ny, nz = shape
+    kw = dict(absorb_cells=2, absorb_sigma=0.3) if sponge else {}
+    rng = np.random.default_rng(7)
+    probe = (1, 5, rng.standard_normal((n, nz, ny)).astype(np.float32))
+    out = {}
+    for flag in ("0", "1"):
+        monkeypatch.setenv("FDTD_ADJOINT_SPLIT", flag)
+        out[flag] = gpu_adjoint(shape, dx, dt, beta, delta, "f32", fields, lam0, n, probe, **kw)
+    (l1, gb1, gd1), (l2, gb2, gd2) = out["0"], out["1"]
+    for c in range(6):
+        assert np.array_equal(l1[c], l2[c]), f"component {c}"
+    scale = max(np.abs(gb2).max(), np.abs(gd2).max())
+    assert np.max(np.abs(gb1 - gb2)) <= 1e-5 * scale
+    assert np.max(np.abs(gd1 - gd2)) <= 1e-5 * scale

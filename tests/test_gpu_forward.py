@@ -250,6 +250,30 @@ def test_fused_kernel_bitwise_equals_reference_form(dtype, shape, monkeypatch):
         assert torch.equal(a, b)
 
 
+# The FP32 step kernel keeps each thread's own rows in tensor memory in slots that rotate with
+# the plane index inside a z-chunk; the chunk length depends on the grid (whole waves of resident
+# CTAs).  These shapes give single-plane grids, one- and two-plane chunks, ragged last chunks,
+# chunks of 16-64 planes and launches of one to several waves.
+@pytest.mark.parametrize("shape", [(64, 8, 2), (64, 8, 3), (192, 24, 5), (128, 40, 17),
+                                   (256, 16, 38), (64, 64, 75), (256, 64, 64)])
+def test_fused_fp32_tmem_kernel_bitwise_equals_reference_form(shape, monkeypatch):
+    beta, delta = admissible_theta(11)
+    dx = [1.0, 1.0, 1.0]
+    dt = 0.95 * D.dt_max(beta, delta, dx, 3)
+    fields = inputs.random_fields(shape, seed=23)
+    outs = []
+    for flag in ("1", "0"):
+        monkeypatch.setenv("FDTD_FUSED", flag)
+        sm = S.Simulation(shape, dx, dt, beta, delta, dims=3, dtype="f32")
+        sm.set_state([torch.from_numpy(f) for f in fields])
+        sm.step(5)
+        sm.sync()
+        outs.append(sm.get_state())
+        sm.close()
+    for a, b in zip(*outs):
+        assert torch.equal(a, b)
+
+
 @pytest.mark.parametrize("dtype,shape", [("f64", (64, 32, 4)), ("f32", (64, 32, 5)), ("f64", (36, 10, 3))])
 def test_batched_2d_equals_independent_runs(dtype, shape):
     """batched = 1: the nz planes are independent 2D problems (z multipliers are zero)."""
