@@ -317,8 +317,13 @@ adjF_kernel(const __grid_constant__ FusedMaps maps, Geom g, Mult<float> m, Field
         failed = __syncthreads_or(!ok0);
     }
     // iteration it: phase A on plane p = z0-2+it (p <= zend), phase B on q = p-2
-    // (z0 <= q < zend); the last iteration only completes lambda_E'_y of plane zend-1
-    for (; !failed && it <= niter + 4; ++it) {
+    // (z0 <= q < zend); the last iteration only completes lambda_E'_y of plane zend-1.
+    // Plane bookkeeping by counters (no integer division in the loop): pw = p mod nz,
+    // qw = q mod nz, sp = ring slot of plane p = (it + 2) mod 5 (plane q: sp + 3, q-2: + 1, ...)
+    int pw = wrapz(z0 - 2), qw = wrapz(z0 - 4), sp = slot(z0 - 2);
+    auto inc5 = [](int a, int k) { return a + k >= NL ? a + k - NL : a + k; };
+    for (; !failed && it <= niter + 4; ++it, qw = (qw + 1 == g.nz ? 0 : qw + 1),
+                                       pw = (pw + 1 == g.nz ? 0 : pw + 1), sp = inc5(sp, 1)) {
         const int p = z0 - 2 + it;
         const int q = p - 2;
         bool ok = true;
@@ -338,14 +343,14 @@ adjF_kernel(const __grid_constant__ FusedMaps maps, Geom g, Mult<float> m, Field
         }
         // ---- phase A: mu(p)
         if (ok && p <= zend) {
-            const int pw = wrapz(p), pw1 = wrapz(p + 1);
+            const int pw1 = pw + 1 == g.nz ? 0 : pw + 1;
 #pragma unroll
             for (int c = 0; c < 3; ++c)
 #pragma unroll
                 for (int u = 0; u < W; ++u) bo[c][u] = bn[c][u];
             if (p + 1 <= zend) load_b(pw1, bn);
-            const float* L0 = sL + slot(p) * 3 * LSLOT;
-            const float* L1 = sL + slot(p + 1) * 3 * LSLOT;
+            const float* L0 = sL + sp * 3 * LSLOT;
+            const float* L1 = sL + inc5(sp, 1) * 3 * LSLOT;
             const Q4 ex = ldq(L0, ea), ey = ldq(L0 + LSLOT, ea), ez = ldq(L0 + 2 * LSLOT, ea);
             const Q4 exy = ldq(L0, ea + LW), ezy = ldq(L0 + 2 * LSLOT, ea + LW);
             const Q4 exz = ldq(L1, ea), eyz = ldq(L1 + LSLOT, ea);
@@ -374,7 +379,7 @@ adjF_kernel(const __grid_constant__ FusedMaps maps, Geom g, Mult<float> m, Field
                 muz[u] = s0 * nz_;
             }
             if (has_task) {
-                float* M = sM + slot(p) * 3 * MSLOT;
+                float* M = sM + sp * 3 * MSLOT;
                 stv(M, ea, mux);
                 stv(M + MSLOT, ea, muy);
                 stv(M + 2 * MSLOT, ea, muz);
@@ -388,17 +393,17 @@ adjF_kernel(const __grid_constant__ FusedMaps maps, Geom g, Mult<float> m, Field
         }
         // ---- phase B: lambda_E'(q) and the gradient terms (warp-uniform)
         if (ok && q >= z0 && q < zend) {
-            const int qw = wrapz(q);
 #pragma unroll
             for (int c = 0; c < 2; ++c)
 #pragma unroll
                 for (int u = 0; u < W; ++u) eo[c][u] = en[c][u];
-            if (q + 1 < zend) load_e(wrapz(q + 1), en);
-            const float* Gmm = sM + slot(q - 2) * 3 * MSLOT;
-            const float* Gm = sM + slot(q - 1) * 3 * MSLOT;
-            const float* G0 = sM + slot(q) * 3 * MSLOT;
-            const float* Gp = sM + slot(q + 1) * 3 * MSLOT;
-            const float* Lq = sL + slot(q) * 3 * LSLOT;
+            if (q + 1 < zend) load_e(qw + 1 == g.nz ? 0 : qw + 1, en);
+            const int sq = inc5(sp, 3);
+            const float* Gmm = sM + inc5(sp, 1) * 3 * MSLOT;
+            const float* Gm = sM + inc5(sp, 2) * 3 * MSLOT;
+            const float* G0 = sM + sq * 3 * MSLOT;
+            const float* Gp = sM + inc5(sp, 4) * 3 * MSLOT;
+            const float* Lq = sL + sq * 3 * LSLOT;
             const float s0 = spy != nullptr ? spy[jw] * spz[qw] : 1.0f;
             const unsigned po = (unsigned)qw * plane;
             float t1[W], t2[W], v[W];
