@@ -165,15 +165,19 @@ adjB_kernel(const __grid_constant__ FusedMaps maps, Geom g, Mult<float> m, Field
             float mux[4], muy[4], muz[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-                const float ex0 = s0 * L.ex[u], ey0 = s0 * L.ey[u], ez0 = s0 * L.ez[u];
-                const float ezx = s0 * L.ez[u + 1];
-                const float eyx = s0 * L.ey[u + 1];
-                const float nx_ = L.bx[u] + (m.cE[2] * (ey0 - szp * L.eyz[u]) - m.cE[1] * (ez0 - syp * L.ezy[u]));
-                const float ny_ = L.by[u] + (m.cE[0] * (ez0 - ezx) - m.cE[2] * (ex0 - szp * L.exz[u]));
-                const float nz_ = L.bz[u] + (m.cE[1] * (ex0 - syp * L.exy[u]) - m.cE[0] * (ey0 - eyx));
-                mux[u] = s0 * nx_;
-                muy[u] = s0 * ny_;
-                muz[u] = s0 * nz_;
+                // a fixed rounding order (intrinsics are never contracted), the one the
+                // one-kernel reverse step uses on cell pairs
+                const float ex0 = __fmul_rn(s0, L.ex[u]), ey0 = __fmul_rn(s0, L.ey[u]),
+                            ez0 = __fmul_rn(s0, L.ez[u]);
+                const float gx = __fmaf_rn(m.cE[2], __fmaf_rn(-szp, L.eyz[u], ey0),
+                                           __fmul_rn(-m.cE[1], __fmaf_rn(-syp, L.ezy[u], ez0)));
+                const float gy = __fmaf_rn(m.cE[0], __fmaf_rn(-s0, L.ez[u + 1], ez0),
+                                           __fmul_rn(-m.cE[2], __fmaf_rn(-szp, L.exz[u], ex0)));
+                const float gz = __fmaf_rn(m.cE[1], __fmaf_rn(-syp, L.exy[u], ex0),
+                                           __fmul_rn(-m.cE[0], __fmaf_rn(-s0, L.ey[u + 1], ey0)));
+                mux[u] = __fmul_rn(s0, __fadd_rn(L.bx[u], gx));
+                muy[u] = __fmul_rn(s0, __fadd_rn(L.by[u], gy));
+                muz[u] = __fmul_rn(s0, __fadd_rn(L.bz[u], gz));
             }
             if (it + 1 < niter) load_lam(p + 1);
             // gradient brackets from the E^n ring (planes p-1 .. p+2 in slots s_m .. s_2)

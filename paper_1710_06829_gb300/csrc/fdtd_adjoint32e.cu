@@ -221,19 +221,19 @@ adjE_kernel(const __grid_constant__ FusedMaps maps, Geom g, Mult<float> m, Field
             dtz(Qmm + ESLOT, Qm + ESLOT, Q0 + ESLOT, Qp + ESLOT, e, lb, rb, m.cA[2], m.cD[2],
                 m.cB[2][0], m.cB[2][1], t2);
 #pragma unroll
-            for (int u = 0; u < W; ++u) ex[u] = s0 * lo[0][u] + (t1[u] - t2[u]);
+            for (int u = 0; u < W; ++u) ex[u] = __fmaf_rn(s0, lo[0][u], __fsub_rn(t1[u], t2[u]));
             // E_y: S lE_y + (DT_z mu_x - DT_x mu_z)
             dtz(Qmm, Qm, Q0, Qp, e, lb, rb, m.cA[2], m.cD[2], m.cB[2][0], m.cB[2][1], t1);
             dtx(Qm + 2 * ESLOT, Q0 + 2 * ESLOT, Qp + 2 * ESLOT, e, lb, rb, m.cA[0], m.cD[0],
                 m.cB[0][1], m.cB[0][2], t2);
 #pragma unroll
-            for (int u = 0; u < W; ++u) ey[u] = s0 * lo[1][u] + (t1[u] - t2[u]);
+            for (int u = 0; u < W; ++u) ey[u] = __fmaf_rn(s0, lo[1][u], __fsub_rn(t1[u], t2[u]));
             // E_z: S lE_z + (DT_x mu_y - DT_y mu_x)
             dtx(Qm + ESLOT, Q0 + ESLOT, Qp + ESLOT, e, lb, rb, m.cA[0], m.cD[0], m.cB[0][1],
                 m.cB[0][2], t1);
             dty(Qm, Q0, Qp, e, lb, rb, m.cA[1], m.cD[1], m.cB[1][0], m.cB[1][2], t2);
 #pragma unroll
-            for (int u = 0; u < W; ++u) ez[u] = s0 * lo[2][u] + (t1[u] - t2[u]);
+            for (int u = 0; u < W; ++u) ez[u] = __fmaf_rn(s0, lo[2][u], __fsub_rn(t1[u], t2[u]));
             const unsigned po = (unsigned)qw * plane;
             put_seg(lam.c[0], po, dst, ex);
             put_seg(lam.c[1], po, dst, ey);

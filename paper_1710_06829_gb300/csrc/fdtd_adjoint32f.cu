@@ -233,6 +233,8 @@ adjF_kernel(const __grid_constant__ FusedMaps maps, Geom g, Mult<float> m, Field
     const bool row16 = abx >= 0 && abx < TX;
     const bool a_rb = !has_task || !row16 || abx == TX - W;
     const bool a_own = has_task && row16 && aby >= 0 && aby < TY;
+    // phase A runs in every warp that has a task (warp 3 has none)
+    const bool a_warp = (tid >> 5) != 3;
     const int ea = (aby + 2) * LW + (abx + 4);
     int jwa = (y0 + aby) % g.ny;
     if (jwa < 0) jwa += g.ny;
@@ -337,12 +339,12 @@ adjF_kernel(const __grid_constant__ FusedMaps maps, Geom g, Mult<float> m, Field
             const Q4 b = ldq(sY + ((it + 1) & 1) * NOWN * W, o * W);
             float v[W];
 #pragma unroll
-            for (int u = 0; u < W; ++u) v[u] = ys0 * yl[u] + (ya[u] - b.v[u]);
+            for (int u = 0; u < W; ++u) v[u] = __fmaf_rn(ys0, yl[u], __fsub_rn(ya[u], b.v[u]));
             put_seg(out.c[1], ypo, dst, v);
             ypend = false;
         }
-        // ---- phase A: mu(p)
-        if (ok && p <= zend) {
+        // ---- phase A: mu(p) (warps with a task)
+        if (ok && p <= zend && a_warp) {
             const int pw1 = pw + 1 == g.nz ? 0 : pw + 1;
 #pragma unroll
             for (int c = 0; c < 3; ++c)
@@ -368,15 +370,21 @@ adjF_kernel(const __grid_constant__ FusedMaps maps, Geom g, Mult<float> m, Field
             float mux[W], muy[W], muz[W];
 #pragma unroll
             for (int u = 0; u < W; ++u) {
-                const float ex0 = s0 * ex.v[u], ey0 = s0 * ey.v[u], ez0 = s0 * ez.v[u];
-                const float ezx = s0 * (u < W - 1 ? ez.v[u + 1] : ez4);
-                const float eyx = s0 * (u < W - 1 ? ey.v[u + 1] : ey4);
-                const float nx_ = bo[0][u] + (m.cE[2] * (ey0 - szp * eyz.v[u]) - m.cE[1] * (ez0 - syp * ezy.v[u]));
-                const float ny_ = bo[1][u] + (m.cE[0] * (ez0 - ezx) - m.cE[2] * (ex0 - szp * exz.v[u]));
-                const float nz_ = bo[2][u] + (m.cE[1] * (ex0 - syp * exy.v[u]) - m.cE[0] * (ey0 - eyx));
-                mux[u] = s0 * nx_;
-                muy[u] = s0 * ny_;
-                muz[u] = s0 * nz_;
+                // the rounding order of the two-kernel step's mu (fdtd_adjoint32.cu), fixed by
+                // intrinsics, which the compiler never contracts
+                const float ex0 = __fmul_rn(s0, ex.v[u]), ey0 = __fmul_rn(s0, ey.v[u]),
+                            ez0 = __fmul_rn(s0, ez.v[u]);
+                const float ezx = u < W - 1 ? ez.v[u + 1] : ez4;   // x+1, unscaled
+                const float eyx = u < W - 1 ? ey.v[u + 1] : ey4;
+                const float gx = __fmaf_rn(m.cE[2], __fmaf_rn(-szp, eyz.v[u], ey0),
+                                           __fmul_rn(-m.cE[1], __fmaf_rn(-syp, ezy.v[u], ez0)));
+                const float gy = __fmaf_rn(m.cE[0], __fmaf_rn(-s0, ezx, ez0),
+                                           __fmul_rn(-m.cE[2], __fmaf_rn(-szp, exz.v[u], ex0)));
+                const float gz = __fmaf_rn(m.cE[1], __fmaf_rn(-syp, exy.v[u], ex0),
+                                           __fmul_rn(-m.cE[0], __fmaf_rn(-s0, eyx, ey0)));
+                mux[u] = __fmul_rn(s0, __fadd_rn(bo[0][u], gx));
+                muy[u] = __fmul_rn(s0, __fadd_rn(bo[1][u], gy));
+                muz[u] = __fmul_rn(s0, __fadd_rn(bo[2][u], gz));
             }
             if (has_task) {
                 float* M = sM + sp * 3 * MSLOT;
@@ -415,7 +423,7 @@ adjF_kernel(const __grid_constant__ FusedMaps maps, Geom g, Mult<float> m, Field
                             m.cD[2], m.cB[2][0], m.cB[2][1], eo[0], racc + 3, t2);
                 const Q4 lx = ldq(Lq, e);
 #pragma unroll
-                for (int u = 0; u < W; ++u) v[u] = s0 * lx.v[u] + (t1[u] - t2[u]);
+                for (int u = 0; u < W; ++u) v[u] = __fmaf_rn(s0, lx.v[u], __fsub_rn(t1[u], t2[u]));
                 put_seg(out.c[0], po, dst, v);
                 // DT_z mu_x of lambda_E'_y
                 dtz_g<false>(Gmm, Gm, G0, Gp, e, lb, rb, m.cA[2], m.cD[2], m.cB[2][0], m.cB[2][1],
@@ -438,7 +446,7 @@ adjF_kernel(const __grid_constant__ FusedMaps maps, Geom g, Mult<float> m, Field
                             racc + 3, t2);
                 const Q4 lz = ldq(Lq + 2 * LSLOT, e);
 #pragma unroll
-                for (int u = 0; u < W; ++u) v[u] = s0 * lz.v[u] + (t1[u] - t2[u]);
+                for (int u = 0; u < W; ++u) v[u] = __fmaf_rn(s0, lz.v[u], __fsub_rn(t1[u], t2[u]));
                 put_seg(out.c[2], po, dst, v);
             }
 #pragma unroll

@@ -332,7 +332,9 @@ def test_one_kernel_reverse_step_equals_two_kernel_step(shape, sponge, monkeypat
         out[flag] = gpu_adjoint(shape, dx, dt, beta, delta, "f32", fields, lam0, n, probe, **kw)
     (l1, gb1, gd1), (l2, gb2, gd2) = out["0"], out["1"]
     for c in range(6):
-        assert np.array_equal(l1[c], l2[c]), f"component {c}"
+        nd = int(np.count_nonzero(l1[c] != l2[c]))
+        assert nd == 0, (f"component {c}: {nd} of {l1[c].size} differ, max |diff| "
+                         f"{np.max(np.abs(l1[c] - l2[c])):.3e}, at {np.argwhere(l1[c] != l2[c])[:4].tolist()}")
     scale = max(np.abs(gb2).max(), np.abs(gd2).max())
     assert np.max(np.abs(gb1 - gb2)) <= 1e-5 * scale
     assert np.max(np.abs(gd1 - gd2)) <= 1e-5 * scale
