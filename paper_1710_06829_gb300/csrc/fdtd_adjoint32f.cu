@@ -27,18 +27,21 @@
 //     planes q-2 .. q+1 (formed in the four previous iterations), lambda_E(q) (ring) and
 //     E^n(q) (HBM, one plane ahead).
 // One block barrier per plane.  mu of the halo planes z0-2, z0-1 and zend is recomputed by
-// each chunk.  The result goes to the other adjoint state set: CTAs of neighbouring tiles
+// each chunk.  Each thread's own rows of mu (five planes) and of lambda_E (three planes) are
+// also kept in tensor memory (TMEM, 128 columns per CTA), written once in phase A and read in
+// phase B, which then takes only the neighbouring rows from the shared ring.  The result goes to the other adjoint state set: CTAs of neighbouring tiles
 // read halos of lambda_E and lambda_B, so an in-place update would race.
 //
-// Tasks of phase A (four-cell row segment at x0+bx, row y0+by):
-//   t <  128: own rows by = t / 16, bx = 4 (t % 16) (these threads also run phase B)
-//   t in [128, 144): row -1;  [144, 160): row -2;  [160, 176): row 8   (bx = 4 (t % 16))
-//   t in [176, 186): bx = -4, rows -1 .. 8;   t in [186, 195): bx = 64, rows -1 .. 7
-//   t >= 195: a copy of task 194 whose result is dropped (the warp's shuffles need every
-//   lane); thread PRODUCER waits for and issues the TMA copies.
+// Threads: two groups of four warps; in phase B both take the 128 own segments (row o / 16,
+// x offset 4 (o % 16) for o = thread mod 128) and split the six transposed stencils three and
+// three.  Phase A (mu on 195 four-cell segments: the 128 own ones, rows -2, -1 and 8, and the
+// columns x0-4 (rows -1 .. 8) and x0+64 (rows -1 .. 7)) runs own rows 0-5 in warps 0-2, own
+// rows 6-7 in warp 7 (each in a warp of the TMEM quadrant that holds them), the halo in warps
+// 4-6; lanes without a segment compute a copy whose result is dropped (the warp's shuffles need
+// every lane).  Thread PRODUCER (an idle lane of warp 6) waits for and issues the TMA copies.
 // Every mbarrier wait is bounded; on expiry the CTA raises *err, drains its copies in flight
 // (bounded) and returns.
-#include "fdtd_seg.cuh"
+#include "fdtd_tmem.cuh"
 
 namespace fdtd {
 namespace adj32f {
@@ -49,7 +52,7 @@ constexpr int W = 4, TX = 64, TY = 8;
 constexpr int NSEG = TX / W;
 constexpr int NOWN = NSEG * TY;                                 // 128 own segments
 constexpr int NT = 2 * NOWN;                                    // 256 threads: two groups
-constexpr int PRODUCER = NT - 16;                               // lane 16 of the last warp
+constexpr int PRODUCER = NT - 48;                               // lane 16 of warp 6
 constexpr int LW = TX + 8, LH = TY + 4, LPL = LW * LH;          // lambda_E box 72 x 12
 constexpr int LSLOT = ((LPL * 4 + 127) / 128) * 128 / 4;
 constexpr int MH = TY + 3, MPL = LW * MH;                       // mu plane 72 x 11
@@ -58,7 +61,13 @@ constexpr int NL = 5, NM = 5, NS = 2;
 constexpr size_t OFF_M = (size_t)NL * 3 * LSLOT * 4;
 constexpr size_t OFF_Y = OFF_M + (size_t)NM * 3 * MSLOT * 4;      // DT_x mu_z, 2 x 128 x 4
 constexpr size_t OFF_BAR = OFF_Y + (size_t)2 * NOWN * W * 4;
-constexpr size_t SMEM = OFF_BAR + (size_t)(NS + 1) * 8;
+constexpr size_t OFF_TM = OFF_BAR + (size_t)(NS + 1) * 8;      // TMEM address
+constexpr size_t SMEM = OFF_TM + 16;
+// TMEM columns of a thread's own segment (lane = own segment o): mu component c of ring slot s
+// at 4 (c NM + s); lambda_E component c of plane p at COL_LE + 4 (3 c + (p's iteration mod 3))
+constexpr uint32_t TM_COLS = 128;   // per CTA (two CTAs per SM: 256 of the 512 columns)
+constexpr int COL_LE = 4 * 3 * NM;
+static_assert(COL_LE + 4 * 9 <= (int)TM_COLS, "TMEM columns");
 constexpr uint32_t UNIT_BYTES = 3u * LPL * 4;
 static_assert(LW == 72 && LH == 12, "the lambda_E boxes are the 72 x 12 boxes of encode_ebox_f32");
 
@@ -72,14 +81,14 @@ __device__ __forceinline__ void bracket_acc(float* acc, float w, float d0, float
     acc[2] = fmaf(ww, fmaf(-2.0f, d0, sc), acc[2]);
 }
 
-// DT_z of a mu component with plane slots Gmm (q-2), Gm (q-1), G0 (q), Gp (q+1) on the four
-// cells at e (transverse x, then y); gradient terms of D*_z (delta_z, beta_zx, beta_zy)
+// DT_z of a mu component on the four cells at e (transverse x, then y): the own row of planes
+// q-2 .. q+1 in cmm, cm, c0, cp (from TMEM), the neighbouring rows from the shared planes Gm
+// (q-1) and G0 (q); gradient terms of D*_z (delta_z, beta_zx, beta_zy)
 template <bool NEG>
-__device__ __forceinline__ void dtz_g(const float* Gmm, const float* Gm, const float* G0,
-                                      const float* Gp, int e, bool lb, bool rb, float cA, float cD,
-                                      float cBx, float cBy, const float* w, float* acc,
-                                      float out[4]) {
-    const Q4 cm = ldq(Gm, e), c0 = ldq(G0, e), cmm = ldq(Gmm, e), cp = ldq(Gp, e);
+__device__ __forceinline__ void dtz_g(const float* Gm, const float* G0, const Q4& cmm,
+                                      const Q4& cm, const Q4& c0, const Q4& cp, int e, bool lb,
+                                      bool rb, float cA, float cD, float cBx, float cBy,
+                                      const float* w, float* acc, float out[4]) {
     const Q4 ym = ldq(Gm, e - LW), y0m = ldq(G0, e - LW), yp = ldq(Gm, e + LW),
              y0p = ldq(G0, e + LW);
     float d[6];   // d[k] = G(q-1) - G(q) at x-1+k
@@ -97,14 +106,15 @@ __device__ __forceinline__ void dtz_g(const float* Gmm, const float* Gm, const f
     }
 }
 
-// DT_y (transverse x, then z); gradient terms of D*_y (delta_y, beta_yx, beta_yz)
+// DT_y (transverse x, then z); own rows of planes q-1, q, q+1 in zm, a0, zp; gradient terms of
+// D*_y (delta_y, beta_yx, beta_yz)
 template <bool NEG>
-__device__ __forceinline__ void dty_g(const float* Gm, const float* G0, const float* Gp, int e,
-                                      bool lb, bool rb, float cA, float cD, float cBx, float cBz,
+__device__ __forceinline__ void dty_g(const float* Gm, const float* G0, const float* Gp,
+                                      const Q4& zm, const Q4& a0, const Q4& zp, int e, bool lb,
+                                      bool rb, float cA, float cD, float cBx, float cBz,
                                       const float* w, float* acc, float out[4]) {
-    const Q4 a0 = ldq(G0, e), am = ldq(G0, e - LW), amm = ldq(G0, e - 2 * LW),
-             ap = ldq(G0, e + LW);
-    const Q4 zm = ldq(Gm, e), zmy = ldq(Gm, e - LW), zp = ldq(Gp, e), zpy = ldq(Gp, e - LW);
+    const Q4 am = ldq(G0, e - LW), amm = ldq(G0, e - 2 * LW), ap = ldq(G0, e + LW);
+    const Q4 zmy = ldq(Gm, e - LW), zpy = ldq(Gp, e - LW);
     float d[6];   // d[k] = G(y-1) - G(y) at x-1+k, plane q
 #pragma unroll
     for (int u = 0; u < 4; ++u) d[1 + u] = am.v[u] - a0.v[u];
@@ -120,13 +130,14 @@ __device__ __forceinline__ void dty_g(const float* Gm, const float* G0, const fl
     }
 }
 
-// DT_x (transverse y, then z); gradient terms of D*_x (delta_x, beta_xy, beta_xz)
+// DT_x (transverse y, then z); own rows of planes q-1, q, q+1 in Zm, R, Zp; gradient terms of
+// D*_x (delta_x, beta_xy, beta_xz)
 template <bool NEG>
-__device__ __forceinline__ void dtx_g(const float* Gm, const float* G0, const float* Gp, int e,
-                                      bool lb, bool rb, float cA, float cD, float cBy, float cBz,
+__device__ __forceinline__ void dtx_g(const float* Gm, const float* G0, const float* Gp,
+                                      const Q4& Zm, const Q4& R, const Q4& Zp, int e, bool lb,
+                                      bool rb, float cA, float cD, float cBy, float cBz,
                                       const float* w, float* acc, float out[4]) {
-    const Q4 R = ldq(G0, e), Ym = ldq(G0, e - LW), Yp = ldq(G0, e + LW), Zm = ldq(Gm, e),
-             Zp = ldq(Gp, e);
+    const Q4 Ym = ldq(G0, e - LW), Yp = ldq(G0, e + LW);
     float r[7];                         // G(q) at x-2 .. x+4
     float ym[5], yp[5], zm[5], zp[5];   // x-1 .. x+3
 #pragma unroll
@@ -202,29 +213,34 @@ adjF_kernel(const __grid_constant__ FusedMaps maps, Geom g, Mult<float> m, Field
             tma_load_3d(sL + (slot(P) * 3 + c) * LSLOT, &maps.e[c], x0, y0, wrapz(P), b);
     };
 
-    // ---- phase A task of this thread (segment at x0+abx, row y0+aby)
+    // ---- phase A task of this thread (segment at x0+abx, row y0+aby).  An own row is formed
+    // by a warp of the TMEM quadrant that holds it (warps w and w+4 reach lanes 32 (w mod 4) ..
+    // + 31, lane = own segment o): rows 0-5 by warps 0-2, rows 6-7 by warp 7; the halo by
+    // warps 4-6; warp 3 has no task
+    const int wq = tid >> 5;
     int abx = TX, aby = TY - 1;   // no task: a copy of the last right-column task
     bool has_task = true;
-    if (tid < 6 * NSEG) {   // group 0: own rows 0 .. 5
+    if (wq < 3) {   // own rows 0 .. 5
         aby = tid / NSEG;
         abx = W * (tid % NSEG);
-    } else if (tid < NOWN) {
+    } else if (wq == 7) {   // own rows 6, 7
+        const int t = tid - 7 * 32;
+        aby = 6 + t / NSEG;
+        abx = W * (t % NSEG);
+    } else if (wq == 3) {
         has_task = false;
     } else {
-        const int t = tid - NOWN;
-        if (t < 2 * NSEG) {   // own rows 6, 7
-            aby = 6 + t / NSEG;
-            abx = W * (t % NSEG);
-        } else if (t < 5 * NSEG) {   // halo rows -1, -2, 8
-            const int r = t / NSEG - 2;
+        const int t = tid - 4 * 32;
+        if (t < 3 * NSEG) {   // halo rows -1, -2, 8
+            const int r = t / NSEG;
             aby = r == 0 ? -1 : r == 1 ? -2 : TY;
             abx = W * (t % NSEG);
-        } else if (t < 5 * NSEG + 10) {   // left column, rows -1 .. 8
+        } else if (t < 3 * NSEG + 10) {   // left column, rows -1 .. 8
             abx = -W;
-            aby = t - 5 * NSEG - 1;
-        } else if (t < 5 * NSEG + 19) {   // right column, rows -1 .. 7
+            aby = t - 3 * NSEG - 1;
+        } else if (t < 3 * NSEG + 19) {   // right column, rows -1 .. 7
             abx = TX;
-            aby = t - 5 * NSEG - 11;
+            aby = t - 3 * NSEG - 11;
         } else {
             has_task = false;
         }
@@ -233,8 +249,8 @@ adjF_kernel(const __grid_constant__ FusedMaps maps, Geom g, Mult<float> m, Field
     const bool row16 = abx >= 0 && abx < TX;
     const bool a_rb = !has_task || !row16 || abx == TX - W;
     const bool a_own = has_task && row16 && aby >= 0 && aby < TY;
-    // phase A runs in every warp that has a task (warp 3 has none)
-    const bool a_warp = (tid >> 5) != 3;
+    // phase A runs in every warp that has a task (warp 3 has none); a_own is warp-uniform
+    const bool a_warp = wq != 3;
     const int ea = (aby + 2) * LW + (abx + 4);
     int jwa = (y0 + aby) % g.ny;
     if (jwa < 0) jwa += g.ny;
@@ -257,7 +273,15 @@ adjF_kernel(const __grid_constant__ FusedMaps maps, Geom g, Mult<float> m, Field
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
+    // TMEM: warp 0 allocates the CTA's columns, the address goes through shared memory
+    uint32_t* tm_slot = reinterpret_cast<uint32_t*>(smem + OFF_TM);
+    if (wq == 0) tm_alloc<TM_COLS>(tm_slot);
+    tm_fence_before();
     __syncthreads();
+    tm_fence_after();
+    const uint32_t tb = *tm_slot + ((uint32_t)(32 * (wq & 3)) << 16);
+    auto cmu = [&](int c, int sl) { return tb + (uint32_t)(4 * (c * NM + sl)); };
+    auto cle = [&](int c, int s3) { return tb + (uint32_t)(COL_LE + 4 * (3 * c + s3)); };
     int issued = 0;
     const int nunits = niter + 3;   // lambda_E planes z0-1 .. zend+1
     if (tid == PRODUCER) {
@@ -323,9 +347,11 @@ adjF_kernel(const __grid_constant__ FusedMaps maps, Geom g, Mult<float> m, Field
     // Plane bookkeeping by counters (no integer division in the loop): pw = p mod nz,
     // qw = q mod nz, sp = ring slot of plane p = (it + 2) mod 5 (plane q: sp + 3, q-2: + 1, ...)
     int pw = wrapz(z0 - 2), qw = wrapz(z0 - 4), sp = slot(z0 - 2);
+    int e3 = 0;   // it mod 3: TMEM slot of lambda_E(p); plane q's is (it + 1) mod 3
     auto inc5 = [](int a, int k) { return a + k >= NL ? a + k - NL : a + k; };
     for (; !failed && it <= niter + 4; ++it, qw = (qw + 1 == g.nz ? 0 : qw + 1),
-                                       pw = (pw + 1 == g.nz ? 0 : pw + 1), sp = inc5(sp, 1)) {
+                                       pw = (pw + 1 == g.nz ? 0 : pw + 1), sp = inc5(sp, 1),
+                                       e3 = (e3 == 2 ? 0 : e3 + 1)) {
         const int p = z0 - 2 + it;
         const int q = p - 2;
         bool ok = true;
@@ -392,6 +418,14 @@ adjF_kernel(const __grid_constant__ FusedMaps maps, Geom g, Mult<float> m, Field
                 stv(M + MSLOT, ea, muy);
                 stv(M + 2 * MSLOT, ea, muz);
             }
+            if (a_own) {   // own rows of mu(p) and lambda_E(p) to TMEM (warp-uniform)
+                tm_st(cmu(0, sp), mux);
+                tm_st(cmu(1, sp), muy);
+                tm_st(cmu(2, sp), muz);
+                tm_st(cle(0, e3), ex);
+                tm_st(cle(1, e3), ey);
+                tm_st(cle(2, e3), ez);
+            }
             if (a_own && p >= z0 && p < zend) {   // mu -> lambda_B' (own cells and their images)
                 const unsigned po = (unsigned)pw * plane;
                 put_seg(out.c[3], po, adst, mux);
@@ -406,47 +440,91 @@ adjF_kernel(const __grid_constant__ FusedMaps maps, Geom g, Mult<float> m, Field
 #pragma unroll
                 for (int u = 0; u < W; ++u) eo[c][u] = en[c][u];
             if (q + 1 < zend) load_e(qw + 1 == g.nz ? 0 : qw + 1, en);
-            const int sq = inc5(sp, 3);
-            const float* Gmm = sM + inc5(sp, 1) * 3 * MSLOT;
-            const float* Gm = sM + inc5(sp, 2) * 3 * MSLOT;
+            // mu planes q-2 .. q+1 (shared ring and, own rows, TMEM slots alike) and lambda_E(q)
+            const int smm = inc5(sp, 1), sm = inc5(sp, 2), sq = inc5(sp, 3), spp = inc5(sp, 4);
+            const int lq = e3 == 2 ? 0 : e3 + 1;
+            const float* Gm = sM + sm * 3 * MSLOT;
             const float* G0 = sM + sq * 3 * MSLOT;
-            const float* Gp = sM + inc5(sp, 4) * 3 * MSLOT;
-            const float* Lq = sL + sq * 3 * LSLOT;
+            const float* Gp = sM + spp * 3 * MSLOT;
             const float s0 = spy != nullptr ? spy[jw] * spz[qw] : 1.0f;
             const unsigned po = (unsigned)qw * plane;
             float t1[W], t2[W], v[W];
             if (!grp1) {
                 // lambda_E'_x = S lE_x + (DT_y mu_z - DT_z mu_y)
-                dty_g<false>(Gm + 2 * MSLOT, G0 + 2 * MSLOT, Gp + 2 * MSLOT, e, lb, rb, m.cA[1],
-                             m.cD[1], m.cB[1][0], m.cB[1][2], eo[0], racc + 0, t1);
-                dtz_g<true>(Gmm + MSLOT, Gm + MSLOT, G0 + MSLOT, Gp + MSLOT, e, lb, rb, m.cA[2],
-                            m.cD[2], m.cB[2][0], m.cB[2][1], eo[0], racc + 3, t2);
-                const Q4 lx = ldq(Lq, e);
+                {
+                    Q4 zm, z0_, zp;
+                    tm_ld(cmu(2, sm), zm);
+                    tm_ld(cmu(2, sq), z0_);
+                    tm_ld(cmu(2, spp), zp);
+                    tm_wait_ld(zm, z0_, zp);
+                    dty_g<false>(Gm + 2 * MSLOT, G0 + 2 * MSLOT, Gp + 2 * MSLOT, zm, z0_, zp, e, lb,
+                                 rb, m.cA[1], m.cD[1], m.cB[1][0], m.cB[1][2], eo[0], racc + 0, t1);
+                }
+                {
+                    Q4 cmm, cm, c0, cp, lx;
+                    tm_ld(cmu(1, smm), cmm);
+                    tm_ld(cmu(1, sm), cm);
+                    tm_ld(cmu(1, sq), c0);
+                    tm_ld(cmu(1, spp), cp);
+                    tm_ld(cle(0, lq), lx);
+                    tm_wait_ld(cmm, cm, c0, cp, lx);
+                    dtz_g<true>(Gm + MSLOT, G0 + MSLOT, cmm, cm, c0, cp, e, lb, rb, m.cA[2], m.cD[2],
+                                m.cB[2][0], m.cB[2][1], eo[0], racc + 3, t2);
 #pragma unroll
-                for (int u = 0; u < W; ++u) v[u] = __fmaf_rn(s0, lx.v[u], __fsub_rn(t1[u], t2[u]));
+                    for (int u = 0; u < W; ++u) v[u] = __fmaf_rn(s0, lx.v[u], __fsub_rn(t1[u], t2[u]));
+                }
                 put_seg(out.c[0], po, dst, v);
                 // DT_z mu_x of lambda_E'_y
-                dtz_g<false>(Gmm, Gm, G0, Gp, e, lb, rb, m.cA[2], m.cD[2], m.cB[2][0], m.cB[2][1],
-                             eo[1], racc + 3, ya);
-                const Q4 ly = ldq(Lq + LSLOT, e);
+                {
+                    Q4 cmm, cm, c0, cp, ly;
+                    tm_ld(cmu(0, smm), cmm);
+                    tm_ld(cmu(0, sm), cm);
+                    tm_ld(cmu(0, sq), c0);
+                    tm_ld(cmu(0, spp), cp);
+                    tm_ld(cle(1, lq), ly);
+                    tm_wait_ld(cmm, cm, c0, cp, ly);
+                    dtz_g<false>(Gm, G0, cmm, cm, c0, cp, e, lb, rb, m.cA[2], m.cD[2], m.cB[2][0],
+                                 m.cB[2][1], eo[1], racc + 3, ya);
 #pragma unroll
-                for (int u = 0; u < W; ++u) yl[u] = ly.v[u];
+                    for (int u = 0; u < W; ++u) yl[u] = ly.v[u];
+                }
                 ys0 = s0;
                 ypo = po;
                 ypend = true;
             } else {
                 // DT_x mu_z of lambda_E'_y, to group 0
-                dtx_g<true>(Gm + 2 * MSLOT, G0 + 2 * MSLOT, Gp + 2 * MSLOT, e, lb, rb, m.cA[0],
-                            m.cD[0], m.cB[0][1], m.cB[0][2], eo[0], racc + 0, t1);
+                {
+                    Q4 zm, z0_, zp;
+                    tm_ld(cmu(2, sm), zm);
+                    tm_ld(cmu(2, sq), z0_);
+                    tm_ld(cmu(2, spp), zp);
+                    tm_wait_ld(zm, z0_, zp);
+                    dtx_g<true>(Gm + 2 * MSLOT, G0 + 2 * MSLOT, Gp + 2 * MSLOT, zm, z0_, zp, e, lb,
+                                rb, m.cA[0], m.cD[0], m.cB[0][1], m.cB[0][2], eo[0], racc + 0, t1);
+                }
                 stv(sY + (it & 1) * NOWN * W, o * W, t1);
                 // lambda_E'_z = S lE_z + (DT_x mu_y - DT_y mu_x)
-                dtx_g<false>(Gm + MSLOT, G0 + MSLOT, Gp + MSLOT, e, lb, rb, m.cA[0], m.cD[0],
-                             m.cB[0][1], m.cB[0][2], eo[1], racc + 0, t1);
-                dty_g<true>(Gm, G0, Gp, e, lb, rb, m.cA[1], m.cD[1], m.cB[1][0], m.cB[1][2], eo[1],
-                            racc + 3, t2);
-                const Q4 lz = ldq(Lq + 2 * LSLOT, e);
+                {
+                    Q4 ym, y0_, yp;
+                    tm_ld(cmu(1, sm), ym);
+                    tm_ld(cmu(1, sq), y0_);
+                    tm_ld(cmu(1, spp), yp);
+                    tm_wait_ld(ym, y0_, yp);
+                    dtx_g<false>(Gm + MSLOT, G0 + MSLOT, Gp + MSLOT, ym, y0_, yp, e, lb, rb, m.cA[0],
+                                 m.cD[0], m.cB[0][1], m.cB[0][2], eo[1], racc + 0, t1);
+                }
+                {
+                    Q4 xm, x0_, xp, lz;
+                    tm_ld(cmu(0, sm), xm);
+                    tm_ld(cmu(0, sq), x0_);
+                    tm_ld(cmu(0, spp), xp);
+                    tm_ld(cle(2, lq), lz);
+                    tm_wait_ld(xm, x0_, xp, lz);
+                    dty_g<true>(Gm, G0, Gp, xm, x0_, xp, e, lb, rb, m.cA[1], m.cD[1], m.cB[1][0],
+                                m.cB[1][2], eo[1], racc + 3, t2);
 #pragma unroll
-                for (int u = 0; u < W; ++u) v[u] = __fmaf_rn(s0, lz.v[u], __fsub_rn(t1[u], t2[u]));
+                    for (int u = 0; u < W; ++u) v[u] = __fmaf_rn(s0, lz.v[u], __fsub_rn(t1[u], t2[u]));
+                }
                 put_seg(out.c[2], po, dst, v);
             }
 #pragma unroll
@@ -461,7 +539,12 @@ adjF_kernel(const __grid_constant__ FusedMaps maps, Geom g, Mult<float> m, Field
         bool ok_next = true;
         if (tid == PRODUCER && it + 1 < nunits)
             ok_next = mbar_wait(&bar[(it + 1) % NS], (uint32_t)(((it + 1) / NS) & 1));
-        if (__syncthreads_or(!ok || !ok_next)) {
+        // the TMEM rows stored in this iteration are read by other warps after the barrier
+        tm_wait_st();
+        tm_fence_before();
+        const bool stop = __syncthreads_or(!ok || !ok_next);
+        tm_fence_after();
+        if (stop) {
             failed = true;
             break;
         }
@@ -472,15 +555,18 @@ adjF_kernel(const __grid_constant__ FusedMaps maps, Geom g, Mult<float> m, Field
             issued = it + 3;
         }
     }
-    if (failed) {
-        if (tid == PRODUCER) {
-            atomicOr(err, ERR_WAIT);
-            if (it == 0) mbar_wait(&bar[NS], 0);
-            for (int u = it; u < issued; ++u) mbar_wait(&bar[u % NS], (uint32_t)((u / NS) & 1));
-        }
-        __syncthreads();
-        return;
+    if (failed && tid == PRODUCER) {   // drain this CTA's copies in flight
+        atomicOr(err, ERR_WAIT);
+        if (it == 0) mbar_wait(&bar[NS], 0);
+        for (int u = it; u < issued; ++u) mbar_wait(&bar[u % NS], (uint32_t)((u / NS) & 1));
     }
+    // release the TMEM columns (every path reaches this point)
+    tm_wait_st();
+    tm_fence_before();
+    __syncthreads();
+    tm_fence_after();
+    if (wq == 0) tm_dealloc<TM_COLS>(*tm_slot);
+    if (failed) return;
     // block reduction of the FP64 accumulators: entry k of group 0 is coefficient 3 + k,
     // entry k of group 1 coefficient k
     __shared__ double red[NT / 32][9];
@@ -514,7 +600,9 @@ bool adjoint32f_prepare() {
 
 static int adjoint32f_tz(const Geom& g) {
     static int slots = -1;
-    if (slots < 0) slots = resident_slots((const void*)adj32f::adjF_kernel, adj32f::NT, adj32f::SMEM);
+    if (slots < 0)
+        slots = resident_slots_tmem((const void*)adj32f::adjF_kernel, adj32f::NT, adj32f::SMEM,
+                                    adj32f::TM_COLS);
     return zchunk_len((g.nx / adj32f::TX) * (g.ny / adj32f::TY), g.nz, slots, 16, 64);
 }
 

@@ -547,7 +547,7 @@ int resident_slots(const void* kernel, int threads, size_t smem) {
 // CTA limit and its TMEM columns (512 per SM).  The occupancy API is not used here: for a
 // kernel that allocates tensor memory it reports fewer resident CTAs than actually run (one
 // where three fit), which made the z-chunk choice launch too few CTAs on small grids.
-static int resident_slots_tmem(const void* kernel, int threads, size_t smem, int tmem_cols) {
+int resident_slots_tmem(const void* kernel, int threads, size_t smem, int tmem_cols) {
     int dev = 0, sms = 0, smem_sm = 0, resv = 0, regs_sm = 0, thr_sm = 0, blk_sm = 0;
     cudaFuncAttributes fa;
     if (cudaGetDevice(&dev) != cudaSuccess ||

@@ -167,6 +167,9 @@ void launch_reduce_grad(const double* part, int nblocks, GradScale sc, double* g
 // z-chunk length in [tz_min, tz_max] of a tiled plane-marching kernel with `tiles_xy` CTAs per
 // z-chunk that fills whole waves of `slots` CTAs best.
 int resident_slots(const void* kernel, int threads, size_t smem);
+// the same for a kernel that allocates tmem_cols TMEM columns per CTA (the occupancy API
+// under-reports those)
+int resident_slots_tmem(const void* kernel, int threads, size_t smem, int tmem_cols);
 int zchunk_len(int tiles_xy, int nz, int slots, int tz_min, int tz_max);
 
 // thread-local error message

@@ -73,6 +73,13 @@ __device__ __forceinline__ void tm_wait_ld(Q4& a, Q4& b, Q4& c) {
                    "+f"(b.v[1]), "+f"(b.v[2]), "+f"(b.v[3]), "+f"(c.v[0]), "+f"(c.v[1]),
                    "+f"(c.v[2]), "+f"(c.v[3])::"memory");
 }
+__device__ __forceinline__ void tm_wait_ld(Q4& a, Q4& b, Q4& c, Q4& d) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+f"(a.v[0]), "+f"(a.v[1]), "+f"(a.v[2]), "+f"(a.v[3]), "+f"(b.v[0]),
+                   "+f"(b.v[1]), "+f"(b.v[2]), "+f"(b.v[3]), "+f"(c.v[0]), "+f"(c.v[1]),
+                   "+f"(c.v[2]), "+f"(c.v[3]), "+f"(d.v[0]), "+f"(d.v[1]), "+f"(d.v[2]),
+                   "+f"(d.v[3])::"memory");
+}
 __device__ __forceinline__ void tm_wait_ld(Q4& a, Q4& b, Q4& c, Q4& d, Q4& e) {
     asm volatile("tcgen05.wait::ld.sync.aligned;"
                  : "+f"(a.v[0]), "+f"(a.v[1]), "+f"(a.v[2]), "+f"(a.v[3]), "+f"(b.v[0]),
