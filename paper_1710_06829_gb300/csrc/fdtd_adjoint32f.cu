@@ -567,15 +567,24 @@ adjF_kernel(const __grid_constant__ FusedMaps maps, Geom g, Mult<float> m, Field
     tm_fence_after();
     if (wq == 0) tm_dealloc<TM_COLS>(*tm_slot);
     if (failed) return;
-    // block reduction of the FP64 accumulators: entry k of group 0 is coefficient 3 + k,
-    // entry k of group 1 coefficient k
+    // block reduction: entry k of group 0 is coefficient 3 + k, entry k of group 1 coefficient
+    // k.  Within a warp the compensated pairs (value gs - gc) are added in FP32 with an exact
+    // two-sum at every step (Knuth's TwoSum: s + e = a + b exactly), so no FP64 arithmetic runs
+    // until one conversion per warp; across warps and blocks the sums are FP64
     __shared__ double red[NT / 32][9];
     const int wp = tid >> 5, l = tid & 31;
 #pragma unroll
     for (int k = 0; k < 6; ++k) {
-        double v = (double)gs[k] - (double)gc[k];
-        for (int s = 16; s > 0; s >>= 1) v += __shfl_down_sync(FULL, v, s);
-        if (l == 0) red[wp][grp1 ? k : 3 + k] = v;
+        float vs = gs[k], vc = gc[k];
+        for (int sh = 16; sh > 0; sh >>= 1) {
+            const float os = __shfl_down_sync(FULL, vs, sh), oc = __shfl_down_sync(FULL, vc, sh);
+            const float t = __fadd_rn(vs, os);
+            const float bv = __fsub_rn(t, vs);
+            const float err = __fadd_rn(__fsub_rn(vs, __fsub_rn(t, bv)), __fsub_rn(os, bv));
+            vs = t;
+            vc = __fsub_rn(__fadd_rn(vc, oc), err);
+        }
+        if (l == 0) red[wp][grp1 ? k : 3 + k] = (double)vs - (double)vc;
     }
     if (l < 3) red[wp][grp1 ? 6 + l : l] = 0.0;
     __syncthreads();
