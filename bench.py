@@ -43,7 +43,7 @@ PIC_N = 1 << 22
 PIC_WORKLOAD = ("PIC cycle 512x256x256 FP32, 16-cell absorbing layers on y and z, extended "
                 "stencil (seeded coefficient set 0), Courant 0.95; gamma=10 electron bunch, "
                 "2^22 macro-particles, sigma_par=4, sigma_perp=8 cells, along +x")
-STEP_TRAFFIC = {"sources_sha256_16": "04035c41cf1c3273", "bytes_per_launch": 829302528}
+STEP_TRAFFIC = {"sources_sha256_16": "01c68493b745f82c", "bytes_per_launch": 828906496}
 STEP_SOURCES = ["fdtd_fused32.cu", "fdtd_seg.cuh", "fdtd_tma.cuh", "fdtd_internal.cuh", "fdtd_tmem.cuh"]
 
 
