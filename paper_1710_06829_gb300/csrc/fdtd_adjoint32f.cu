@@ -57,8 +57,9 @@ constexpr int LW = TX + 8, LH = TY + 4, LPL = LW * LH;          // lambda_E box 
 constexpr int LSLOT = ((LPL * 4 + 127) / 128) * 128 / 4;
 constexpr int MH = TY + 3, MPL = LW * MH;                       // mu plane 72 x 11
 constexpr int MSLOT = ((MPL * 4 + 127) / 128) * 128 / 4;
-constexpr int NL = 5, NM = 5, NS = 2;
-constexpr size_t OFF_M = (size_t)NL * 3 * LSLOT * 4;
+constexpr int NL = 3, NB = 2, NM = 5, NS = 2;   // lambda_E, lambda_B, mu ring slots
+constexpr size_t OFF_B = (size_t)NL * 3 * LSLOT * 4;             // lambda_B boxes 72 x 11
+constexpr size_t OFF_M = OFF_B + (size_t)NB * 3 * MSLOT * 4;
 constexpr size_t OFF_Y = OFF_M + (size_t)NM * 3 * MSLOT * 4;      // DT_x mu_z, 2 x 128 x 4
 constexpr size_t OFF_BAR = OFF_Y + (size_t)2 * NOWN * W * 4;
 constexpr size_t OFF_TM = OFF_BAR + (size_t)(NS + 1) * 8;      // TMEM address
@@ -68,8 +69,10 @@ constexpr size_t SMEM = OFF_TM + 16;
 constexpr uint32_t TM_COLS = 128;   // per CTA (two CTAs per SM: 256 of the 512 columns)
 constexpr int COL_LE = 4 * 3 * NM;
 static_assert(COL_LE + 4 * 9 <= (int)TM_COLS, "TMEM columns");
-constexpr uint32_t UNIT_BYTES = 3u * LPL * 4;
+constexpr uint32_t UNIT_BYTES = 3u * (LPL + MPL) * 4;   // lambda_E and lambda_B boxes
+constexpr uint32_t PRO_BYTES = 3u * LPL * 4;
 static_assert(LW == 72 && LH == 12, "the lambda_E boxes are the 72 x 12 boxes of encode_ebox_f32");
+static_assert(MH == 11, "the lambda_B boxes are 72 x 11 (encode_box_f32)");
 
 // Accumulates s w(u) (T_delta, T_beta_b, T_beta_c) into acc[0..2] for the four cells
 template <bool NEG>
@@ -182,6 +185,7 @@ adjF_kernel(const __grid_constant__ FusedMaps maps, Geom g, Mult<float> m, Field
             int* __restrict__ err) {
     extern __shared__ __align__(128) unsigned char smem[];
     float* sL = reinterpret_cast<float*>(smem);
+    float* sB = reinterpret_cast<float*>(smem + OFF_B);
     float* sM = reinterpret_cast<float*>(smem + OFF_M);
     float* sY = reinterpret_cast<float*>(smem + OFF_Y);
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem + OFF_BAR);
@@ -202,15 +206,20 @@ adjF_kernel(const __grid_constant__ FusedMaps maps, Geom g, Mult<float> m, Field
         int r = q % g.nz;
         return r < 0 ? r + g.nz : r;
     };
-    // ring slot of plane P (P >= z0-4): lambda_E and mu rings alike
-    auto slot = [&](int P) { return (P - z0 + 4) % NL; };
-    // unit u: the three lambda_E boxes of plane z0-1+u (the leading plane of iteration u)
+    // ring slots of plane P: lambda_E (P >= z0-2), mu (P >= z0-4); lambda_B of plane P in slot
+    // (P - z0) mod 2
+    auto lslot = [&](int P) { return (P - z0 + 2) % NL; };
+    auto slot = [&](int P) { return (P - z0 + 4) % NM; };
+    // unit u: the lambda_E boxes of plane z0-1+u (the leading plane of iteration u) and the
+    // lambda_B boxes of plane z0-2+u (phase A's plane in iteration u)
     auto issue_unit = [&](int u) {
         const int P = z0 - 1 + u;
         uint64_t* b = &bar[u % NS];
         mbar_expect_tx(b, UNIT_BYTES);
-        for (int c = 0; c < 3; ++c)
-            tma_load_3d(sL + (slot(P) * 3 + c) * LSLOT, &maps.e[c], x0, y0, wrapz(P), b);
+        for (int c = 0; c < 3; ++c) {
+            tma_load_3d(sL + (lslot(P) * 3 + c) * LSLOT, &maps.e[c], x0, y0, wrapz(P), b);
+            tma_load_3d(sB + ((u & 1) * 3 + c) * MSLOT, &maps.b[c], x0, y0, wrapz(P - 1), b);
+        }
     };
 
     // ---- phase A task of this thread (segment at x0+abx, row y0+aby).  An own row is formed
@@ -256,7 +265,6 @@ adjF_kernel(const __grid_constant__ FusedMaps maps, Geom g, Mult<float> m, Field
     if (jwa < 0) jwa += g.ny;
     const int jwap = jwa + 1 == g.ny ? 0 : jwa + 1;
     const unsigned plane = (unsigned)g.plane;
-    const unsigned a_off = (unsigned)((y0 + aby + PY) * g.nxp + (x0 + abx + PX));
     const SegOut adst = seg_out(g, x0 + (a_own ? abx : 0), y0 + (a_own ? aby : 0), edge);
 
     // ---- phase B: own segment o of this thread, group 0 (warps 0-3) or 1 (warps 4-7)
@@ -286,36 +294,25 @@ adjF_kernel(const __grid_constant__ FusedMaps maps, Geom g, Mult<float> m, Field
     const int nunits = niter + 3;   // lambda_E planes z0-1 .. zend+1
     if (tid == PRODUCER) {
         const int P = z0 - 2;
-        mbar_expect_tx(&bar[NS], UNIT_BYTES);
+        mbar_expect_tx(&bar[NS], PRO_BYTES);
         for (int c = 0; c < 3; ++c)
-            tma_load_3d(sL + (slot(P) * 3 + c) * LSLOT, &maps.e[c], x0, y0, wrapz(P), &bar[NS]);
+            tma_load_3d(sL + (lslot(P) * 3 + c) * LSLOT, &maps.e[c], x0, y0, wrapz(P), &bar[NS]);
         for (int u = 0; u < 2 && u < nunits; ++u) {
             issue_unit(u);
             issued = u + 1;
         }
     }
 
-    // lambda_B of the phase A segment and the two E^n components of phase B (group 0: E_x,
-    // E_y; group 1: E_y, E_z), read from HBM one plane ahead into *n, moved to *o when used
-    float bo[3][W], bn[3][W], eo[2][W], en[2][W];
+    // the two E^n components of phase B (group 0: E_x, E_y; group 1: E_y, E_z), read from HBM
+    // one plane ahead into en, moved to eo when used
+    float eo[2][W], en[2][W];
     const float* ea0 = grp1 ? e_y : e_x;
     const float* ea1 = grp1 ? e_z : e_y;
-    auto load_b = [&](int pw, float (&to)[3][W]) {
-        const unsigned off = (unsigned)pw * plane + a_off;
-#pragma unroll
-        for (int c = 0; c < 3; ++c)
-            unpackv(*reinterpret_cast<const float4*>(lam.c[3 + c] + off), to[c]);
-    };
     auto load_e = [&](int qw, float (&to)[2][W]) {
         const unsigned off = (unsigned)qw * plane + dst.ro;
         unpackv(__ldg(reinterpret_cast<const float4*>(ea0 + off)), to[0]);
         unpackv(__ldg(reinterpret_cast<const float4*>(ea1 + off)), to[1]);
     };
-#pragma unroll
-    for (int c = 0; c < 3; ++c)
-#pragma unroll
-        for (int u = 0; u < W; ++u) bn[c][u] = 0.0f;
-    load_b(wrapz(z0 - 2), bn);
     load_e(wrapz(z0), en);
 
     // gradient partial sums: group 0 holds D*_y, D*_z (entries 3..8), group 1 D*_x, D*_y (0..5).
@@ -346,11 +343,12 @@ adjF_kernel(const __grid_constant__ FusedMaps maps, Geom g, Mult<float> m, Field
     // (z0 <= q < zend); the last iteration only completes lambda_E'_y of plane zend-1.
     // Plane bookkeeping by counters (no integer division in the loop): pw = p mod nz,
     // qw = q mod nz, sp = ring slot of plane p = (it + 2) mod 5 (plane q: sp + 3, q-2: + 1, ...)
-    int pw = wrapz(z0 - 2), qw = wrapz(z0 - 4), sp = slot(z0 - 2);
+    int pw = wrapz(z0 - 2), qw = wrapz(z0 - 4), sp = slot(z0 - 2), lp = lslot(z0 - 2);
     int e3 = 0;   // it mod 3: TMEM slot of lambda_E(p); plane q's is (it + 1) mod 3
-    auto inc5 = [](int a, int k) { return a + k >= NL ? a + k - NL : a + k; };
+    auto inc5 = [](int a, int k) { return a + k >= NM ? a + k - NM : a + k; };   // mu ring slots
     for (; !failed && it <= niter + 4; ++it, qw = (qw + 1 == g.nz ? 0 : qw + 1),
                                        pw = (pw + 1 == g.nz ? 0 : pw + 1), sp = inc5(sp, 1),
+                                       lp = (lp == NL - 1 ? 0 : lp + 1),
                                        e3 = (e3 == 2 ? 0 : e3 + 1)) {
         const int p = z0 - 2 + it;
         const int q = p - 2;
@@ -372,13 +370,10 @@ adjF_kernel(const __grid_constant__ FusedMaps maps, Geom g, Mult<float> m, Field
         // ---- phase A: mu(p) (warps with a task)
         if (ok && p <= zend && a_warp) {
             const int pw1 = pw + 1 == g.nz ? 0 : pw + 1;
-#pragma unroll
-            for (int c = 0; c < 3; ++c)
-#pragma unroll
-                for (int u = 0; u < W; ++u) bo[c][u] = bn[c][u];
-            if (p + 1 <= zend) load_b(pw1, bn);
-            const float* L0 = sL + sp * 3 * LSLOT;
-            const float* L1 = sL + inc5(sp, 1) * 3 * LSLOT;
+            const float* L0 = sL + lp * 3 * LSLOT;
+            const float* L1 = sL + (lp == NL - 1 ? 0 : lp + 1) * 3 * LSLOT;
+            const float* Bp = sB + (it & 1) * 3 * MSLOT;
+            const Q4 bxq = ldq(Bp, ea), byq = ldq(Bp + MSLOT, ea), bzq = ldq(Bp + 2 * MSLOT, ea);
             const Q4 ex = ldq(L0, ea), ey = ldq(L0 + LSLOT, ea), ez = ldq(L0 + 2 * LSLOT, ea);
             const Q4 exy = ldq(L0, ea + LW), ezy = ldq(L0 + 2 * LSLOT, ea + LW);
             const Q4 exz = ldq(L1, ea), eyz = ldq(L1 + LSLOT, ea);
@@ -408,9 +403,9 @@ adjF_kernel(const __grid_constant__ FusedMaps maps, Geom g, Mult<float> m, Field
                                            __fmul_rn(-m.cE[2], __fmaf_rn(-szp, exz.v[u], ex0)));
                 const float gz = __fmaf_rn(m.cE[1], __fmaf_rn(-syp, exy.v[u], ex0),
                                            __fmul_rn(-m.cE[0], __fmaf_rn(-s0, eyx, ey0)));
-                mux[u] = __fmul_rn(s0, __fadd_rn(bo[0][u], gx));
-                muy[u] = __fmul_rn(s0, __fadd_rn(bo[1][u], gy));
-                muz[u] = __fmul_rn(s0, __fadd_rn(bo[2][u], gz));
+                mux[u] = __fmul_rn(s0, __fadd_rn(bxq.v[u], gx));
+                muy[u] = __fmul_rn(s0, __fadd_rn(byq.v[u], gy));
+                muz[u] = __fmul_rn(s0, __fadd_rn(bzq.v[u], gz));
             }
             if (has_task) {
                 float* M = sM + sp * 3 * MSLOT;
@@ -548,7 +543,8 @@ adjF_kernel(const __grid_constant__ FusedMaps maps, Geom g, Mult<float> m, Field
             failed = true;
             break;
         }
-        // the slot of plane q (last read by this iteration's phase B) takes plane p+3
+        // the lambda_E slot of plane p and the lambda_B slot of plane p (both read in this
+        // iteration's phase A) take planes p+3 and p+2
         if (tid == PRODUCER && it + 2 < nunits) {
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             issue_unit(it + 2);
@@ -620,7 +616,8 @@ int adjoint32f_blocks(const Geom& g) {
     return (g.nx / adj32f::TX) * (g.ny / adj32f::TY) * ((g.nz + tz - 1) / tz);
 }
 
-// maps.e[c]: 72 x 12 boxes of lambda_E component c of the input set `lam`; E: the forward
+// maps.e[c]: 72 x 12 boxes of lambda_E component c of the input set `lam`, maps.b[c]: 72 x 11
+// boxes of its lambda_B component c; E: the forward
 // E^n of the step (padded arrays); the result goes to `out` (the other set)
 void launch_adjoint32_fused(const FusedMaps& maps, const Geom& g, const Mult<float>& m,
                             FieldSet<float> lam, FieldSet<float> out, const float* const E[3],

@@ -302,6 +302,11 @@ bool encode_ebox_f32(CUtensorMap* map, const Geom& g, float* base) {
     return encode<float>(map, g, base, Layout<float>::EW, Layout<float>::EH);
 }
 
+// a bw x bh box (FP32) of one padded array
+bool encode_box_f32(CUtensorMap* map, const Geom& g, float* base, int bw, int bh) {
+    return encode<float>(map, g, base, bw, bh);
+}
+
 template <typename T>
 FusedPlan* fused_plan_create(const Geom& g, T* const set0[6], T* const set1[6]) {
     if (!fused_supported<T>(g)) return nullptr;

@@ -50,6 +50,7 @@ void launch_omega(const double alpha[3], const double beta[3][3], const double d
                   const double dx[3], int dims, const double* k_dev, int n, double* out_dev,
                   cudaStream_t st);
 bool encode_ebox_f32(CUtensorMap* map, const Geom& g, float* base);
+bool encode_box_f32(CUtensorMap* map, const Geom& g, float* base, int bw, int bh);
 bool adjoint32_supported(const Geom& g);
 int adjoint32_blocks(const Geom& g);
 bool adjoint32_prepare();
@@ -273,7 +274,7 @@ struct fdtd_handle {
     FusedMaps lam_maps;                 // .e[c]: TMA descriptors of lambda_B component c (FP32)
     bool lam_staged = false;            // lam_maps valid: the staged FP32 adjoint E kernel runs
     // FP32 one-kernel reverse step: two adjoint state sets (the kernel writes the other one),
-    // lam_emaps[s].e[c] the TMA descriptors of lambda_E component c of set s
+    // lam_emaps[s].e[c] / .b[c] the TMA descriptors of lambda_E / lambda_B component c of set s
     bool lam_fused = false;
     int lam_sets = 1, lam_cur = 0;
     FusedMaps lam_emaps[2];
@@ -633,7 +634,8 @@ static int ensure_lam(fdtd_handle* h) {
         bool ok = true;
         for (int s = 0; s < 2; ++s)
             for (int c = 0; c < 3; ++c)
-                ok = ok && encode_ebox_f32(&h->lam_emaps[s].e[c], h->g, (float*)h->lam_arr_set(s, c));
+                ok = ok && encode_ebox_f32(&h->lam_emaps[s].e[c], h->g, (float*)h->lam_arr_set(s, c)) &&
+                     encode_box_f32(&h->lam_emaps[s].b[c], h->g, (float*)h->lam_arr_set(s, 3 + c), 72, 11);
         h->lam_fused = ok;   // otherwise the two-kernel reverse step runs on set 0
     }
     if (!h->lam_fused && h->grid.dtype == FDTD_F32 && h->plan && adjoint32e_supported(h->g) &&

@@ -186,6 +186,47 @@ def test_batched_2d_adjoint_gradient_is_the_sum_over_members():
     assert g[2] == 0 and g[5] == 0 and g[6] == 0 and g[7] == 0 and g[11] == 0
 
 
+def test_batched_2d_adjoint_fp32_one_kernel_matches_oracle():
+    """Batched 2D problems (z indexes independent members) through the FP32 one-kernel reverse
+    step (a TMA-eligible grid): each member's lambda against the oracle's 2D adjoint on the
+    FP32-rounded multipliers, the gradient against the sum over members, the absent z axis's
+    entries exactly zero."""
+    shape = (64, 16, 5)
+    nx, ny, nz = shape
+    beta = np.zeros((3, 3))
+    beta[0, 1], beta[1, 0] = 0.02, -0.01
+    delta = np.array([-0.04, -0.02, 0.0])
+    dx = [1.0, 1.0, 1.0]
+    dt = 0.9 * D.dt_max(beta, delta, dx, 2)
+    fields = [f.astype(np.float32) for f in inputs.random_fields(shape, 33)]
+    lam0 = [f.astype(np.float32) for f in inputs.random_fields(shape, 34)]
+    n = 5
+    rng = np.random.default_rng(2)
+    tgt = rng.standard_normal((n, nz, ny)).astype(np.float32)
+    sm = S.Simulation(shape, dx, dt, beta, delta, dims=2, dtype="f32", batched=True)
+    sm.set_state([torch.from_numpy(f) for f in fields])
+    sm.step(n, record=True)
+    sm.set_adjoint([torch.from_numpy(f) for f in lam0])
+    grad = torch.zeros(12, dtype=torch.float64, device="cuda")
+    sm.step_adjoint(n, grad, probe=S.Probe(1, 7, torch.from_numpy(tgt).cuda()))
+    lam = [t.double().cpu().numpy() for t in sm.get_adjoint()]
+    g = grad.cpu().numpy()
+    sm.close()
+    c = rounded_coeffs(beta, delta, dx, dt, 2, np.float32)
+    gb_sum, gd_sum = np.zeros((3, 3)), np.zeros(3)
+    for k in range(nz):
+        rl, gb, gd = oracle_adjoint(c, [f[k:k + 1].astype(np.float64) for f in fields],
+                                    [f[k:k + 1].astype(np.float64) for f in lam0], n, None,
+                                    (1, 7, tgt[:, k:k + 1, :].astype(np.float64)))
+        assert_elementwise([x[k:k + 1] for x in lam], rl, 2e-5, f"member {k}")
+        gb_sum += gb
+        gd_sum += gd
+    scale = max(np.abs(gb_sum).max(), np.abs(gd_sum).max())
+    assert np.max(np.abs(g[:9].reshape(3, 3) - gb_sum)) <= 2e-5 * scale
+    assert np.max(np.abs(g[9:] - gd_sum)) <= 2e-5 * scale
+    assert g[2] == 0 and g[5] == 0 and g[6] == 0 and g[7] == 0 and g[11] == 0
+
+
 @pytest.mark.parametrize("shape,sponge", [((64, 16, 12), False), ((128, 24, 40), True), ((64, 8, 1), False)])
 def test_adjoint_fp32_staged_kernel_matches_oracle(shape, sponge):
     """FP32 adjoint on TMA-eligible grids (nx % 64 == 0, ny % 8 == 0) vs the oracle adjoint run
