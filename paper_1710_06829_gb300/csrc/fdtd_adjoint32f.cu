@@ -177,6 +177,10 @@ __device__ __forceinline__ void dtx_g(const float* Gm, const float* G0, const fl
     }
 }
 
+// SP: absorbing layers present (spy, spz not null); without them S = 1 is a compile-time
+// constant and the multiplications by it fold away (same results: x * 1 and fma(-1, y, x) are
+// exact)
+template <bool SP>
 __global__ void __launch_bounds__(NT, 2)
 adjF_kernel(const __grid_constant__ FusedMaps maps, Geom g, Mult<float> m, FieldSet<float> lam,
             FieldSet<float> out, const float* __restrict__ e_x, const float* __restrict__ e_y,
@@ -383,7 +387,7 @@ adjF_kernel(const __grid_constant__ FusedMaps maps, Geom g, Mult<float> m, Field
                 ez4 = L0[2 * LSLOT + ea + 4];
             }
             float s0 = 1.0f, syp = 1.0f, szp = 1.0f;
-            if (spy != nullptr) {
+            if (SP) {
                 s0 = spy[jwa] * spz[pw];
                 syp = spy[jwap] * spz[pw];
                 szp = spy[jwa] * spz[pw1];
@@ -441,7 +445,7 @@ adjF_kernel(const __grid_constant__ FusedMaps maps, Geom g, Mult<float> m, Field
             const float* Gm = sM + sm * 3 * MSLOT;
             const float* G0 = sM + sq * 3 * MSLOT;
             const float* Gp = sM + spp * 3 * MSLOT;
-            const float s0 = spy != nullptr ? spy[jw] * spz[qw] : 1.0f;
+            const float s0 = SP ? spy[jw] * spz[qw] : 1.0f;
             const unsigned po = (unsigned)qw * plane;
             float t1[W], t2[W], v[W];
             if (!grp1) {
@@ -599,14 +603,18 @@ bool adjoint32f_supported(const Geom& g) {
 }
 
 bool adjoint32f_prepare() {
-    return cudaFuncSetAttribute(adj32f::adjF_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    return cudaFuncSetAttribute(adj32f::adjF_kernel<true>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)adj32f::SMEM) == cudaSuccess &&
+           cudaFuncSetAttribute(adj32f::adjF_kernel<false>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)adj32f::SMEM) == cudaSuccess;
 }
 
 static int adjoint32f_tz(const Geom& g) {
     static int slots = -1;
     if (slots < 0)
-        slots = resident_slots_tmem((const void*)adj32f::adjF_kernel, adj32f::NT, adj32f::SMEM,
+        slots = resident_slots_tmem((const void*)adj32f::adjF_kernel<true>, adj32f::NT, adj32f::SMEM,
                                     adj32f::TM_COLS);
     return zchunk_len((g.nx / adj32f::TX) * (g.ny / adj32f::TY), g.nz, slots, 16, 64);
 }
@@ -623,8 +631,10 @@ void launch_adjoint32_fused(const FusedMaps& maps, const Geom& g, const Mult<flo
                             FieldSet<float> lam, FieldSet<float> out, const float* const E[3],
                             const float* spy, const float* spz, double* partials, int* err,
                             cudaStream_t st) {
-    adj32f::adjF_kernel<<<adjoint32f_blocks(g), adj32f::NT, adj32f::SMEM, st>>>(
-        maps, g, m, lam, out, E[0], E[1], E[2], spy, spz, partials, adjoint32f_tz(g), err);
+    auto kern = spy != nullptr ? adj32f::adjF_kernel<true> : adj32f::adjF_kernel<false>;
+    kern<<<adjoint32f_blocks(g), adj32f::NT, adj32f::SMEM, st>>>(maps, g, m, lam, out, E[0], E[1],
+                                                                  E[2], spy, spz, partials,
+                                                                  adjoint32f_tz(g), err);
 }
 
 }  // namespace fdtd
