@@ -263,10 +263,8 @@ struct fdtd_handle {
     int jx_cap;
     double* partials;   // adjoint gradient partials
     int npart;
-    char* staging[2];   // two dense arrays: host transfers of one component overlap the
-                        // (un)packing of the previous one
-    cudaStream_t xfer;  // copy stream of the host transfers
-    cudaEvent_t filled[2], freed[2];   // per staging buffer: data in place / buffer reusable
+    cudaStream_t xfer;  // copy stream of the host transfers (created on first use)
+    cudaEvent_t filled[2];   // ordering events between the handle's stream and the copy stream
     long long step;
     int use_fused;
     double* dpart;      // diagnostics partials (3 per block)
@@ -493,16 +491,34 @@ int fdtd_set_coeffs(fdtd_handle* h, double dt, const fdtd_coeffs* coeffs) {
     return FDTD_OK;
 }
 
-static int ensure_staging(fdtd_handle* h) {
-    if (h->staging[0]) return FDTD_OK;
-    const size_t n = (size_t)h->g.nx * h->g.ny * h->g.nz * h->esz;
+static int ensure_xfer(fdtd_handle* h) {
+    if (h->xfer) return FDTD_OK;
     CK(cudaStreamCreateWithFlags(&h->xfer, cudaStreamNonBlocking));
-    for (int b = 0; b < 2; ++b) {
-        CK(cudaEventCreateWithFlags(&h->filled[b], cudaEventDisableTiming));
-        CK(cudaEventCreateWithFlags(&h->freed[b], cudaEventDisableTiming));
-    }
-    for (int b = 0; b < 2; ++b) CK(cudaMalloc(&h->staging[b], n));
+    for (int b = 0; b < 2; ++b) CK(cudaEventCreateWithFlags(&h->filled[b], cudaEventDisableTiming));
     return FDTD_OK;
+}
+
+// One 3D copy between a dense host array (nx, ny, nz) and the owned cells of a padded device
+// array (x offset PX, y offset PY, row pitch nxp, nyp rows per plane)
+template <typename T>
+static cudaMemcpy3DParms owned_copy(const Geom& g, void* host, T* dev, bool to_device) {
+    cudaMemcpy3DParms p = {};
+    const cudaPitchedPtr hp = make_cudaPitchedPtr(host, (size_t)g.nx * sizeof(T), g.nx, g.ny);
+    const cudaPitchedPtr dp = make_cudaPitchedPtr(dev, (size_t)g.nxp * sizeof(T), g.nxp, g.nyp);
+    const cudaPos owned = make_cudaPos((size_t)PX * sizeof(T), PY, 0);
+    if (to_device) {
+        p.srcPtr = hp;
+        p.dstPtr = dp;
+        p.dstPos = owned;
+        p.kind = cudaMemcpyHostToDevice;
+    } else {
+        p.srcPtr = dp;
+        p.srcPos = owned;
+        p.dstPtr = hp;
+        p.kind = cudaMemcpyDeviceToHost;
+    }
+    p.extent = make_cudaExtent((size_t)g.nx * sizeof(T), g.ny, g.nz);
+    return p;
 }
 
 // the copy stream starts after everything already queued on the handle's stream
@@ -512,68 +528,57 @@ static int xfer_after_stream(fdtd_handle* h) {
     return FDTD_OK;
 }
 
-// Host -> device: component c goes host -> staging[c % 2] on the copy stream, then is unpacked
-// (padded layout, periodic images) on the handle's stream; the copy of c + 1 overlaps the
-// unpacking of c.
+// Host -> device: each component's owned cells are copied straight into the padded array on the
+// copy stream (one 3D copy), then the periodic images are refreshed on the handle's stream.  A
+// device source goes through the unpacking kernel (padded layout and images in one pass).
 template <typename T>
 static int copy_in(fdtd_handle* h, void* const fields[6], int32_t mem, T* const dst[6]) {
-    const size_t n = (size_t)h->g.nx * h->g.ny * h->g.nz;
     if (mem == FDTD_MEM_HOST) {
-        int rc = ensure_staging(h);
+        int rc = ensure_xfer(h);
         if (rc) return rc;
-        rc = xfer_after_stream(h);
+        rc = xfer_after_stream(h);   // the arrays may still be in use on the handle's stream
         if (rc) return rc;
+        for (int c = 0; c < 6; ++c)
+            if (fields && fields[c]) {
+                const cudaMemcpy3DParms p = owned_copy<T>(h->g, fields[c], dst[c], true);
+                CK(cudaMemcpy3DAsync(&p, h->xfer));
+            }
+        CK(cudaEventRecord(h->filled[1], h->xfer));
+        CK(cudaStreamWaitEvent(h->stream, h->filled[1], 0));
     }
     for (int c = 0; c < 6; ++c) {
         const T* src = (const T*)(fields ? fields[c] : nullptr);
-        if (src && mem == FDTD_MEM_HOST) {
-            const int b = c & 1;
-            if (c >= 2) CK(cudaStreamWaitEvent(h->xfer, h->freed[b], 0));
-            CK(cudaMemcpyAsync(h->staging[b], src, n * sizeof(T), cudaMemcpyHostToDevice, h->xfer));
-            CK(cudaEventRecord(h->filled[b], h->xfer));
-            CK(cudaStreamWaitEvent(h->stream, h->filled[b], 0));
-            launch_unpack<T>(h->g, (const T*)h->staging[b], dst[c], h->stream);
-            CK(cudaGetLastError());
-            CK(cudaEventRecord(h->freed[b], h->stream));
-        } else {
-            launch_unpack<T>(h->g, src, dst[c], h->stream);
-            CK(cudaGetLastError());
-        }
+        if (src && mem == FDTD_MEM_HOST)
+            launch_fill_ghosts<T>(h->g, dst[c], h->stream);
+        else
+            launch_unpack<T>(h->g, src, dst[c], h->stream);   // NULL source: zeros
+        CK(cudaGetLastError());
     }
     if (mem == FDTD_MEM_HOST) CK(cudaStreamSynchronize(h->stream));
     return FDTD_OK;
 }
 
-// Device -> host: component c is packed into staging[c % 2] on the handle's stream, then copied
-// to the host on the copy stream; the packing of c + 1 overlaps the copy of c.
+// Device -> host: one 3D copy of each component's owned cells on the copy stream, after the
+// work queued on the handle's stream; to device memory, the packing kernel.
 template <typename T>
 static int copy_out(fdtd_handle* h, void* const fields[6], int32_t mem, T* const srcs[6]) {
-    const size_t n = (size_t)h->g.nx * h->g.ny * h->g.nz;
     if (mem == FDTD_MEM_HOST) {
-        int rc = ensure_staging(h);
+        int rc = ensure_xfer(h);
         if (rc) return rc;
+        rc = xfer_after_stream(h);
+        if (rc) return rc;
+        for (int c = 0; c < 6; ++c)
+            if (fields[c]) {
+                const cudaMemcpy3DParms p = owned_copy<T>(h->g, fields[c], srcs[c], false);
+                CK(cudaMemcpy3DAsync(&p, h->xfer));
+            }
+        CK(cudaStreamSynchronize(h->xfer));
+        return FDTD_OK;
     }
-    int used = 0;
     for (int c = 0; c < 6; ++c) {
         if (!fields[c]) continue;
-        if (mem == FDTD_MEM_HOST) {
-            const int b = used & 1;
-            if (used >= 2) CK(cudaStreamWaitEvent(h->stream, h->freed[b], 0));
-            launch_pack<T>(h->g, srcs[c], (T*)h->staging[b], h->stream);
-            CK(cudaGetLastError());
-            CK(cudaEventRecord(h->filled[b], h->stream));
-            CK(cudaStreamWaitEvent(h->xfer, h->filled[b], 0));
-            CK(cudaMemcpyAsync(fields[c], h->staging[b], n * sizeof(T), cudaMemcpyDeviceToHost, h->xfer));
-            CK(cudaEventRecord(h->freed[b], h->xfer));
-            ++used;
-        } else {
-            launch_pack<T>(h->g, srcs[c], (T*)fields[c], h->stream);
-            CK(cudaGetLastError());
-        }
-    }
-    if (mem == FDTD_MEM_HOST) {
-        CK(cudaStreamSynchronize(h->xfer));
-        CK(cudaStreamSynchronize(h->stream));
+        launch_pack<T>(h->g, srcs[c], (T*)fields[c], h->stream);
+        CK(cudaGetLastError());
     }
     return FDTD_OK;
 }
@@ -1290,13 +1295,9 @@ void fdtd_destroy(fdtd_handle* h) {
     if (h->aux) cudaFree(h->aux);
     if (h->jx) cudaFree(h->jx);
     if (h->partials) cudaFree(h->partials);
-    if (h->staging[0]) {
+    if (h->xfer) {
         cudaStreamSynchronize(h->xfer);
-        for (int b = 0; b < 2; ++b) {
-            cudaFree(h->staging[b]);
-            cudaEventDestroy(h->filled[b]);
-            cudaEventDestroy(h->freed[b]);
-        }
+        for (int b = 0; b < 2; ++b) cudaEventDestroy(h->filled[b]);
         cudaStreamDestroy(h->xfer);
     }
     if (h->err_dev) cudaFree(h->err_dev);

@@ -154,6 +154,9 @@ template <typename T>
 void launch_pack(const Geom& g, const T* padded, T* dense, cudaStream_t st);
 template <typename T>
 void launch_unpack(const Geom& g, const T* dense, T* padded, cudaStream_t st);
+// the periodic images (ghost cells) of a padded array from its owned cells
+template <typename T>
+void launch_fill_ghosts(const Geom& g, T* padded, cudaStream_t st);
 
 // grad12[beta 3x3 row-major, delta 3] += s[q] * sum over blocks of partial q, where partial
 // q = 3a + w is (axis a; w = 0: delta_a, 1 / 2: beta of the first / second other axis).

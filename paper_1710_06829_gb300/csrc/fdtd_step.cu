@@ -375,6 +375,44 @@ void launch_pack(const Geom& g, const T* padded, T* dense, cudaStream_t st) {
     const long long n = (long long)g.nx * g.ny * g.nz;
     pack_kernel<T><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(g, padded, dense);
 }
+// Periodic images only: every ghost cell of the padded array (rows 0 .. PY-1 and
+// ny+PY .. nyp-1, columns 0 .. PX-1 and nx+PX .. nxp-1 of the owned rows) takes the value of the
+// owned cell it is the image of.  After a host transfer has written the owned cells directly.
+template <typename T>
+__global__ void ghosts_kernel(Geom g, T* __restrict__ F) {
+    const long long per = 2LL * PY * g.nxp + 2LL * PX * g.ny;   // ghost cells per plane
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= per * g.nz) return;
+    const int k = (int)(t / per);
+    int r = (int)(t - (long long)k * per);
+    int ip, jp;
+    const int rows = 2 * PY * g.nxp;
+    if (r < rows) {   // ghost rows
+        const int row = r / g.nxp;
+        ip = r - row * g.nxp;
+        jp = row < PY ? row : g.ny + row;
+    } else {          // ghost columns of the owned rows
+        r -= rows;
+        const int jo = r / (2 * PX);
+        const int c = r - jo * 2 * PX;
+        jp = jo + PY;
+        ip = c < PX ? c : g.nx + c;
+    }
+    int i = (ip - PX) % g.nx;
+    if (i < 0) i += g.nx;
+    int j = (jp - PY) % g.ny;
+    if (j < 0) j += g.ny;
+    const long long base = (long long)k * g.plane;
+    F[base + (long long)jp * g.nxp + ip] = F[base + (long long)(j + PY) * g.nxp + (i + PX)];
+}
+
+template <typename T>
+void launch_fill_ghosts(const Geom& g, T* padded, cudaStream_t st) {
+    const long long n = (2LL * PY * g.nxp + 2LL * PX * g.ny) * g.nz;
+    ghosts_kernel<T><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(g, padded);
+}
+template void launch_fill_ghosts<float>(const Geom&, float*, cudaStream_t);
+template void launch_fill_ghosts<double>(const Geom&, double*, cudaStream_t);
 template void launch_unpack<float>(const Geom&, const float*, float*, cudaStream_t);
 template void launch_unpack<double>(const Geom&, const double*, double*, cudaStream_t);
 template void launch_pack<float>(const Geom&, const float*, float*, cudaStream_t);
