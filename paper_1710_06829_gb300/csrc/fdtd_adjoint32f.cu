@@ -74,14 +74,18 @@ constexpr uint32_t PRO_BYTES = 3u * LPL * 4;
 static_assert(LW == 72 && LH == 12, "the lambda_E boxes are the 72 x 12 boxes of encode_ebox_f32");
 static_assert(MH == 11, "the lambda_B boxes are 72 x 11 (encode_box_f32)");
 
-// Accumulates s w(u) (T_delta, T_beta_b, T_beta_c) into acc[0..2] for the four cells
+// Gradient terms of one cell: s w (T_delta, T_beta_b, T_beta_c) with T_delta = t2 - 3 d0,
+// T_beta = sb - 2 d0, T_beta_c = sc - 2 d0, accumulated as the four sums acc[0..3] of s w times
+// (t2, sb, sc, d0) (four FMAs a cell instead of six); grad_terms() forms the three terms from
+// them once per plane
 template <bool NEG>
 __device__ __forceinline__ void bracket_acc(float* acc, float w, float d0, float t2, float sb,
                                             float sc) {
     const float ww = NEG ? -w : w;
-    acc[0] = fmaf(ww, fmaf(-3.0f, d0, t2), acc[0]);
-    acc[1] = fmaf(ww, fmaf(-2.0f, d0, sb), acc[1]);
-    acc[2] = fmaf(ww, fmaf(-2.0f, d0, sc), acc[2]);
+    acc[0] = fmaf(ww, t2, acc[0]);
+    acc[1] = fmaf(ww, sb, acc[1]);
+    acc[2] = fmaf(ww, sc, acc[2]);
+    acc[3] = fmaf(ww, d0, acc[3]);
 }
 
 // DT_z of a mu component on the four cells at e (transverse x, then y): the own row of planes
@@ -320,13 +324,15 @@ adjF_kernel(const __grid_constant__ FusedMaps maps, Geom g, Mult<float> m, Field
     load_e(wrapz(z0), en);
 
     // gradient partial sums: group 0 holds D*_y, D*_z (entries 3..8), group 1 D*_x, D*_y (0..5).
-    // racc: the plane's FP32 sum; gs, gc: Kahan-compensated FP32 running sum over the planes
-    // (FP64 arithmetic runs at 1/64 of the FP32 rate on this part: a per-plane FP64 add kept its
-    // pipe 41 % busy); FP64 only in the block and grid reductions
-    float racc[6], gs[6], gc[6];
+    // racc: the plane's FP32 sums (four per axis, see bracket_acc); gs, gc: Kahan-compensated
+    // FP32 running sums of the three terms per axis over the planes (FP64 arithmetic runs at 1/64
+    // of the FP32 rate on this part: a per-plane FP64 add kept its pipe 41 % busy); FP64 only in
+    // the block and grid reductions
+    float racc[8], gs[6], gc[6];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) racc[k] = 0.0f;
 #pragma unroll
     for (int k = 0; k < 6; ++k) {
-        racc[k] = 0.0f;
         gs[k] = 0.0f;
         gc[k] = 0.0f;
     }
@@ -468,7 +474,7 @@ adjF_kernel(const __grid_constant__ FusedMaps maps, Geom g, Mult<float> m, Field
                     tm_ld(cle(0, lq), lx);
                     tm_wait_ld(cmm, cm, c0, cp, lx);
                     dtz_g<true>(Gm + MSLOT, G0 + MSLOT, cmm, cm, c0, cp, e, lb, rb, m.cA[2], m.cD[2],
-                                m.cB[2][0], m.cB[2][1], eo[0], racc + 3, t2);
+                                m.cB[2][0], m.cB[2][1], eo[0], racc + 4, t2);
 #pragma unroll
                     for (int u = 0; u < W; ++u) v[u] = __fmaf_rn(s0, lx.v[u], __fsub_rn(t1[u], t2[u]));
                 }
@@ -483,7 +489,7 @@ adjF_kernel(const __grid_constant__ FusedMaps maps, Geom g, Mult<float> m, Field
                     tm_ld(cle(1, lq), ly);
                     tm_wait_ld(cmm, cm, c0, cp, ly);
                     dtz_g<false>(Gm, G0, cmm, cm, c0, cp, e, lb, rb, m.cA[2], m.cD[2], m.cB[2][0],
-                                 m.cB[2][1], eo[1], racc + 3, ya);
+                                 m.cB[2][1], eo[1], racc + 4, ya);
 #pragma unroll
                     for (int u = 0; u < W; ++u) yl[u] = ly.v[u];
                 }
@@ -520,20 +526,23 @@ adjF_kernel(const __grid_constant__ FusedMaps maps, Geom g, Mult<float> m, Field
                     tm_ld(cle(2, lq), lz);
                     tm_wait_ld(xm, x0_, xp, lz);
                     dty_g<true>(Gm, G0, Gp, xm, x0_, xp, e, lb, rb, m.cA[1], m.cD[1], m.cB[1][0],
-                                m.cB[1][2], eo[1], racc + 3, t2);
+                                m.cB[1][2], eo[1], racc + 4, t2);
 #pragma unroll
                     for (int u = 0; u < W; ++u) v[u] = __fmaf_rn(s0, lz.v[u], __fsub_rn(t1[u], t2[u]));
                 }
                 put_seg(out.c[2], po, dst, v);
             }
 #pragma unroll
-            for (int k = 0; k < 6; ++k) {   // compensated add of the plane's partial sum
-                const float y = racc[k] - gc[k];
+            for (int k = 0; k < 6; ++k) {   // the plane's three terms per axis, compensated add
+                const float* r4 = racc + 4 * (k / 3);
+                const float x = fmaf(k % 3 == 0 ? -3.0f : -2.0f, r4[3], r4[k % 3]);
+                const float y = x - gc[k];
                 const float t = gs[k] + y;
                 gc[k] = (t - gs[k]) - y;
                 gs[k] = t;
-                racc[k] = 0.0f;
             }
+#pragma unroll
+            for (int k = 0; k < 8; ++k) racc[k] = 0.0f;
         }
         bool ok_next = true;
         if (tid == PRODUCER && it + 1 < nunits)
