@@ -147,6 +147,45 @@ def test_autograd_checkpointed_matches_oracle():
     assert np.allclose(theta.grad.numpy(), g_ref, rtol=1e-10, atol=1e-12 * np.abs(g_ref).max())
 
 
+def test_autograd_checkpointed_fp32_one_kernel_matches_oracle():
+    """The checkpointed autograd path in FP32 on a TMA-eligible grid: every reverse segment runs
+    the one-kernel step, whose two adjoint state sets alternate across segments of odd length
+    (checkpoint every 5 of 25 steps); loss and tied-theta gradient against the oracle on the
+    FP32-rounded multipliers."""
+    shape = (64, 16, 16)
+    nx, ny, nz = shape
+    dx = [1.0, 1.0, 1.0]
+    theta0 = torch.tensor([-0.05, -0.04, 0.02, 0.01], dtype=torch.float64)
+    b0, d0 = inputs.isotropic_theta(*theta0.tolist())
+    dt = 0.95 * D.dt_max(b0, d0, dx, 3)
+    Ez = inputs.pulse_ez_3d(shape, dx, 20.0, 8.0, 8.0, 8.0).astype(np.float32)
+    z = np.zeros_like(Ez)
+    init = [torch.from_numpy(a) for a in (z, z, Ez, z, z, z)]
+    n, every, xp = 25, 5, 30
+    rng = np.random.default_rng(4)
+    tgt = (rng.standard_normal((n, nz, ny)) * 0.01).astype(np.float32)
+    prob = ProbeLossProblem(shape, dx, dt, init, 2, xp, torch.from_numpy(tgt).cuda(), n, every,
+                            dtype="f32")
+    theta = theta0.clone().requires_grad_(True)
+    beta, delta = tied_coefficients(theta)
+    loss = FdtdProbeLoss.apply(beta, delta, prob)
+    loss.backward()
+    c = rounded_coeffs(b0, d0, dx, dt, 3, np.float32)
+    fields = [a.numpy().astype(np.float64) for a in init]
+    t64 = tgt.astype(np.float64)
+    _, rgb, rgd = oracle_adjoint(c, fields, [np.zeros_like(fields[0])] * 6, n, None, (2, xp, t64))
+    g_ref = np.array([rgd[0], rgd[1] + rgd[2], rgb[0, 1] + rgb[0, 2] + rgb[1, 0] + rgb[2, 0],
+                      rgb[1, 2] + rgb[2, 1]])
+    st = F.State(fields[:3], fields[3:])
+    ref_loss = 0.0
+    for m in range(n):
+        F.step(st, c)
+        ref_loss += float(np.sum((st.E[2][:, :, xp] - t64[m]) ** 2))
+    assert float(loss) == pytest.approx(ref_loss, rel=1e-5)
+    g = theta.grad.numpy()
+    assert np.max(np.abs(g - g_ref)) <= 1e-4 * np.abs(g_ref).max(), (g, g_ref)
+
+
 def test_batched_2d_adjoint_gradient_is_the_sum_over_members():
     shape = (64, 16, 3)
     nx, ny, nz = shape
