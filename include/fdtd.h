@@ -167,7 +167,12 @@ int fdtd_get_adjoint(fdtd_handle* h, void* const fields[6], int32_t mem);
  * non-NULL).  Adds dt * sum_cells lambda_B^{s+1/2} . (dF/dtheta) E^s to
  * grad_dev (12 device doubles: beta[3][3] row-major, then delta[3]; the
  * diagonal entries stay unchanged), where F E = -D* x E.  The sponge is
- * applied as its own transpose.  On return the history is consumed. */
+ * applied as its own transpose.  On return the history is consumed.
+ * FP32 handles whose grid the TMA tiles fit (nx a multiple of 64, ny of 8) run one kernel
+ * per reverse step, out of place: the library then holds two adjoint sets (12 padded arrays,
+ * allocated with the first adjoint call) and alternates between them; fdtd_get_adjoint always
+ * reads the current one.  Setting FDTD_ADJOINT_SPLIT=1 in the environment before
+ * fdtd_create selects the two-kernel in-place step instead (same lambda bitwise). */
 int fdtd_step_adjoint(fdtd_handle* h, int32_t n, const fdtd_probe* probe, double* grad_dev);
 
 /* Diagnostics on the current state, FP64 accumulation, result in device memory
