@@ -20,17 +20,18 @@
 // A CTA owns a 64 x 8 (x, y) tile and a chunk of z planes z0 .. zend-1 and marches z:
 //   phase A, plane p: mu(p) on the tile and on the halo the transposed stencils reach
 //     (x0-2 .. x0+64, y0-2 .. y0+8), from lambda_E planes p and p+1 (TMA boxes 72 x 12 at
-//     x0-4, y0-2 in a five-slot shared ring, copies two planes ahead) and lambda_B(p) (read
-//     from HBM one plane ahead); mu goes to a five-plane shared ring and, for the own cells
-//     of planes z0 .. zend-1, to lambda_B';
+//     x0-4, y0-2, three-slot ring) and lambda_B(p) (TMA boxes 72 x 11, two-slot ring), both
+//     copied two planes ahead; mu goes to a five-plane shared ring and, for the own cells of
+//     planes z0 .. zend-1, to lambda_B';
 //   phase B, plane q = p-2: lambda_E'(q) and the gradient terms of the own cells, from mu
-//     planes q-2 .. q+1 (formed in the four previous iterations), lambda_E(q) (ring) and
-//     E^n(q) (HBM, one plane ahead).
+//     planes q-2 .. q+1 (formed in the four previous iterations), lambda_E(q) and E^n(q) (HBM,
+//     one plane ahead).
 // One block barrier per plane.  mu of the halo planes z0-2, z0-1 and zend is recomputed by
 // each chunk.  Each thread's own rows of mu (five planes) and of lambda_E (three planes) are
 // also kept in tensor memory (TMEM, 128 columns per CTA), written once in phase A and read in
-// phase B, which then takes only the neighbouring rows from the shared ring.  The result goes to the other adjoint state set: CTAs of neighbouring tiles
-// read halos of lambda_E and lambda_B, so an in-place update would race.
+// phase B, which then takes only the neighbouring rows from the shared ring.  The result goes
+// to the other adjoint state set: CTAs of neighbouring tiles read halos of lambda_E and
+// lambda_B, so an in-place update would race.
 //
 // Threads: two groups of four warps; in phase B both take the 128 own segments (row o / 16,
 // x offset 4 (o % 16) for o = thread mod 128) and split the six transposed stencils three and

@@ -133,7 +133,8 @@ def test_host_buffers_roundtrip():
 
 
 @pytest.mark.parametrize("dtype,shape", [("f32", (64, 16, 12)), ("f64", (64, 16, 12)),
-                                          ("f32", (20, 12, 6)), ("f32", (68, 9, 5))])
+                                          ("f32", (20, 12, 6)), ("f32", (68, 9, 5)),
+                                          ("f64", (4, 1, 2))])
 def test_host_upload_equals_device_upload(dtype, shape):
     """A state uploaded from pinned host memory (owned cells copied straight into the padded
     arrays, then the periodic images filled) steps bitwise like the same state uploaded from
