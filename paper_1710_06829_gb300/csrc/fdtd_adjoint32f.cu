@@ -363,14 +363,8 @@ adjF_kernel(const __grid_constant__ FusedMaps maps, Geom g, Mult<float> m, Field
                                        e3 = (e3 == 2 ? 0 : e3 + 1)) {
         const int p = z0 - 2 + it;
         const int q = p - 2;
-        bool ok = true;
-        if (it < nunits) {
-            if (it == 0) ok = mbar_wait(&bar[NS], 0);
-            ok = ok && mbar_wait(&bar[it % NS], (uint32_t)((it / NS) & 1));
-        }
-        ok = __all_sync(FULL, ok);   // keeps the shuffles below warp-uniform
         // ---- lambda_E'_y of the previous plane (group 0)
-        if (ok && !grp1 && ypend) {
+        if (!grp1 && ypend) {
             const Q4 b = ldq(sY + ((it + 1) & 1) * NOWN * W, o * W);
             float v[W];
 #pragma unroll
@@ -378,69 +372,10 @@ adjF_kernel(const __grid_constant__ FusedMaps maps, Geom g, Mult<float> m, Field
             put_seg(out.c[1], ypo, dst, v);
             ypend = false;
         }
-        // ---- phase A: mu(p) (warps with a task)
-        if (ok && p <= zend && a_warp) {
-            const int pw1 = pw + 1 == g.nz ? 0 : pw + 1;
-            const float* L0 = sL + lp * 3 * LSLOT;
-            const float* L1 = sL + (lp == NL - 1 ? 0 : lp + 1) * 3 * LSLOT;
-            const float* Bp = sB + (it & 1) * 3 * MSLOT;
-            const Q4 bxq = ldq(Bp, ea), byq = ldq(Bp + MSLOT, ea), bzq = ldq(Bp + 2 * MSLOT, ea);
-            const Q4 ex = ldq(L0, ea), ey = ldq(L0 + LSLOT, ea), ez = ldq(L0 + 2 * LSLOT, ea);
-            const Q4 exy = ldq(L0, ea + LW), ezy = ldq(L0 + 2 * LSLOT, ea + LW);
-            const Q4 exz = ldq(L1, ea), eyz = ldq(L1 + LSLOT, ea);
-            float ey4 = from_right(ey.v[0]), ez4 = from_right(ez.v[0]);
-            if (a_rb) {
-                ey4 = L0[LSLOT + ea + 4];
-                ez4 = L0[2 * LSLOT + ea + 4];
-            }
-            float s0 = 1.0f, syp = 1.0f, szp = 1.0f;
-            if (SP) {
-                s0 = spy[jwa] * spz[pw];
-                syp = spy[jwap] * spz[pw];
-                szp = spy[jwa] * spz[pw1];
-            }
-            float mux[W], muy[W], muz[W];
-#pragma unroll
-            for (int u = 0; u < W; ++u) {
-                // the rounding order of the two-kernel step's mu (fdtd_adjoint32.cu), fixed by
-                // intrinsics, which the compiler never contracts
-                const float ex0 = __fmul_rn(s0, ex.v[u]), ey0 = __fmul_rn(s0, ey.v[u]),
-                            ez0 = __fmul_rn(s0, ez.v[u]);
-                const float ezx = u < W - 1 ? ez.v[u + 1] : ez4;   // x+1, unscaled
-                const float eyx = u < W - 1 ? ey.v[u + 1] : ey4;
-                const float gx = __fmaf_rn(m.cE[2], __fmaf_rn(-szp, eyz.v[u], ey0),
-                                           __fmul_rn(-m.cE[1], __fmaf_rn(-syp, ezy.v[u], ez0)));
-                const float gy = __fmaf_rn(m.cE[0], __fmaf_rn(-s0, ezx, ez0),
-                                           __fmul_rn(-m.cE[2], __fmaf_rn(-szp, exz.v[u], ex0)));
-                const float gz = __fmaf_rn(m.cE[1], __fmaf_rn(-syp, exy.v[u], ex0),
-                                           __fmul_rn(-m.cE[0], __fmaf_rn(-s0, eyx, ey0)));
-                mux[u] = __fmul_rn(s0, __fadd_rn(bxq.v[u], gx));
-                muy[u] = __fmul_rn(s0, __fadd_rn(byq.v[u], gy));
-                muz[u] = __fmul_rn(s0, __fadd_rn(bzq.v[u], gz));
-            }
-            if (has_task) {
-                float* M = sM + sp * 3 * MSLOT;
-                stv(M, ea, mux);
-                stv(M + MSLOT, ea, muy);
-                stv(M + 2 * MSLOT, ea, muz);
-            }
-            if (a_own) {   // own rows of mu(p) and lambda_E(p) to TMEM (warp-uniform)
-                tm_st(cmu(0, sp), mux);
-                tm_st(cmu(1, sp), muy);
-                tm_st(cmu(2, sp), muz);
-                tm_st(cle(0, e3), ex);
-                tm_st(cle(1, e3), ey);
-                tm_st(cle(2, e3), ez);
-            }
-            if (a_own && p >= z0 && p < zend) {   // mu -> lambda_B' (own cells and their images)
-                const unsigned po = (unsigned)pw * plane;
-                put_seg(out.c[3], po, adst, mux);
-                put_seg(out.c[4], po, adst, muy);
-                put_seg(out.c[5], po, adst, muz);
-            }
-        }
-        // ---- phase B: lambda_E'(q) and the gradient terms (warp-uniform)
-        if (ok && q >= z0 && q < zend) {
+        // ---- phase B: lambda_E'(q) and the gradient terms (warp-uniform); it reads no data of
+        // this iteration's copies (mu of earlier planes, lambda_E(q) from TMEM, E^n from registers),
+        // so it runs before the wait for them
+        if (q >= z0 && q < zend) {
 #pragma unroll
             for (int c = 0; c < 2; ++c)
 #pragma unroll
@@ -545,13 +480,78 @@ adjF_kernel(const __grid_constant__ FusedMaps maps, Geom g, Mult<float> m, Field
 #pragma unroll
             for (int k = 0; k < 8; ++k) racc[k] = 0.0f;
         }
-        bool ok_next = true;
-        if (tid == PRODUCER && it + 1 < nunits)
-            ok_next = mbar_wait(&bar[(it + 1) % NS], (uint32_t)(((it + 1) / NS) & 1));
+        // ---- the copies of this iteration (lambda_E(p+1), lambda_B(p)), issued two planes ago
+        bool ok = true;
+        if (it < nunits) {
+            if (it == 0) ok = mbar_wait(&bar[NS], 0);
+            ok = ok && mbar_wait(&bar[it % NS], (uint32_t)((it / NS) & 1));
+        }
+        ok = __all_sync(FULL, ok);   // keeps the shuffles below warp-uniform
+        // ---- phase A: mu(p) (warps with a task)
+        if (ok && p <= zend && a_warp) {
+            const int pw1 = pw + 1 == g.nz ? 0 : pw + 1;
+            const float* L0 = sL + lp * 3 * LSLOT;
+            const float* L1 = sL + (lp == NL - 1 ? 0 : lp + 1) * 3 * LSLOT;
+            const float* Bp = sB + (it & 1) * 3 * MSLOT;
+            const Q4 bxq = ldq(Bp, ea), byq = ldq(Bp + MSLOT, ea), bzq = ldq(Bp + 2 * MSLOT, ea);
+            const Q4 ex = ldq(L0, ea), ey = ldq(L0 + LSLOT, ea), ez = ldq(L0 + 2 * LSLOT, ea);
+            const Q4 exy = ldq(L0, ea + LW), ezy = ldq(L0 + 2 * LSLOT, ea + LW);
+            const Q4 exz = ldq(L1, ea), eyz = ldq(L1 + LSLOT, ea);
+            float ey4 = from_right(ey.v[0]), ez4 = from_right(ez.v[0]);
+            if (a_rb) {
+                ey4 = L0[LSLOT + ea + 4];
+                ez4 = L0[2 * LSLOT + ea + 4];
+            }
+            float s0 = 1.0f, syp = 1.0f, szp = 1.0f;
+            if (SP) {
+                s0 = spy[jwa] * spz[pw];
+                syp = spy[jwap] * spz[pw];
+                szp = spy[jwa] * spz[pw1];
+            }
+            float mux[W], muy[W], muz[W];
+#pragma unroll
+            for (int u = 0; u < W; ++u) {
+                // the rounding order of the two-kernel step's mu (fdtd_adjoint32.cu), fixed by
+                // intrinsics, which the compiler never contracts
+                const float ex0 = __fmul_rn(s0, ex.v[u]), ey0 = __fmul_rn(s0, ey.v[u]),
+                            ez0 = __fmul_rn(s0, ez.v[u]);
+                const float ezx = u < W - 1 ? ez.v[u + 1] : ez4;   // x+1, unscaled
+                const float eyx = u < W - 1 ? ey.v[u + 1] : ey4;
+                const float gx = __fmaf_rn(m.cE[2], __fmaf_rn(-szp, eyz.v[u], ey0),
+                                           __fmul_rn(-m.cE[1], __fmaf_rn(-syp, ezy.v[u], ez0)));
+                const float gy = __fmaf_rn(m.cE[0], __fmaf_rn(-s0, ezx, ez0),
+                                           __fmul_rn(-m.cE[2], __fmaf_rn(-szp, exz.v[u], ex0)));
+                const float gz = __fmaf_rn(m.cE[1], __fmaf_rn(-syp, exy.v[u], ex0),
+                                           __fmul_rn(-m.cE[0], __fmaf_rn(-s0, eyx, ey0)));
+                mux[u] = __fmul_rn(s0, __fadd_rn(bxq.v[u], gx));
+                muy[u] = __fmul_rn(s0, __fadd_rn(byq.v[u], gy));
+                muz[u] = __fmul_rn(s0, __fadd_rn(bzq.v[u], gz));
+            }
+            if (has_task) {
+                float* M = sM + sp * 3 * MSLOT;
+                stv(M, ea, mux);
+                stv(M + MSLOT, ea, muy);
+                stv(M + 2 * MSLOT, ea, muz);
+            }
+            if (a_own) {   // own rows of mu(p) and lambda_E(p) to TMEM (warp-uniform)
+                tm_st(cmu(0, sp), mux);
+                tm_st(cmu(1, sp), muy);
+                tm_st(cmu(2, sp), muz);
+                tm_st(cle(0, e3), ex);
+                tm_st(cle(1, e3), ey);
+                tm_st(cle(2, e3), ez);
+            }
+            if (a_own && p >= z0 && p < zend) {   // mu -> lambda_B' (own cells and their images)
+                const unsigned po = (unsigned)pw * plane;
+                put_seg(out.c[3], po, adst, mux);
+                put_seg(out.c[4], po, adst, muy);
+                put_seg(out.c[5], po, adst, muz);
+            }
+        }
         // the TMEM rows stored in this iteration are read by other warps after the barrier
         tm_wait_st();
         tm_fence_before();
-        const bool stop = __syncthreads_or(!ok || !ok_next);
+        const bool stop = __syncthreads_or(!ok);
         tm_fence_after();
         if (stop) {
             failed = true;
