@@ -26,8 +26,9 @@
 //   phase B, plane q = p-2: lambda_E'(q) and the gradient terms of the own cells, from mu
 //     planes q-2 .. q+1 (formed in the four previous iterations), lambda_E(q) and E^n(q) (HBM,
 //     one plane ahead).
-// One block barrier per plane.  mu of the halo planes z0-2, z0-1 and zend is recomputed by
-// each chunk.  Each thread's own rows of mu (five planes) and of lambda_E (three planes) are
+// Within an iteration phase B runs first: it reads none of the plane's new copies, so the
+// copies get its duration to land before phase A waits for them.  One block barrier per plane.
+// mu of the halo planes z0-2, z0-1 and zend is recomputed by each chunk.  Each thread's own rows of mu (five planes) and of lambda_E (three planes) are
 // also kept in tensor memory (TMEM, 128 columns per CTA), written once in phase A and read in
 // phase B, which then takes only the neighbouring rows from the shared ring.  The result goes
 // to the other adjoint state set: CTAs of neighbouring tiles read halos of lambda_E and
