@@ -143,7 +143,7 @@ def test_autograd_checkpointed_matches_oracle():
     for m in range(n):
         F.step(s, c)
         ref_loss += float(np.sum((s.E[2][:, :, xp] - tgt[m]) ** 2))
-    assert float(loss) == pytest.approx(ref_loss, rel=1e-12)
+    assert float(loss.detach()) == pytest.approx(ref_loss, rel=1e-12)
     assert np.allclose(theta.grad.numpy(), g_ref, rtol=1e-10, atol=1e-12 * np.abs(g_ref).max())
 
 
@@ -181,7 +181,7 @@ def test_autograd_checkpointed_fp32_one_kernel_matches_oracle():
     for m in range(n):
         F.step(st, c)
         ref_loss += float(np.sum((st.E[2][:, :, xp] - t64[m]) ** 2))
-    assert float(loss) == pytest.approx(ref_loss, rel=1e-5)
+    assert float(loss.detach()) == pytest.approx(ref_loss, rel=1e-5)
     g = theta.grad.numpy()
     assert np.max(np.abs(g - g_ref)) <= 1e-4 * np.abs(g_ref).max(), (g, g_ref)
 
